@@ -32,6 +32,8 @@ One iteration, with relaxation ``alpha``::
 """
 from __future__ import annotations
 
+import time
+
 import numpy as np
 import scipy.linalg as sla
 
@@ -152,7 +154,8 @@ def solve(A, b, c, cone, *, eps=1e-4, eps_infeas=None, alpha=1.5, max_iters=1000
         unbounded   if -c^T u_x > 0 and ||A u_x + v_s|| <= eps_infeas (-c^T u_x)
 
     Returns a dict with ``x, y, s, status, iters, pobj, dobj, pri, dual, gap,
-    u, v, cg_steps`` and, if ``trajectory`` > 0, the first ``trajectory``
+    u, v, cg_steps``, the wall times ``t_setup`` / ``t_iter`` of the setup and
+    of the iterations, and, if ``trajectory`` > 0, the first ``trajectory``
     iterates ``traj_u``/``traj_v``.
     """
     op = A if isinstance(A, Operator) else Operator(A)
@@ -161,9 +164,11 @@ def solve(A, b, c, cone, *, eps=1e-4, eps_infeas=None, alpha=1.5, max_iters=1000
     c = np.asarray(c, dtype=np.float64)
     if eps_infeas is None:
         eps_infeas = eps
+    t0 = time.perf_counter()
     ls = _LinSys(op, "direct" if linsys == "direct" else "cg")
 
     g_x, g_y, hg = setup(op, b, c, ls)
+    t1 = time.perf_counter()
 
     u = np.zeros(n + m + 1)
     v = np.zeros(n + m + 1)
@@ -210,6 +215,7 @@ def solve(A, b, c, cone, *, eps=1e-4, eps_infeas=None, alpha=1.5, max_iters=1000
                 status = st
                 break
 
+    t2 = time.perf_counter()
     tau = u[-1]
     x = u[:n] / tau if tau > 0 else np.full(n, np.nan)
     y = u[n:n + m] / tau if tau > 0 else np.full(m, np.nan)
@@ -225,7 +231,8 @@ def solve(A, b, c, cone, *, eps=1e-4, eps_infeas=None, alpha=1.5, max_iters=1000
     out = {"x": x, "y": y, "s": s, "status": status, "iters": it,
            "pobj": float(c @ x), "dobj": float(-(b @ y)),
            "pri": res[0], "dual": res[1], "gap": res[2],
-           "u": u, "v": v, "cg_steps": cg_steps, "g_x": g_x, "g_y": g_y, "hg": hg}
+           "u": u, "v": v, "cg_steps": cg_steps, "g_x": g_x, "g_y": g_y, "hg": hg,
+           "t_setup": t1 - t0, "t_iter": t2 - t1}
     if trajectory:
         out["traj_u"] = np.array(traj_u)
         out["traj_v"] = np.array(traj_v)

@@ -1,0 +1,127 @@
+// Internal declarations shared by the translation units of libcvxb300.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+
+#include <atomic>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/cvxb300.h"
+
+namespace cf {
+
+// ------------------------------------------------------------------ errors
+void set_error(const std::string& msg);
+cf_err fail(cf_err code, const std::string& msg);
+cf_err cuda_fail(cudaError_t e, const char* what, const char* file, int line);
+
+#define CF_CUDA(expr)                                                       \
+  do {                                                                      \
+    cudaError_t _e = (expr);                                                \
+    if (_e != cudaSuccess) return ::cf::cuda_fail(_e, #expr, __FILE__, __LINE__); \
+  } while (0)
+
+#define CF_TRY(expr)                 \
+  do {                               \
+    cf_err _r = (expr);              \
+    if (_r != CF_OK) return _r;      \
+  } while (0)
+
+// Copy between any two addresses (host or device) through unified addressing.
+cf_err copy_any(void* dst, const void* src, size_t bytes, cudaStream_t s);
+bool is_device_ptr(const void* p);
+
+constexpr int kThreads = 256;       // block size of the vector kernels
+constexpr int kMaxRedBlocks = 1184; // 148 SMs x 8: cap on reduction grids
+constexpr int kRedSlots = 8;        // doubles per block in a partial-sum buffer
+
+inline int grid_for(int64_t n, int per_thread = 4) {
+  int64_t g = (n + (int64_t)kThreads * per_thread - 1) / ((int64_t)kThreads * per_thread);
+  if (g < 1) g = 1;
+  if (g > kMaxRedBlocks) g = kMaxRedBlocks;
+  return (int)g;
+}
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace cf
+
+// ----------------------------------------------------------------- context
+struct cf_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int sm_count = 148;
+};
+
+// ---------------------------------------------------------------- operators
+enum OpKind {
+  OP_DENSE, OP_CSR, OP_CONV1D, OP_CONV2D, OP_DIAG, OP_ZERO,
+  OP_VSTACK, OP_HSTACK, OP_BLOCKDIAG, OP_PRODUCT, OP_SUM, OP_SCALE, OP_ADJOINT, OP_KRON
+};
+
+struct cf_op {
+  std::atomic<int> refs{1};
+  cf_ctx* ctx = nullptr;
+  OpKind kind = OP_ZERO;
+  int64_t m = 0, n = 0;
+  std::vector<cf_op*> parts;
+  double alpha = 1.0;
+  // dense: row-major, leading dimension lda >= n (multiple of 16 elements)
+  cf_prec prec = CF_FP32;
+  void* a = nullptr;
+  float* row_scale = nullptr;
+  int64_t lda = 0;
+  // csr (and its transpose, built at creation for a deterministic adjoint)
+  int64_t nnz = 0;
+  int32_t *rowptr = nullptr, *col = nullptr, *t_rowptr = nullptr, *t_col = nullptr;
+  void *val = nullptr, *t_val = nullptr;
+  // conv1d: taps reversed and zero-padded to Lp (multiple of 8), for the
+  // forward map and for the adjoint (whose taps are k reversed)
+  int64_t L = 0, Lp = 0;
+  float *w_fwd = nullptr, *w_adj = nullptr;
+  // conv2d
+  int64_t h = 0, w = 0, kh = 0, kw = 0;
+  float *k2_fwd = nullptr, *k2_adj = nullptr;
+  // diag (nullptr: identity)
+  float* d = nullptr;
+  size_t device_bytes = 0;  // bytes this node itself owns on the device
+};
+
+namespace cf {
+
+// Workspace (float count) op_apply needs for this node and below.
+size_t op_ws_floats(const cf_op* op, bool trans);
+// Device bytes of the whole tree (shared parts counted once per reference).
+size_t op_tree_bytes(const cf_op* op);
+// y = alpha * op(x) + (acc ? y : 0), op(x) = A x or A^T x; ws: op_ws_floats floats.
+void op_apply(const cf_op* op, bool trans, float alpha, const float* x, float* y, bool acc,
+              float* ws, cudaStream_t s);
+void op_retain(cf_op* op);
+
+// ---- leaf launchers (kernels in k_*.cu)
+void launch_fill(cudaStream_t s, int64_t n, float v, float* y);
+void launch_diag(cudaStream_t s, int64_t n, const float* d, float alpha, const float* x, float* y,
+                 bool acc);
+void launch_conv1d(cudaStream_t s, int64_t n_out, int64_t n_in, int64_t Lp, int64_t shift,
+                   const float* wrev, float alpha, const float* x, float* y, bool acc);
+void launch_conv2d(cudaStream_t s, int64_t Ho, int64_t Wo, int64_t Hi, int64_t Wi, int64_t kh,
+                   int64_t kw, int64_t sh, int64_t sw, const float* kern, float alpha,
+                   const float* x, float* y, bool acc);
+void launch_gemv_n(cudaStream_t s, cf_prec p, int64_t m, int64_t n, int64_t lda, const void* A,
+                   const float* rs, float alpha, const float* x, float* y, bool acc);
+size_t gemv_t_ws_floats(int64_t m, int64_t n, int64_t lda);
+void launch_gemv_t(cudaStream_t s, cf_prec p, int64_t m, int64_t n, int64_t lda, const void* A,
+                   const float* rs, float alpha, const float* x, float* y, bool acc, float* ws);
+void launch_csr(cudaStream_t s, cf_prec p, int64_t m, const int32_t* rowptr, const int32_t* col,
+                const void* val, float alpha, const float* x, float* y, bool acc);
+void launch_gemm(cudaStream_t s, int64_t M, int64_t N, int64_t K, const float* A, int64_t lda,
+                 bool ta, const float* B, int64_t ldb, bool tb, float alpha, float* C, bool acc);
+void launch_quantize(cudaStream_t s, cf_prec p, int64_t m, int64_t n, int64_t lda,
+                     const float* src, void* dst, float* rs);
+
+}  // namespace cf

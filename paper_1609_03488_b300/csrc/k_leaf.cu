@@ -1,0 +1,484 @@
+// Leaf kernels of the structured operators (Section 3.1): every kernel
+// computes y = alpha * op(x) + (acc ? y : 0).
+#include "internal.cuh"
+
+namespace cf {
+
+// ------------------------------------------------------------ elementwise
+__global__ void k_fill(int64_t n, float v, float* __restrict__ y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = v;
+}
+
+__global__ void k_diag(int64_t n, const float* __restrict__ d, float alpha,
+                       const float* __restrict__ x, float* __restrict__ y, bool acc) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float v = alpha * (d ? d[i] * x[i] : x[i]);
+    y[i] = acc ? y[i] + v : v;
+  }
+}
+
+void launch_fill(cudaStream_t s, int64_t n, float v, float* y) {
+  if (n <= 0) return;
+  k_fill<<<grid_for(n), kThreads, 0, s>>>(n, v, y);
+}
+
+void launch_diag(cudaStream_t s, int64_t n, const float* d, float alpha, const float* x, float* y,
+                 bool acc) {
+  if (n <= 0) return;
+  k_diag<<<grid_for(n), kThreads, 0, s>>>(n, d, alpha, x, y, acc);
+}
+
+// ------------------------------------------------------------ 1-D convolution
+// out[i] = sum_{l < Lp} w[l] in[i + shift - l]  (in = 0 outside [0, n_in)),
+// given wrev[j] = w[Lp - 1 - j].  Forward full convolution: w = k, shift = 0;
+// adjoint (correlation): w = k reversed, shift = L - 1.
+//
+// A CTA owns kConvTile consecutive outputs; each thread keeps kConvR
+// consecutive outputs in registers and slides a 2*kConvR input window over
+// the taps, so one 16-byte shared load feeds kConvR fused multiply-adds.
+// The shared input tile is padded by 4 floats every 32 so that the 16-byte
+// window loads of 8 neighbouring lanes (stride kConvR floats) hit distinct
+// banks.  Taps are processed in chunks of at most kConvChunk.
+constexpr int kConvThreads = 128;
+constexpr int kConvR = 8;
+constexpr int kConvTile = kConvThreads * kConvR;
+constexpr int kConvChunk = 2048;
+
+__device__ __forceinline__ int conv_pad(int j) { return j + ((j >> 5) << 2); }
+
+__global__ void __launch_bounds__(kConvThreads)
+k_conv1d(int64_t n_out, int64_t n_in, int64_t Lp, int64_t shift, const float* __restrict__ wrev,
+         float alpha, const float* __restrict__ x, float* __restrict__ y, bool acc) {
+  extern __shared__ __align__(16) float sm[];
+  const int tid = threadIdx.x;
+  const int64_t i0 = (int64_t)blockIdx.x * kConvTile;
+  float accum[kConvR];
+#pragma unroll
+  for (int r = 0; r < kConvR; ++r) accum[r] = 0.f;
+
+  const int lc_max = (int)(Lp < kConvChunk ? Lp : (int64_t)kConvChunk);
+  float* in_s = sm;
+  float* w_s = sm + conv_pad(kConvTile + lc_max + kConvR) + 4;
+
+  for (int64_t l0 = 0; l0 < Lp; l0 += kConvChunk) {
+    const int lc = (int)((Lp - l0) < kConvChunk ? (Lp - l0) : (int64_t)kConvChunk);
+    const int64_t base = i0 + shift - l0 - (lc - 1);
+    __syncthreads();
+    for (int j = tid; j < kConvTile + lc + kConvR; j += kConvThreads) {
+      int64_t g = base + j;
+      in_s[conv_pad(j)] = (g >= 0 && g < n_in) ? __ldg(x + g) : 0.f;
+    }
+    const float* wsrc = wrev + (Lp - l0 - lc);
+    for (int j = tid; j < lc; j += kConvThreads) w_s[j] = __ldg(wsrc + j);
+    __syncthreads();
+
+    const int o = tid * kConvR;
+    float win[2 * kConvR];
+#pragma unroll
+    for (int q = 0; q < kConvR; q += 4) {
+      float4 t4 = *reinterpret_cast<const float4*>(&in_s[conv_pad(o + q)]);
+      win[q] = t4.x; win[q + 1] = t4.y; win[q + 2] = t4.z; win[q + 3] = t4.w;
+    }
+    for (int mb = 0; mb < lc; mb += kConvR) {
+#pragma unroll
+      for (int q = 0; q < kConvR; q += 4) {
+        float4 t4 = *reinterpret_cast<const float4*>(&in_s[conv_pad(o + mb + kConvR + q)]);
+        win[kConvR + q] = t4.x; win[kConvR + q + 1] = t4.y;
+        win[kConvR + q + 2] = t4.z; win[kConvR + q + 3] = t4.w;
+      }
+      float wv[kConvR];
+#pragma unroll
+      for (int q = 0; q < kConvR; q += 4) {
+        float4 t4 = *reinterpret_cast<const float4*>(&w_s[mb + q]);
+        wv[q] = t4.x; wv[q + 1] = t4.y; wv[q + 2] = t4.z; wv[q + 3] = t4.w;
+      }
+#pragma unroll
+      for (int dd = 0; dd < kConvR; ++dd)
+#pragma unroll
+        for (int r = 0; r < kConvR; ++r) accum[r] = fmaf(wv[dd], win[r + dd], accum[r]);
+#pragma unroll
+      for (int q = 0; q < kConvR; ++q) win[q] = win[kConvR + q];
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < kConvR; ++r) {
+    int64_t i = i0 + tid * kConvR + r;
+    if (i < n_out) {
+      float v = alpha * accum[r];
+      y[i] = acc ? y[i] + v : v;
+    }
+  }
+}
+
+void launch_conv1d(cudaStream_t s, int64_t n_out, int64_t n_in, int64_t Lp, int64_t shift,
+                   const float* wrev, float alpha, const float* x, float* y, bool acc) {
+  if (n_out <= 0) return;
+  int lc_max = (int)std::min<int64_t>(Lp, kConvChunk);
+  size_t smem = (size_t)(((kConvTile + lc_max + kConvR) + (((kConvTile + lc_max + kConvR) >> 5) << 2)) + 4 + lc_max) * sizeof(float);
+  int64_t grid = (n_out + kConvTile - 1) / kConvTile;
+  k_conv1d<<<(unsigned)grid, kConvThreads, smem, s>>>(n_out, n_in, Lp, shift, wrev, alpha, x, y, acc);
+}
+
+// ------------------------------------------------------------ 2-D convolution
+// out[a, b] = sum_{p<kh, q<kw} w[p, q] in[a + sh - p, b + sw - q]; a 16 x 16
+// output tile per CTA with its input halo and the taps staged in shared memory.
+constexpr int kC2T = 16;
+
+__global__ void __launch_bounds__(kC2T* kC2T)
+k_conv2d(int64_t Ho, int64_t Wo, int64_t Hi, int64_t Wi, int kh, int kw, int64_t sh, int64_t sw,
+         const float* __restrict__ kern, float alpha, const float* __restrict__ x,
+         float* __restrict__ y, bool acc) {
+  extern __shared__ float sm[];
+  const int TH = kC2T + kh - 1, TW = kC2T + kw - 1;
+  float* in_s = sm;
+  float* k_s = sm + TH * TW;
+  const int64_t a0 = (int64_t)blockIdx.y * kC2T, b0 = (int64_t)blockIdx.x * kC2T;
+  const int tid = threadIdx.y * kC2T + threadIdx.x;
+  for (int j = tid; j < kh * kw; j += kC2T * kC2T) k_s[j] = kern[j];
+  // input rows a0 + sh - (kh-1) .. a0 + sh + kC2T - 1
+  for (int j = tid; j < TH * TW; j += kC2T * kC2T) {
+    int r = j / TW, c = j % TW;
+    int64_t gi = a0 + sh - (kh - 1) + r, gj = b0 + sw - (kw - 1) + c;
+    in_s[j] = (gi >= 0 && gi < Hi && gj >= 0 && gj < Wi) ? x[gi * Wi + gj] : 0.f;
+  }
+  __syncthreads();
+  const int ty = threadIdx.y, tx = threadIdx.x;
+  float accv = 0.f;
+  for (int p = 0; p < kh; ++p)
+    for (int q = 0; q < kw; ++q)
+      accv = fmaf(k_s[p * kw + q], in_s[(ty + kh - 1 - p) * TW + (tx + kw - 1 - q)], accv);
+  int64_t a = a0 + ty, b = b0 + tx;
+  if (a < Ho && b < Wo) {
+    float v = alpha * accv;
+    y[a * Wo + b] = acc ? y[a * Wo + b] + v : v;
+  }
+}
+
+void launch_conv2d(cudaStream_t s, int64_t Ho, int64_t Wo, int64_t Hi, int64_t Wi, int64_t kh,
+                   int64_t kw, int64_t sh, int64_t sw, const float* kern, float alpha,
+                   const float* x, float* y, bool acc) {
+  if (Ho <= 0 || Wo <= 0) return;
+  dim3 grid((unsigned)((Wo + kC2T - 1) / kC2T), (unsigned)((Ho + kC2T - 1) / kC2T));
+  size_t smem = ((kC2T + kh - 1) * (kC2T + kw - 1) + kh * kw) * sizeof(float);
+  k_conv2d<<<grid, dim3(kC2T, kC2T), smem, s>>>(Ho, Wo, Hi, Wi, (int)kh, (int)kw, sh, sw, kern,
+                                                alpha, x, y, acc);
+}
+
+// ------------------------------------------------------------ dense GEMV
+// 16-byte loads of the stored operand, unpacked to float32.
+template <typename T> struct Vec;
+template <> struct Vec<float> {
+  static constexpr int N = 4;
+  __device__ static void unpack(const uint4& u, float* f) {
+    f[0] = __uint_as_float(u.x); f[1] = __uint_as_float(u.y);
+    f[2] = __uint_as_float(u.z); f[3] = __uint_as_float(u.w);
+  }
+};
+template <> struct Vec<__nv_bfloat16> {
+  static constexpr int N = 8;
+  __device__ static void unpack(const uint4& u, float* f) {
+    const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      f[2 * k] = __uint_as_float(w[k] << 16);
+      f[2 * k + 1] = __uint_as_float(w[k] & 0xffff0000u);
+    }
+  }
+};
+template <> struct Vec<__nv_fp8_e4m3> {
+  static constexpr int N = 16;
+  __device__ static void unpack(const uint4& u, float* f) {
+    const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+#pragma unroll
+      for (int b = 0; b < 4; b += 2) {
+        __nv_fp8x2_storage_t pair = (__nv_fp8x2_storage_t)((w[k] >> (8 * b)) & 0xffff);
+        __half2_raw h2 = __nv_cvt_fp8x2_to_halfraw2(pair, __NV_E4M3);
+        __half2 hh = *reinterpret_cast<__half2*>(&h2);
+        float2 ff = __half22float2(hh);
+        f[4 * k + b] = ff.x;
+        f[4 * k + b + 1] = ff.y;
+      }
+    }
+  }
+};
+
+constexpr int kGemvRows = 4;  // rows per warp in y = A x
+
+// y[i] = alpha * s_i * sum_j A[i, j] x[j]: a warp handles kGemvRows rows, so
+// each slice of x it loads is reused kGemvRows times.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_gemv_n(int64_t m, int64_t n, int64_t lda, const T* __restrict__ A, const float* __restrict__ rs,
+         float alpha, const float* __restrict__ x, float* __restrict__ y, bool acc) {
+  constexpr int V = Vec<T>::N;
+  const int lane = threadIdx.x & 31;
+  const int64_t row0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * kGemvRows;
+  if (row0 >= m) return;
+  const bool xal = ((reinterpret_cast<uintptr_t>(x) & 15) == 0);
+  float accv[kGemvRows];
+#pragma unroll
+  for (int r = 0; r < kGemvRows; ++r) accv[r] = 0.f;
+  for (int64_t c = (int64_t)lane * V; c < n; c += 32 * V) {
+    float xv[V];
+    if (xal && c + V <= n) {
+#pragma unroll
+      for (int q = 0; q < V; q += 4) {
+        float4 t = __ldg(reinterpret_cast<const float4*>(x + c + q));
+        xv[q] = t.x; xv[q + 1] = t.y; xv[q + 2] = t.z; xv[q + 3] = t.w;
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < V; ++q) xv[q] = (c + q < n) ? __ldg(x + c + q) : 0.f;
+    }
+#pragma unroll
+    for (int r = 0; r < kGemvRows; ++r) {
+      int64_t row = row0 + r;
+      if (row < m) {
+        uint4 u = __ldg(reinterpret_cast<const uint4*>(A + row * lda + c));
+        float av[V];
+        Vec<T>::unpack(u, av);
+#pragma unroll
+        for (int q = 0; q < V; ++q) accv[r] = fmaf(av[q], xv[q], accv[r]);
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < kGemvRows; ++r) {
+    float v = accv[r];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    int64_t row = row0 + r;
+    if (lane == 0 && row < m) {
+      float out = alpha * (rs ? rs[row] * v : v);
+      y[row] = acc ? y[row] + out : out;
+    }
+  }
+}
+
+void launch_gemv_n(cudaStream_t s, cf_prec p, int64_t m, int64_t n, int64_t lda, const void* A,
+                   const float* rs, float alpha, const float* x, float* y, bool acc) {
+  if (m <= 0) return;
+  const int rows_per_cta = (256 / 32) * kGemvRows;
+  unsigned grid = (unsigned)((m + rows_per_cta - 1) / rows_per_cta);
+  if (p == CF_FP32)
+    k_gemv_n<float><<<grid, 256, 0, s>>>(m, n, lda, (const float*)A, rs, alpha, x, y, acc);
+  else if (p == CF_BF16)
+    k_gemv_n<__nv_bfloat16><<<grid, 256, 0, s>>>(m, n, lda, (const __nv_bfloat16*)A, rs, alpha, x, y, acc);
+  else
+    k_gemv_n<__nv_fp8_e4m3><<<grid, 256, 0, s>>>(m, n, lda, (const __nv_fp8_e4m3*)A, rs, alpha, x, y, acc);
+}
+
+// x^T-side: part[rb, j] = sum_{i in row block rb} A[i, j] (s_i y_i); each
+// thread owns V consecutive columns, so every row is read once with 16-byte
+// coalesced loads.  A second kernel sums the row blocks in a fixed order.
+constexpr int kGemvTThreads = 256;
+constexpr int kGemvTMaxRows = 512;
+
+template <typename T>
+__global__ void __launch_bounds__(kGemvTThreads)
+k_gemv_t_part(int64_t m, int64_t n, int64_t lda, int64_t rows_per_block, const T* __restrict__ A,
+              const float* __restrict__ rs, const float* __restrict__ yv, float* __restrict__ part) {
+  constexpr int V = Vec<T>::N;
+  __shared__ float sy[kGemvTMaxRows];
+  const int64_t r0 = (int64_t)blockIdx.y * rows_per_block;
+  const int64_t r1 = (r0 + rows_per_block < m) ? r0 + rows_per_block : m;
+  for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x)
+    sy[i - r0] = rs ? rs[i] * yv[i] : yv[i];
+  __syncthreads();
+  const int64_t c0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * V;
+  if (c0 >= n) return;
+  float accv[V];
+#pragma unroll
+  for (int q = 0; q < V; ++q) accv[q] = 0.f;
+  int64_t i = r0;
+  for (; i + 4 <= r1; i += 4) {
+    uint4 u[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) u[k] = __ldg(reinterpret_cast<const uint4*>(A + (i + k) * lda + c0));
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      float av[V];
+      Vec<T>::unpack(u[k], av);
+      const float sv = sy[i + k - r0];
+#pragma unroll
+      for (int q = 0; q < V; ++q) accv[q] = fmaf(av[q], sv, accv[q]);
+    }
+  }
+  for (; i < r1; ++i) {
+    uint4 u = __ldg(reinterpret_cast<const uint4*>(A + i * lda + c0));
+    float av[V];
+    Vec<T>::unpack(u, av);
+    const float sv = sy[i - r0];
+#pragma unroll
+    for (int q = 0; q < V; ++q) accv[q] = fmaf(av[q], sv, accv[q]);
+  }
+  float* dst = part + (int64_t)blockIdx.y * lda + c0;
+#pragma unroll
+  for (int q = 0; q < V; q += 4)
+    *reinterpret_cast<float4*>(dst + q) = make_float4(accv[q], accv[q + 1], accv[q + 2], accv[q + 3]);
+}
+
+__global__ void k_gemv_t_reduce(int64_t n, int64_t lda, int nrb, const float* __restrict__ part,
+                                float alpha, float* __restrict__ x, bool acc) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    float sum = 0.f;
+    for (int b = 0; b < nrb; ++b) sum += part[(int64_t)b * lda + j];
+    float v = alpha * sum;
+    x[j] = acc ? x[j] + v : v;
+  }
+}
+
+static int gemv_t_row_blocks(int64_t m, int64_t n) {
+  int64_t col_tiles = (n + kGemvTThreads * 4 - 1) / (kGemvTThreads * 4);
+  int64_t want = (4 * 148 + col_tiles - 1) / col_tiles;       // about 4 CTAs per SM
+  int64_t min_rb = (m + kGemvTMaxRows - 1) / kGemvTMaxRows;   // shared-memory cap
+  int64_t max_rb = std::max<int64_t>(1, m / 32);
+  int64_t rb = std::min(want, max_rb);
+  return (int)std::max<int64_t>(std::max<int64_t>(rb, min_rb), 1);
+}
+
+size_t gemv_t_ws_floats(int64_t m, int64_t n, int64_t lda) {
+  return (size_t)gemv_t_row_blocks(m, n) * (size_t)lda;
+}
+
+void launch_gemv_t(cudaStream_t s, cf_prec p, int64_t m, int64_t n, int64_t lda, const void* A,
+                   const float* rs, float alpha, const float* x, float* y, bool acc, float* ws) {
+  if (n <= 0) return;
+  if (m <= 0) {
+    if (!acc) launch_fill(s, n, 0.f, y);
+    return;
+  }
+  const int rb = gemv_t_row_blocks(m, n);
+  const int64_t rows_per_block = (m + rb - 1) / rb;
+  const int V = p == CF_FP32 ? 4 : (p == CF_BF16 ? 8 : 16);
+  dim3 grid((unsigned)((n + kGemvTThreads * V - 1) / (kGemvTThreads * V)), (unsigned)rb);
+  if (p == CF_FP32)
+    k_gemv_t_part<float><<<grid, kGemvTThreads, 0, s>>>(m, n, lda, rows_per_block, (const float*)A, rs, x, ws);
+  else if (p == CF_BF16)
+    k_gemv_t_part<__nv_bfloat16><<<grid, kGemvTThreads, 0, s>>>(m, n, lda, rows_per_block, (const __nv_bfloat16*)A, rs, x, ws);
+  else
+    k_gemv_t_part<__nv_fp8_e4m3><<<grid, kGemvTThreads, 0, s>>>(m, n, lda, rows_per_block, (const __nv_fp8_e4m3*)A, rs, x, ws);
+  k_gemv_t_reduce<<<grid_for(n, 1), kThreads, 0, s>>>(n, lda, rb, ws, alpha, y, acc);
+}
+
+// ------------------------------------------------------------ quantisation
+// One CTA per row: row max, then codes (the stored operand defines the
+// problem instance).  Columns n..lda-1 are zero padding.
+__global__ void k_quantize(cf_prec p, int64_t n, int64_t lda, const float* __restrict__ src,
+                           void* __restrict__ dst, float* __restrict__ rs) {
+  const int64_t row = blockIdx.x;
+  const float* a = src + row * n;
+  __shared__ float smax[32];
+  __shared__ float s_scale;
+  float scale = 1.f;
+  if (p == CF_FP8_E4M3) {
+    float mx = 0.f;
+    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) mx = fmaxf(mx, fabsf(a[j]));
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_down_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) smax[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float t = 0.f;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = fmaxf(t, smax[w]);
+      s_scale = t > 0.f ? t / 448.0f : 1.0f;
+      rs[row] = s_scale;
+    }
+    __syncthreads();
+    scale = s_scale;
+  }
+  for (int64_t j = threadIdx.x; j < lda; j += blockDim.x) {
+    float v = j < n ? a[j] : 0.f;
+    if (p == CF_FP32) {
+      ((float*)dst)[row * lda + j] = v;
+    } else if (p == CF_BF16) {
+      ((__nv_bfloat16*)dst)[row * lda + j] = __float2bfloat16_rn(v);
+    } else {
+      float q = v / scale;
+      ((__nv_fp8_storage_t*)dst)[row * lda + j] = __nv_cvt_float_to_fp8(q, __NV_SATFINITE, __NV_E4M3);
+    }
+  }
+}
+
+void launch_quantize(cudaStream_t s, cf_prec p, int64_t m, int64_t n, int64_t lda,
+                     const float* src, void* dst, float* rs) {
+  if (m <= 0) return;
+  k_quantize<<<(unsigned)m, 256, 0, s>>>(p, n, lda, src, dst, rs);
+}
+
+// ------------------------------------------------------------ CSR SpMV
+// One warp per row; lanes stride over the row's entries.
+template <bool BF16>
+__global__ void __launch_bounds__(256)
+k_csr(int64_t m, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+      const void* __restrict__ val, float alpha, const float* __restrict__ x,
+      float* __restrict__ y, bool acc) {
+  const int lane = threadIdx.x & 31;
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (row >= m) return;
+  const int32_t b = rowptr[row], e = rowptr[row + 1];
+  float sum = 0.f;
+  for (int32_t k = b + lane; k < e; k += 32) {
+    float v = BF16 ? __bfloat162float(((const __nv_bfloat16*)val)[k]) : ((const float*)val)[k];
+    sum = fmaf(v, __ldg(x + col[k]), sum);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
+  if (lane == 0) {
+    float out = alpha * sum;
+    y[row] = acc ? y[row] + out : out;
+  }
+}
+
+void launch_csr(cudaStream_t s, cf_prec p, int64_t m, const int32_t* rowptr, const int32_t* col,
+                const void* val, float alpha, const float* x, float* y, bool acc) {
+  if (m <= 0) return;
+  unsigned grid = (unsigned)((m + 7) / 8);
+  if (p == CF_BF16)
+    k_csr<true><<<grid, 256, 0, s>>>(m, rowptr, col, val, alpha, x, y, acc);
+  else
+    k_csr<false><<<grid, 256, 0, s>>>(m, rowptr, col, val, alpha, x, y, acc);
+}
+
+// ------------------------------------------------------------ small GEMM
+// C (M x N, row-major, ldc = N) = alpha op(A) op(B) + (acc ? C : 0) for the
+// Kronecker operator's two factor products; 16 x 16 shared-memory tiles.
+constexpr int kGT = 16;
+
+__global__ void k_gemm(int64_t M, int64_t N, int64_t K, const float* __restrict__ A, int64_t lda,
+                       bool ta, const float* __restrict__ B, int64_t ldb, bool tb, float alpha,
+                       float* __restrict__ C, bool acc) {
+  __shared__ float As[kGT][kGT + 1], Bs[kGT][kGT + 1];
+  const int64_t row = (int64_t)blockIdx.y * kGT + threadIdx.y;
+  const int64_t colj = (int64_t)blockIdx.x * kGT + threadIdx.x;
+  float sum = 0.f;
+  for (int64_t k0 = 0; k0 < K; k0 += kGT) {
+    int64_t ka = k0 + threadIdx.x, kb = k0 + threadIdx.y;
+    As[threadIdx.y][threadIdx.x] =
+        (row < M && ka < K) ? (ta ? A[ka * lda + row] : A[row * lda + ka]) : 0.f;
+    Bs[threadIdx.y][threadIdx.x] =
+        (kb < K && colj < N) ? (tb ? B[colj * ldb + kb] : B[kb * ldb + colj]) : 0.f;
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kGT; ++k) sum = fmaf(As[threadIdx.y][k], Bs[k][threadIdx.x], sum);
+    __syncthreads();
+  }
+  if (row < M && colj < N) {
+    float v = alpha * sum;
+    C[row * N + colj] = acc ? C[row * N + colj] + v : v;
+  }
+}
+
+void launch_gemm(cudaStream_t s, int64_t M, int64_t N, int64_t K, const float* A, int64_t lda,
+                 bool ta, const float* B, int64_t ldb, bool tb, float alpha, float* C, bool acc) {
+  if (M <= 0 || N <= 0) return;
+  dim3 grid((unsigned)((N + kGT - 1) / kGT), (unsigned)((M + kGT - 1) / kGT));
+  k_gemm<<<grid, dim3(kGT, kGT), 0, s>>>(M, N, K, A, lda, ta, B, ldb, tb, alpha, C, acc);
+}
+
+}  // namespace cf

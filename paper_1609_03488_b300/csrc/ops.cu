@@ -1,0 +1,560 @@
+// Operator trees: leaves own device data, compositions reference their parts
+// (Section 3.1's structured linear operators; Section 4.1's adjoint by graph
+// transformation: the adjoint of a composition is formed node by node --
+// vstack <-> hstack, products reversed -- and never materialised).
+#include <algorithm>
+#include <cstring>
+#include <memory>
+
+#include "internal.cuh"
+
+namespace cf {
+
+void op_retain(cf_op* op) { op->refs.fetch_add(1); }
+
+static void op_free(cf_op* op) {
+  for (cf_op* p : op->parts) cf_op_destroy(p);
+  void* bufs[] = {op->a, op->row_scale, op->rowptr, op->col, op->t_rowptr, op->t_col,
+                  op->val, op->t_val, op->w_fwd, op->w_adj, op->k2_fwd, op->k2_adj, op->d};
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (op->ctx) cudaSetDevice(op->ctx->device);
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  if (prev >= 0) cudaSetDevice(prev);
+  delete op;
+}
+
+size_t op_tree_bytes(const cf_op* op) {
+  size_t s = op->device_bytes;
+  for (const cf_op* p : op->parts) s += op_tree_bytes(p);
+  return s;
+}
+
+static size_t al16(size_t n) { return align_up(n, 16); }
+
+size_t op_ws_floats(const cf_op* op, bool trans) {
+  switch (op->kind) {
+    case OP_DENSE:
+      return trans ? al16(gemv_t_ws_floats(op->m, op->n, op->lda)) : 0;
+    case OP_CSR: case OP_CONV1D: case OP_CONV2D: case OP_DIAG: case OP_ZERO:
+      return 0;
+    case OP_SCALE:
+      return op_ws_floats(op->parts[0], trans);
+    case OP_ADJOINT:
+      return op_ws_floats(op->parts[0], !trans);
+    case OP_VSTACK: case OP_HSTACK: case OP_BLOCKDIAG: case OP_SUM: {
+      size_t mx = 0;
+      for (const cf_op* p : op->parts) mx = std::max(mx, op_ws_floats(p, trans));
+      return mx;
+    }
+    case OP_PRODUCT: {
+      // two ping-pong intermediates of the largest inner dimension
+      int64_t inner = 0;
+      for (size_t i = 0; i + 1 < op->parts.size(); ++i) inner = std::max(inner, op->parts[i]->n);
+      size_t mx = 0;
+      for (const cf_op* p : op->parts) mx = std::max(mx, op_ws_floats(p, trans));
+      return 2 * al16((size_t)inner) + mx;
+    }
+    case OP_KRON: {
+      const cf_op *A = op->parts[0], *B = op->parts[1];
+      return al16((size_t)std::max(A->n * B->m, A->m * B->n));
+    }
+  }
+  return 0;
+}
+
+// y = alpha * op(x) + (acc ? y : 0)
+void op_apply(const cf_op* op, bool trans, float alpha, const float* x, float* y, bool acc,
+              float* ws, cudaStream_t s) {
+  const int64_t out_dim = trans ? op->n : op->m;
+  switch (op->kind) {
+    case OP_ZERO:
+      if (!acc) launch_fill(s, out_dim, 0.f, y);
+      return;
+    case OP_DIAG:
+      launch_diag(s, op->n, op->d, alpha, x, y, acc);
+      return;
+    case OP_DENSE:
+      if (!trans)
+        launch_gemv_n(s, op->prec, op->m, op->n, op->lda, op->a, op->row_scale, alpha, x, y, acc);
+      else
+        launch_gemv_t(s, op->prec, op->m, op->n, op->lda, op->a, op->row_scale, alpha, x, y, acc, ws);
+      return;
+    case OP_CSR:
+      if (!trans)
+        launch_csr(s, op->prec, op->m, op->rowptr, op->col, op->val, alpha, x, y, acc);
+      else
+        launch_csr(s, op->prec, op->n, op->t_rowptr, op->t_col, op->t_val, alpha, x, y, acc);
+      return;
+    case OP_CONV1D: {
+      const int64_t nx = op->n, ny = op->m;
+      if (!trans)
+        launch_conv1d(s, ny, nx, op->Lp, 0, op->w_fwd, alpha, x, y, acc);
+      else
+        launch_conv1d(s, nx, ny, op->Lp, op->Lp - 1, op->w_adj, alpha, x, y, acc);
+      return;
+    }
+    case OP_CONV2D: {
+      const int64_t Ho = op->h + op->kh - 1, Wo = op->w + op->kw - 1;
+      if (!trans)
+        launch_conv2d(s, Ho, Wo, op->h, op->w, op->kh, op->kw, 0, 0, op->k2_fwd, alpha, x, y, acc);
+      else
+        launch_conv2d(s, op->h, op->w, Ho, Wo, op->kh, op->kw, op->kh - 1, op->kw - 1, op->k2_adj,
+                      alpha, x, y, acc);
+      return;
+    }
+    case OP_SCALE:
+      op_apply(op->parts[0], trans, (float)(alpha * op->alpha), x, y, acc, ws, s);
+      return;
+    case OP_ADJOINT:
+      op_apply(op->parts[0], !trans, alpha, x, y, acc, ws, s);
+      return;
+    case OP_VSTACK:
+    case OP_HSTACK: {
+      // "stacked" along the output dimension: vstack forward, hstack adjoint
+      const bool split_out = (op->kind == OP_VSTACK) != trans;
+      int64_t off = 0;
+      bool first = true;
+      for (const cf_op* p : op->parts) {
+        if (split_out) {
+          op_apply(p, trans, alpha, x, y + off, acc, ws, s);
+          off += trans ? p->n : p->m;
+        } else {
+          op_apply(p, trans, alpha, x + off, y, first ? acc : true, ws, s);
+          off += trans ? p->m : p->n;
+          first = false;
+        }
+      }
+      return;
+    }
+    case OP_BLOCKDIAG: {
+      int64_t ro = 0, co = 0;
+      for (const cf_op* p : op->parts) {
+        const int64_t din = trans ? p->m : p->n, dout = trans ? p->n : p->m;
+        op_apply(p, trans, alpha, x + ro, y + co, acc, ws, s);
+        ro += din;
+        co += dout;
+      }
+      return;
+    }
+    case OP_SUM: {
+      bool first = true;
+      for (const cf_op* p : op->parts) {
+        op_apply(p, trans, alpha, x, y, first ? acc : true, ws, s);
+        first = false;
+      }
+      return;
+    }
+    case OP_PRODUCT: {
+      // forward: apply P_k ... P_1 right to left; adjoint: P_1^T first.
+      int64_t inner = 0;
+      for (size_t i = 0; i + 1 < op->parts.size(); ++i) inner = std::max(inner, op->parts[i]->n);
+      float* buf[2] = {ws, ws + al16((size_t)inner)};
+      float* rest = ws + 2 * al16((size_t)inner);
+      const size_t k = op->parts.size();
+      const float* cur = x;
+      for (size_t step = 0; step < k; ++step) {
+        const cf_op* p = trans ? op->parts[step] : op->parts[k - 1 - step];
+        const bool last = step + 1 == k;
+        float* dst = last ? y : buf[step & 1];
+        op_apply(p, trans, last ? alpha : 1.f, cur, dst, last ? acc : false, rest, s);
+        cur = dst;
+      }
+      return;
+    }
+    case OP_KRON: {
+      // (A (x) B) vec(X) = vec(A X B^T); adjoint: vec(A^T Y B).
+      const cf_op *A = op->parts[0], *B = op->parts[1];
+      float* T = ws;
+      if (!trans) {
+        // T (nA x mB) = X (nA x nB) B^T;  Y (mA x mB) = A T
+        launch_gemm(s, A->n, B->m, B->n, x, B->n, false, (const float*)B->a, B->lda, true, 1.f, T, false);
+        launch_gemm(s, A->m, B->m, A->n, (const float*)A->a, A->lda, false, T, B->m, false, alpha, y, acc);
+      } else {
+        // T (mA x nB) = Y (mA x mB) B;  X (nA x nB) = A^T T
+        launch_gemm(s, A->m, B->n, B->m, x, B->m, false, (const float*)B->a, B->lda, false, 1.f, T, false);
+        launch_gemm(s, A->n, B->n, A->m, (const float*)A->a, A->lda, true, T, B->n, false, alpha, y, acc);
+      }
+      return;
+    }
+  }
+}
+
+}  // namespace cf
+
+using namespace cf;
+
+// ------------------------------------------------------------------ C ABI
+namespace {
+
+template <typename T>
+cf_err dev_alloc(T** p, size_t count, size_t* bytes) {
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return fail(CF_E_OOM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+  }
+  *bytes += count * sizeof(T);
+  return CF_OK;
+}
+
+struct DevGuard {
+  int prev = -1;
+  explicit DevGuard(int dev) {
+    cudaGetDevice(&prev);
+    cudaSetDevice(dev);
+  }
+  ~DevGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+cf_op* new_op(cf_ctx* ctx, OpKind k, int64_t m, int64_t n) {
+  cf_op* op = new cf_op();
+  op->ctx = ctx;
+  op->kind = k;
+  op->m = m;
+  op->n = n;
+  return op;
+}
+
+cf_err finish(cf_op* op, cf_err r, cf_op** out) {
+  if (r != CF_OK) {
+    cf_op_destroy(op);
+    return r;
+  }
+  *out = op;
+  return CF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+cf_err cf_op_dense(cf_ctx* ctx, int64_t m, int64_t n, const float* A, cf_prec storage,
+                   cf_op** out) {
+  if (!ctx || !out || !A || m <= 0 || n <= 0)
+    return fail(CF_E_INVALID, "cf_op_dense: bad arguments");
+  if (storage != CF_FP32 && storage != CF_BF16 && storage != CF_FP8_E4M3)
+    return fail(CF_E_INVALID, "cf_op_dense: unknown storage");
+  DevGuard g(ctx->device);
+  cf_op* op = new_op(ctx, OP_DENSE, m, n);
+  op->prec = storage;
+  op->lda = (int64_t)align_up((size_t)n, 16);
+  auto run = [&]() -> cf_err {
+    size_t esz = storage == CF_FP32 ? 4 : (storage == CF_BF16 ? 2 : 1);
+    CF_TRY(dev_alloc((uint8_t**)&op->a, (size_t)m * op->lda * esz, &op->device_bytes));
+    if (storage == CF_FP8_E4M3) CF_TRY(dev_alloc(&op->row_scale, (size_t)m, &op->device_bytes));
+    float* tmp = nullptr;
+    size_t dummy = 0;
+    CF_TRY(dev_alloc(&tmp, (size_t)m * n, &dummy));
+    cf_err r = copy_any(tmp, A, (size_t)m * n * sizeof(float), ctx->stream);
+    if (r == CF_OK) {
+      launch_quantize(ctx->stream, storage, m, n, op->lda, tmp, op->a, op->row_scale);
+      cudaError_t e = cudaStreamSynchronize(ctx->stream);
+      if (e == cudaSuccess) e = cudaGetLastError();
+      if (e != cudaSuccess) r = cuda_fail(e, "quantize", __FILE__, __LINE__);
+    }
+    cudaFree(tmp);
+    return r;
+  };
+  return finish(op, run(), out);
+}
+
+cf_err cf_op_csr(cf_ctx* ctx, int64_t m, int64_t n, int64_t nnz, const int32_t* rowptr,
+                 const int32_t* col, const float* val, cf_prec storage, cf_op** out) {
+  if (!ctx || !out || !rowptr || m <= 0 || n <= 0 || nnz < 0 || (nnz > 0 && (!col || !val)))
+    return fail(CF_E_INVALID, "cf_op_csr: bad arguments");
+  if (storage != CF_FP32 && storage != CF_BF16)
+    return fail(CF_E_INVALID, "cf_op_csr: storage must be CF_FP32 or CF_BF16");
+  if (nnz > INT32_MAX) return fail(CF_E_INVALID, "cf_op_csr: nnz exceeds int32");
+  DevGuard g(ctx->device);
+  // Host copies: validate, then build the transpose (CSR of A^T) by a
+  // counting sort over columns, keeping row order inside each column.
+  std::vector<int32_t> rp(m + 1), cl(nnz), trp(n + 1, 0), tcl(nnz);
+  std::vector<float> vl(nnz), tvl(nnz);
+  CF_TRY(copy_any(rp.data(), rowptr, (m + 1) * sizeof(int32_t), ctx->stream));
+  if (nnz) {
+    CF_TRY(copy_any(cl.data(), col, nnz * sizeof(int32_t), ctx->stream));
+    CF_TRY(copy_any(vl.data(), val, nnz * sizeof(float), ctx->stream));
+  }
+  if (rp[0] != 0 || rp[m] != nnz) return fail(CF_E_INVALID, "cf_op_csr: rowptr[0] != 0 or rowptr[m] != nnz");
+  for (int64_t i = 0; i < m; ++i)
+    if (rp[i + 1] < rp[i]) return fail(CF_E_INVALID, "cf_op_csr: rowptr not monotone");
+  for (int64_t k = 0; k < nnz; ++k) {
+    if (cl[k] < 0 || cl[k] >= n) return fail(CF_E_INVALID, "cf_op_csr: column index out of range");
+    trp[cl[k] + 1]++;
+  }
+  for (int64_t j = 0; j < n; ++j) trp[j + 1] += trp[j];
+  {
+    std::vector<int32_t> fill(trp.begin(), trp.end() - 1);
+    for (int64_t i = 0; i < m; ++i)
+      for (int32_t k = rp[i]; k < rp[i + 1]; ++k) {
+        int32_t pos = fill[cl[k]]++;
+        tcl[pos] = (int32_t)i;
+        tvl[pos] = vl[k];
+      }
+  }
+  cf_op* op = new_op(ctx, OP_CSR, m, n);
+  op->prec = storage;
+  op->nnz = nnz;
+  auto run = [&]() -> cf_err {
+    CF_TRY(dev_alloc(&op->rowptr, m + 1, &op->device_bytes));
+    CF_TRY(dev_alloc(&op->col, nnz, &op->device_bytes));
+    CF_TRY(dev_alloc(&op->t_rowptr, n + 1, &op->device_bytes));
+    CF_TRY(dev_alloc(&op->t_col, nnz, &op->device_bytes));
+    CF_CUDA(cudaMemcpy(op->rowptr, rp.data(), (m + 1) * 4, cudaMemcpyHostToDevice));
+    CF_CUDA(cudaMemcpy(op->t_rowptr, trp.data(), (n + 1) * 4, cudaMemcpyHostToDevice));
+    if (nnz) {
+      CF_CUDA(cudaMemcpy(op->col, cl.data(), nnz * 4, cudaMemcpyHostToDevice));
+      CF_CUDA(cudaMemcpy(op->t_col, tcl.data(), nnz * 4, cudaMemcpyHostToDevice));
+    }
+    if (storage == CF_FP32) {
+      CF_TRY(dev_alloc((float**)&op->val, nnz, &op->device_bytes));
+      CF_TRY(dev_alloc((float**)&op->t_val, nnz, &op->device_bytes));
+      if (nnz) {
+        CF_CUDA(cudaMemcpy(op->val, vl.data(), nnz * 4, cudaMemcpyHostToDevice));
+        CF_CUDA(cudaMemcpy(op->t_val, tvl.data(), nnz * 4, cudaMemcpyHostToDevice));
+      }
+    } else {
+      CF_TRY(dev_alloc((__nv_bfloat16**)&op->val, nnz, &op->device_bytes));
+      CF_TRY(dev_alloc((__nv_bfloat16**)&op->t_val, nnz, &op->device_bytes));
+      std::vector<__nv_bfloat16> b1(nnz), b2(nnz);
+      for (int64_t k = 0; k < nnz; ++k) {
+        b1[k] = __float2bfloat16_rn(vl[k]);
+        b2[k] = __float2bfloat16_rn(tvl[k]);
+      }
+      if (nnz) {
+        CF_CUDA(cudaMemcpy(op->val, b1.data(), nnz * 2, cudaMemcpyHostToDevice));
+        CF_CUDA(cudaMemcpy(op->t_val, b2.data(), nnz * 2, cudaMemcpyHostToDevice));
+      }
+    }
+    return CF_OK;
+  };
+  return finish(op, run(), out);
+}
+
+cf_err cf_op_conv1d(cf_ctx* ctx, int64_t n, const float* kernel, int64_t L, cf_op** out) {
+  if (!ctx || !out || !kernel || n <= 0 || L <= 0)
+    return fail(CF_E_INVALID, "cf_op_conv1d: bad arguments");
+  DevGuard g(ctx->device);
+  std::vector<float> k(L);
+  CF_TRY(copy_any(k.data(), kernel, L * sizeof(float), ctx->stream));
+  cf_op* op = new_op(ctx, OP_CONV1D, n + L - 1, n);
+  op->L = L;
+  op->Lp = (int64_t)align_up((size_t)L, 8);
+  // forward taps w = k padded with zeros to Lp; stored reversed.
+  // adjoint taps w' = k reversed (w'[l] = k[L-1-l]); padding zeros at the end
+  // shift nothing because the adjoint kernel is called with shift Lp - 1.
+  std::vector<float> wf(op->Lp, 0.f), wa(op->Lp, 0.f);
+  for (int64_t l = 0; l < L; ++l) wf[op->Lp - 1 - l] = k[l];
+  // adjoint: out[j] = sum_l k[l] y[j + l] = sum_{l'} w'[l'] y[j + (Lp-1) - l']
+  // with w'[l'] = k[Lp-1-l'] (zero where Lp-1-l' >= L); reversed storage:
+  // wrev'[i] = w'[Lp-1-i] = k[i].
+  for (int64_t l = 0; l < L; ++l) wa[l] = k[l];
+  auto run = [&]() -> cf_err {
+    CF_TRY(dev_alloc(&op->w_fwd, op->Lp, &op->device_bytes));
+    CF_TRY(dev_alloc(&op->w_adj, op->Lp, &op->device_bytes));
+    CF_CUDA(cudaMemcpy(op->w_fwd, wf.data(), op->Lp * 4, cudaMemcpyHostToDevice));
+    CF_CUDA(cudaMemcpy(op->w_adj, wa.data(), op->Lp * 4, cudaMemcpyHostToDevice));
+    return CF_OK;
+  };
+  return finish(op, run(), out);
+}
+
+cf_err cf_op_conv2d(cf_ctx* ctx, int64_t h, int64_t w, const float* kernel, int64_t kh,
+                    int64_t kw, cf_op** out) {
+  if (!ctx || !out || !kernel || h <= 0 || w <= 0 || kh <= 0 || kw <= 0)
+    return fail(CF_E_INVALID, "cf_op_conv2d: bad arguments");
+  if (kh > 64 || kw > 64) return fail(CF_E_INVALID, "cf_op_conv2d: kernel larger than 64 x 64");
+  DevGuard g(ctx->device);
+  std::vector<float> k(kh * kw), kr(kh * kw);
+  CF_TRY(copy_any(k.data(), kernel, kh * kw * sizeof(float), ctx->stream));
+  for (int64_t p = 0; p < kh; ++p)
+    for (int64_t q = 0; q < kw; ++q) kr[p * kw + q] = k[(kh - 1 - p) * kw + (kw - 1 - q)];
+  cf_op* op = new_op(ctx, OP_CONV2D, (h + kh - 1) * (w + kw - 1), h * w);
+  op->h = h; op->w = w; op->kh = kh; op->kw = kw;
+  auto run = [&]() -> cf_err {
+    CF_TRY(dev_alloc(&op->k2_fwd, kh * kw, &op->device_bytes));
+    CF_TRY(dev_alloc(&op->k2_adj, kh * kw, &op->device_bytes));
+    CF_CUDA(cudaMemcpy(op->k2_fwd, k.data(), kh * kw * 4, cudaMemcpyHostToDevice));
+    CF_CUDA(cudaMemcpy(op->k2_adj, kr.data(), kh * kw * 4, cudaMemcpyHostToDevice));
+    return CF_OK;
+  };
+  return finish(op, run(), out);
+}
+
+cf_err cf_op_diag(cf_ctx* ctx, int64_t n, const float* d, cf_op** out) {
+  if (!ctx || !out || n <= 0) return fail(CF_E_INVALID, "cf_op_diag: bad arguments");
+  DevGuard g(ctx->device);
+  cf_op* op = new_op(ctx, OP_DIAG, n, n);
+  auto run = [&]() -> cf_err {
+    if (d) {
+      CF_TRY(dev_alloc(&op->d, n, &op->device_bytes));
+      CF_TRY(copy_any(op->d, d, n * sizeof(float), ctx->stream));
+    }
+    return CF_OK;
+  };
+  return finish(op, run(), out);
+}
+
+cf_err cf_op_zero(cf_ctx* ctx, int64_t m, int64_t n, cf_op** out) {
+  if (!ctx || !out || m <= 0 || n <= 0) return fail(CF_E_INVALID, "cf_op_zero: bad arguments");
+  *out = new_op(ctx, OP_ZERO, m, n);
+  return CF_OK;
+}
+
+cf_err operator_compose(cf_ctx* ctx, cf_compose_kind kind, cf_op* const* parts, int32_t k,
+                        double alpha, cf_op** out) {
+  if (!ctx || !out || !parts || k < 1) return fail(CF_E_INVALID, "operator_compose: bad arguments");
+  for (int32_t i = 0; i < k; ++i)
+    if (!parts[i]) return fail(CF_E_INVALID, "operator_compose: NULL part");
+  int64_t m = 0, n = 0;
+  OpKind ok;
+  switch (kind) {
+    case CF_VSTACK:
+      ok = OP_VSTACK;
+      n = parts[0]->n;
+      for (int32_t i = 0; i < k; ++i) {
+        if (parts[i]->n != n) return fail(CF_E_INVALID, "vstack: parts differ in column count");
+        m += parts[i]->m;
+      }
+      break;
+    case CF_HSTACK:
+      ok = OP_HSTACK;
+      m = parts[0]->m;
+      for (int32_t i = 0; i < k; ++i) {
+        if (parts[i]->m != m) return fail(CF_E_INVALID, "hstack: parts differ in row count");
+        n += parts[i]->n;
+      }
+      break;
+    case CF_BLOCKDIAG:
+      ok = OP_BLOCKDIAG;
+      for (int32_t i = 0; i < k; ++i) {
+        m += parts[i]->m;
+        n += parts[i]->n;
+      }
+      break;
+    case CF_PRODUCT:
+      ok = OP_PRODUCT;
+      for (int32_t i = 0; i + 1 < k; ++i)
+        if (parts[i]->n != parts[i + 1]->m) return fail(CF_E_INVALID, "product: inner dimensions differ");
+      m = parts[0]->m;
+      n = parts[k - 1]->n;
+      break;
+    case CF_SUM:
+      ok = OP_SUM;
+      m = parts[0]->m;
+      n = parts[0]->n;
+      for (int32_t i = 0; i < k; ++i)
+        if (parts[i]->m != m || parts[i]->n != n) return fail(CF_E_INVALID, "sum: shapes differ");
+      break;
+    case CF_SCALE:
+      if (k != 1) return fail(CF_E_INVALID, "scale takes one part");
+      ok = OP_SCALE;
+      m = parts[0]->m;
+      n = parts[0]->n;
+      break;
+    case CF_ADJOINT:
+      if (k != 1) return fail(CF_E_INVALID, "adjoint takes one part");
+      ok = OP_ADJOINT;
+      m = parts[0]->n;
+      n = parts[0]->m;
+      break;
+    case CF_KRON:
+      if (k != 2) return fail(CF_E_INVALID, "kron takes two parts");
+      for (int32_t i = 0; i < 2; ++i)
+        if (parts[i]->kind != OP_DENSE || parts[i]->prec != CF_FP32)
+          return fail(CF_E_INVALID, "kron: both parts must be dense FP32 leaves");
+      ok = OP_KRON;
+      m = parts[0]->m * parts[1]->m;
+      n = parts[0]->n * parts[1]->n;
+      break;
+    default:
+      return fail(CF_E_INVALID, "operator_compose: unknown kind");
+  }
+  cf_op* op = new_op(ctx, ok, m, n);
+  op->alpha = alpha;
+  for (int32_t i = 0; i < k; ++i) {
+    op_retain(parts[i]);
+    op->parts.push_back(parts[i]);
+  }
+  *out = op;
+  return CF_OK;
+}
+
+void cf_op_destroy(cf_op* op) {
+  if (!op) return;
+  if (op->refs.fetch_sub(1) == 1) op_free(op);
+}
+
+cf_err cf_op_shape(const cf_op* op, int64_t* m, int64_t* n) {
+  if (!op) return fail(CF_E_INVALID, "cf_op_shape: NULL operator");
+  if (m) *m = op->m;
+  if (n) *n = op->n;
+  return CF_OK;
+}
+
+cf_err cf_op_apply(cf_op* op, int32_t adjoint, const float* x, float* y) {
+  if (!op || !x || !y) return fail(CF_E_INVALID, "cf_op_apply: bad arguments");
+  cf_ctx* ctx = op->ctx;
+  DevGuard g(ctx->device);
+  const bool tr = adjoint != 0;
+  const int64_t din = tr ? op->m : op->n, dout = tr ? op->n : op->m;
+  size_t wsf = op_ws_floats(op, tr);
+  float *dx = nullptr, *dy = nullptr, *ws = nullptr;
+  size_t dummy = 0;
+  auto run = [&]() -> cf_err {
+    CF_TRY(dev_alloc(&dx, (size_t)din, &dummy));
+    CF_TRY(dev_alloc(&dy, (size_t)dout, &dummy));
+    CF_TRY(dev_alloc(&ws, wsf, &dummy));
+    CF_TRY(copy_any(dx, x, din * sizeof(float), ctx->stream));
+    op_apply(op, tr, 1.f, dx, dy, false, ws, ctx->stream);
+    CF_CUDA(cudaGetLastError());
+    CF_TRY(copy_any(y, dy, dout * sizeof(float), ctx->stream));
+    CF_CUDA(cudaStreamSynchronize(ctx->stream));
+    return CF_OK;
+  };
+  cf_err r = run();
+  cudaFree(dx);
+  cudaFree(dy);
+  cudaFree(ws);
+  return r;
+}
+
+cf_err cf_op_workspace_bytes(const cf_op* op, int32_t adjoint, size_t* bytes) {
+  if (!op || !bytes) return fail(CF_E_INVALID, "cf_op_workspace_bytes: bad arguments");
+  *bytes = op_ws_floats(op, adjoint != 0) * sizeof(float);
+  return CF_OK;
+}
+
+cf_err cf_op_apply_async(cf_op* op, int32_t adjoint, float alpha, const float* x, float* y,
+                         int32_t accumulate, void* workspace, void* stream) {
+  if (!op || !x || !y) return fail(CF_E_INVALID, "cf_op_apply_async: bad arguments");
+  const bool tr = adjoint != 0;
+  if (op_ws_floats(op, tr) > 0 && !workspace)
+    return fail(CF_E_INVALID, "cf_op_apply_async: workspace required");
+  if (!is_device_ptr(x) || !is_device_ptr(y) || (workspace && !is_device_ptr(workspace)))
+    return fail(CF_E_INVALID, "cf_op_apply_async: x, y and workspace must be device memory");
+  DevGuard g(op->ctx->device);
+  cudaStream_t s = stream ? (cudaStream_t)stream : op->ctx->stream;
+  op_apply(op, tr, alpha, x, y, accumulate != 0, (float*)workspace, s);
+  CF_CUDA(cudaGetLastError());
+  return CF_OK;
+}
+
+cf_err cf_op_dense_stored(const cf_op* op, void* codes, float* row_scale) {
+  if (!op || op->kind != OP_DENSE || !codes) return fail(CF_E_INVALID, "cf_op_dense_stored: not a dense leaf");
+  DevGuard g(op->ctx->device);
+  const size_t esz = op->prec == CF_FP32 ? 4 : (op->prec == CF_BF16 ? 2 : 1);
+  // strip the row padding
+  CF_CUDA(cudaMemcpy2D(codes, op->n * esz, op->a, op->lda * esz, op->n * esz, op->m, cudaMemcpyDefault));
+  if (op->prec == CF_FP8_E4M3 && row_scale)
+    CF_CUDA(cudaMemcpy(row_scale, op->row_scale, op->m * sizeof(float), cudaMemcpyDefault));
+  return CF_OK;
+}
+
+}  // extern "C"

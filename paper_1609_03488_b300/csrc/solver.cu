@@ -1,0 +1,1170 @@
+// The SCS iteration (Section 5.2, following the published SCS method the
+// paper cites) on one GPU.
+//
+// One ADMM iteration on the homogeneous self-dual embedding, u = (x, y, tau),
+// v = (r, s, kappa), relaxation alpha:
+//   w        = u + v
+//   z_x      : CG on (I + A^T A) z_x = w_x - A^T w_y, warm-started (Section 4.2)
+//   z_y      = w_y + A z_x
+//   u~_tau   = (w_tau + c^T z_x + b^T z_y) / (1 + h^T g),  u~_xy = z - u~_tau g
+//   u_hat    = alpha u~ + (1 - alpha) u
+//   u+       = Pi_C(u_hat - v),   v+ = v - u_hat + u+      (C = R^n x K* x R_+)
+// with g = M^{-1} h computed once by CG at setup.  The r block of v is zero
+// at every iterate (x is free) and is not stored.
+//
+// The whole solve is one CUDA graph: a device-side WHILE node runs ADMM
+// iterations, a nested WHILE node runs CG steps with the stopping test
+// evaluated on the device, and an IF node runs the residual check every
+// check_interval iterations; the host sees the GPU once per solve.  Every loop
+// is bounded by a counter that a single thread advances (max_iters ADMM
+// iterations, cg cap CG steps), independent of the reductions.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <memory>
+
+#include "solver.cuh"
+
+namespace cf {
+
+int64_t now_ns() {
+  return std::chrono::duration_cast<std::chrono::nanoseconds>(
+             std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
+
+constexpr int kSocChunk = 2048;  // rows of a second-order cone per CTA
+
+// ------------------------------------------------------------ reductions
+// Sum NV doubles over the block; thread 0 receives the totals.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV]) {
+  __shared__ double sh[NV][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int j = 0; j < NV; ++j) {
+    double t = v[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    v[j] = t;
+  }
+  __syncthreads();
+  if (lane == 0) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) sh[j][wid] = v[j];
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+      double t = lane < nw ? sh[j][lane] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+      v[j] = t;
+    }
+  }
+}
+
+// Grid-wide deterministic sum: every block stores its partials; the last
+// block to finish (atomic ticket) adds them in block order.  Returns true in
+// the last block, where thread 0 holds the totals.  No block waits on another.
+template <int NV>
+__device__ bool grid_sum(double (&v)[NV], double* part, unsigned int* counter) {
+  block_sum<NV>(v);
+  __shared__ int s_last;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) part[blockIdx.x * NV + j] = v[j];
+    __threadfence();
+    unsigned int prev = atomicAdd(counter, 1u);
+    s_last = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!s_last) return false;
+  __threadfence();
+  double t[NV];
+#pragma unroll
+  for (int j = 0; j < NV; ++j) t[j] = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+#pragma unroll
+    for (int j = 0; j < NV; ++j) t[j] += __ldcg(part + b * NV + j);
+  block_sum<NV>(t);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) v[j] = t[j];
+    *counter = 0u;
+  }
+  return true;
+}
+
+#define GRID_STRIDE(i, n) \
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
+
+// ------------------------------------------------------------ iteration start
+__global__ void k_init(Ctl* c, int64_t n, int64_t m, float* ux, float* uy, float* vs, float* zx,
+                       const double* warm) {
+  const bool w = c->st.warm != 0;
+  const int64_t N = n + m + 1;
+  GRID_STRIDE(i, n) {
+    ux[i] = w ? (float)warm[i] : 0.f;
+    zx[i] = 0.f;
+  }
+  GRID_STRIDE(i, m) {
+    uy[i] = w ? (float)warm[n + i] : 0.f;
+    vs[i] = w ? (float)warm[N + n + i] : 0.f;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    c->tau = w ? warm[n + m] : 1.0;
+    c->kappa = w ? warm[N + n + m] : 1.0;
+    c->k = 0;
+    c->cg_total = 0;
+    c->checks = 0;
+    c->status = CF_MAX_ITERS;
+    c->stop = 0;
+    c->lam = 1.0;
+    c->pri = c->dual = c->gap = INFINITY;
+    c->cx = c->by = 0.0;
+  }
+}
+
+// w_y = u_y + v_s, rhs = u_x (then rhs -= A^T w_y by the operator walk)
+__global__ void k_rhs(Ctl* c, int64_t n, int64_t m, const float* __restrict__ ux,
+                      const float* __restrict__ uy, const float* __restrict__ vs,
+                      float* __restrict__ wy, float* __restrict__ rhs) {
+  GRID_STRIDE(i, m) wy[i] = uy[i] + vs[i];
+  GRID_STRIDE(i, n) rhs[i] = ux[i];
+  if (blockIdx.x == 0 && threadIdx.x == 0) c->w_tau = c->tau + c->kappa;
+}
+
+// ------------------------------------------------------------ CG (Section 4.2)
+// r = rhs - (lam z + q) with q = A^T A z; p = r; stopping threshold.
+__global__ void k_cg_init(Ctl* c, int64_t n, const float* __restrict__ rhs,
+                          const float* __restrict__ z, const float* __restrict__ q,
+                          float* __restrict__ r, float* __restrict__ p, double* part, int mode,
+                          cudaGraphConditionalHandle h) {
+  const float lam = (float)c->lam;
+  double v[2] = {0.0, 0.0};
+  GRID_STRIDE(i, n) {
+    float ri = rhs[i] - (lam * z[i] + q[i]);
+    r[i] = ri;
+    p[i] = ri;
+    v[0] += (double)ri * ri;
+    v[1] += (double)rhs[i] * rhs[i];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) c->cg_guard = 0;
+  if (grid_sum<2>(v, part, &c->red_count) && threadIdx.x == 0) {
+    const double rr = v[0], nrhs = sqrt(v[1]);
+    double tol;
+    int cap, fixed;
+    if (mode == CG_SETUP) {
+      tol = c->st.setup_tol * nrhs;
+      cap = c->st.setup_cg_max;
+      fixed = 0;
+    } else {
+      tol = c->st.cg_tol_rel * nrhs * pow((double)c->k + 1.0, -c->st.cg_tol_exp);
+      tol = fmax(tol, c->st.cg_tol_min);
+      cap = c->st.cg_max;
+      fixed = c->st.cg_fixed;
+    }
+    c->rr = rr;
+    c->tol2 = tol * tol;
+    c->cg_it = 0;
+    const int cont = fixed > 0 ? 1 : ((rr > c->tol2 && cap > 0) ? 1 : 0);
+    c->cg_cont = cont;
+    cudaGraphSetConditional(h, (unsigned)cont);
+  }
+}
+
+// q += lam p (q held A^T A p); alpha = rr / p^T q
+__global__ void k_cg_dot(Ctl* c, int64_t n, const float* __restrict__ p, float* __restrict__ q,
+                         double* part) {
+  const float lam = (float)c->lam;
+  double v[1] = {0.0};
+  GRID_STRIDE(i, n) {
+    float qi = q[i] + lam * p[i];
+    q[i] = qi;
+    v[0] += (double)p[i] * qi;
+  }
+  if (grid_sum<1>(v, part, &c->red_count) && threadIdx.x == 0) {
+    const double pq = v[0];
+    c->alpha_cg = pq > 0.0 ? c->rr / pq : 0.0;
+  }
+}
+
+// z += alpha p; r -= alpha q; beta = ||r_new||^2 / ||r||^2; continue test
+__global__ void k_cg_update(Ctl* c, int64_t n, float* __restrict__ z, float* __restrict__ r,
+                            const float* __restrict__ p, const float* __restrict__ q, double* part,
+                            int mode) {
+  const float a = (float)c->alpha_cg;
+  double v[1] = {0.0};
+  GRID_STRIDE(i, n) {
+    z[i] = fmaf(a, p[i], z[i]);
+    float ri = fmaf(-a, q[i], r[i]);
+    r[i] = ri;
+    v[0] += (double)ri * ri;
+  }
+  if (grid_sum<1>(v, part, &c->red_count) && threadIdx.x == 0) {
+    const double rr_new = v[0];
+    c->beta_cg = c->rr > 0.0 ? rr_new / c->rr : 0.0;
+    c->rr = rr_new;
+    c->cg_it += 1;
+    int cap, fixed;
+    if (mode == CG_SETUP) {
+      c->setup_iters += 1;
+      cap = c->st.setup_cg_max;
+      fixed = 0;
+    } else {
+      c->cg_total += 1;
+      cap = c->st.cg_max;
+      fixed = c->st.cg_fixed;
+    }
+    c->cg_cont = fixed > 0 ? (c->cg_it < fixed) : (rr_new > c->tol2 && c->cg_it < cap);
+  }
+}
+
+// p = r + beta p; decide whether the CG loop runs again.  The guard counter
+// is advanced here by one thread, so the loop ends after at most `cap` steps
+// whatever the reductions produced.
+__global__ void k_cg_p(Ctl* c, int64_t n, const float* __restrict__ r, float* __restrict__ p,
+                       int mode, cudaGraphConditionalHandle h) {
+  const float b = (float)c->beta_cg;
+  GRID_STRIDE(i, n) p[i] = fmaf(b, p[i], r[i]);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const int g = ++c->cg_guard;
+    int cap = mode == CG_SETUP ? c->st.setup_cg_max : (c->st.cg_fixed > 0 ? c->st.cg_fixed : c->st.cg_max);
+    const int cont = (c->cg_cont && g < cap) ? 1 : 0;
+    cudaGraphSetConditional(h, (unsigned)cont);
+  }
+}
+
+// ------------------------------------------------------------ subspace step
+// z_y += w_y (z_y held A z_x); u~_tau = (w_tau + c^T z_x + b^T z_y) / (1 + h^T g)
+__global__ void k_utau(Ctl* c, int64_t n, int64_t m, const float* __restrict__ zx,
+                       float* __restrict__ zy, const float* __restrict__ wy,
+                       const float* __restrict__ bf, const float* __restrict__ cf, double* part) {
+  double v[1] = {0.0};
+  GRID_STRIDE(i, m) {
+    float zi = zy[i] + wy[i];
+    zy[i] = zi;
+    v[0] += (double)bf[i] * zi;
+  }
+  GRID_STRIDE(i, n) v[0] += (double)cf[i] * zx[i];
+  if (grid_sum<1>(v, part, &c->red_count) && threadIdx.x == 0)
+    c->ut_tau = (c->w_tau + v[0]) / (1.0 + c->hg);
+}
+
+// The point projected onto K* for row i of y:
+//   p_i = (alpha (z_y - u~_tau g_y) + (1 - alpha) u_y) - v_s
+// evaluated with explicit roundings so both kernels that need it agree bit
+// for bit.
+__device__ __forceinline__ float y_pre(float a, float a1, float ut, float zy, float gy, float uy,
+                                       float vs) {
+  float uhat = __fadd_rn(__fmul_rn(a, __fsub_rn(zy, __fmul_rn(ut, gy))), __fmul_rn(a1, uy));
+  return __fsub_rn(uhat, vs);
+}
+
+// Per-chunk squared norm of the tail of each second-order cone block of the
+// pre-projection point; the chunk holding a block's head row stores p_head.
+__global__ void k_soc_norm(const Ctl* c, int64_t m_off, const int32_t* __restrict__ chunk_seg,
+                           const int64_t* __restrict__ chunk_r0, const int64_t* __restrict__ chunk_r1,
+                           const int64_t* __restrict__ seg_head, const float* __restrict__ zy,
+                           const float* __restrict__ gy, const float* __restrict__ uy,
+                           const float* __restrict__ vs, double* __restrict__ chunk_n2,
+                           double* __restrict__ seg_p0) {
+  (void)m_off;
+  const int64_t ch = blockIdx.x;
+  const int32_t sg = chunk_seg[ch];
+  const int64_t head = seg_head[sg];
+  const int64_t r0 = chunk_r0[ch], r1 = chunk_r1[ch];
+  const float a = (float)c->st.alpha, a1 = (float)(1.0 - c->st.alpha), ut = (float)c->ut_tau;
+  double v[1] = {0.0};
+  for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+    float pi = y_pre(a, a1, ut, zy[i], gy[i], uy[i], vs[i]);
+    if (i == head)
+      seg_p0[sg] = (double)pi;
+    else
+      v[0] += (double)pi * pi;
+  }
+  block_sum<1>(v);
+  if (threadIdx.x == 0) chunk_n2[ch] = v[0];
+}
+
+// Projection and dual update.  Blocks [0, nlin) cover x (free) and the zero
+// and nonnegative rows of y elementwise; blocks [nlin, nlin + nchunk) cover
+// the second-order cone chunks.  Thread 0 of block 0 updates tau, kappa and
+// the iteration counter and decides whether this iteration ends with a
+// residual check.
+__global__ void k_apply(Ctl* c, int64_t n, int64_t m, int64_t z, int64_t l, int nlin,
+                        float* __restrict__ ux, float* __restrict__ uy, float* __restrict__ vs,
+                        const float* __restrict__ zx, const float* __restrict__ zy,
+                        const float* __restrict__ gx, const float* __restrict__ gy,
+                        const int32_t* __restrict__ chunk_seg, const int64_t* __restrict__ chunk_r0,
+                        const int64_t* __restrict__ chunk_r1, const int64_t* __restrict__ seg_head,
+                        const int32_t* __restrict__ seg_c0, const int32_t* __restrict__ seg_nc,
+                        const double* __restrict__ chunk_n2, const double* __restrict__ seg_p0,
+                        cudaGraphConditionalHandle h_check) {
+  const double al = c->st.alpha;
+  const float a = (float)al, a1 = (float)(1.0 - al), ut = (float)c->ut_tau;
+  if ((int)blockIdx.x < nlin) {
+    const int64_t nl = n + z + l;
+    const int64_t stride = (int64_t)nlin * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nl; i += stride) {
+      if (i < n) {
+        ux[i] = __fadd_rn(__fmul_rn(a, __fsub_rn(zx[i], __fmul_rn(ut, gx[i]))), __fmul_rn(a1, ux[i]));
+      } else {
+        const int64_t j = i - n;
+        float pj = y_pre(a, a1, ut, zy[j], gy[j], uy[j], vs[j]);
+        float uj = j < z ? pj : fmaxf(pj, 0.f);
+        uy[j] = uj;
+        vs[j] = __fsub_rn(uj, pj);
+      }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      const double uhat = al * c->ut_tau + (1.0 - al) * c->tau;
+      const double pt = uhat - c->kappa;
+      const double tn = pt > 0.0 ? pt : 0.0;
+      c->tau = tn;
+      c->kappa = tn - pt;
+      const int k = c->k + 1;
+      c->k = k;
+      const int chk = (k % c->st.check_interval == 0) || (k >= c->st.max_iters);
+      cudaGraphSetConditional(h_check, (unsigned)chk);
+    }
+    return;
+  }
+  // second-order cone chunk
+  const int64_t ch = blockIdx.x - nlin;
+  const int32_t sg = chunk_seg[ch];
+  const int64_t head = seg_head[sg];
+  __shared__ double s_nrm;
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    const int32_t c0 = seg_c0[sg], nc = seg_nc[sg];
+    for (int32_t k = 0; k < nc; ++k) s += chunk_n2[c0 + k];
+    s_nrm = sqrt(s);
+  }
+  __syncthreads();
+  const double nrm = s_nrm, p0 = seg_p0[sg];
+  // 0: keep, 1: zero, 2: scale onto the boundary
+  const int mode = nrm <= p0 ? 0 : (nrm <= -p0 ? 1 : 2);
+  const double ah = 0.5 * (p0 + nrm);
+  const float head_val = (float)ah;
+  const float scl = mode == 2 ? (float)(ah / nrm) : 0.f;
+  const int64_t r0 = chunk_r0[ch], r1 = chunk_r1[ch];
+  for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+    float pi = y_pre(a, a1, ut, zy[i], gy[i], uy[i], vs[i]);
+    float ui;
+    if (mode == 0)
+      ui = pi;
+    else if (mode == 1)
+      ui = 0.f;
+    else
+      ui = (i == head) ? head_val : __fmul_rn(scl, pi);
+    uy[i] = ui;
+    vs[i] = __fsub_rn(ui, pi);
+  }
+}
+
+// ------------------------------------------------------------ termination
+// With cm = A u_x and cn = A^T u_y:
+//   S0 = ||cm + v_s - b tau||^2   S1 = ||cm + v_s||^2   S2 = b^T u_y
+//   S3 = ||cn + c tau||^2         S4 = ||cn||^2         S5 = c^T u_x
+// x = u_x / tau, y = u_y / tau, s = v_s / tau give
+//   pri = sqrt(S0)/tau/(1+||b||), dual = sqrt(S3)/tau/(1+||c||),
+//   gap = |S5 + S2|/tau / (1 + |S5|/tau + |S2|/tau).
+__global__ void k_resid(Ctl* c, int64_t n, int64_t m, const float* __restrict__ cm,
+                        const float* __restrict__ cn, const float* __restrict__ ux,
+                        const float* __restrict__ uy, const float* __restrict__ vs,
+                        const float* __restrict__ bf, const float* __restrict__ cf, double* part) {
+  const double tau = c->tau;
+  double v[6] = {0, 0, 0, 0, 0, 0};
+  GRID_STRIDE(i, m) {
+    double e = (double)cm[i] + (double)vs[i];
+    double d = e - (double)bf[i] * tau;
+    v[0] += d * d;
+    v[1] += e * e;
+    v[2] += (double)bf[i] * uy[i];
+  }
+  GRID_STRIDE(i, n) {
+    double d = (double)cn[i] + (double)cf[i] * tau;
+    v[3] += d * d;
+    v[4] += (double)cn[i] * cn[i];
+    v[5] += (double)cf[i] * ux[i];
+  }
+  if (grid_sum<6>(v, part, &c->red_count) && threadIdx.x == 0) {
+    c->checks += 1;
+    c->cx = v[5];
+    c->by = v[2];
+    bool bad = false;
+    for (int j = 0; j < 6; ++j) bad |= !isfinite(v[j]);
+    if (bad || !isfinite(tau) || !isfinite(c->kappa)) {
+      c->status = CF_NUMERICAL;
+      c->stop = 1;
+      return;
+    }
+    if (tau > 0.0) {
+      const double pri = sqrt(v[0]) / tau / (1.0 + c->nb);
+      const double dual = sqrt(v[3]) / tau / (1.0 + c->nc);
+      const double cx = v[5] / tau, by = v[2] / tau;
+      const double gap = fabs(cx + by) / (1.0 + fabs(cx) + fabs(by));
+      c->pri = pri;
+      c->dual = dual;
+      c->gap = gap;
+      if (pri <= c->st.eps && dual <= c->st.eps && gap <= c->st.eps) {
+        c->status = CF_SOLVED;
+        c->stop = 1;
+        return;
+      }
+    }
+    if (-v[2] > 0.0 && sqrt(v[4]) <= c->st.eps_inf * (-v[2])) {
+      c->status = CF_INFEASIBLE;
+      c->stop = 1;
+    } else if (-v[5] > 0.0 && sqrt(v[1]) <= c->st.eps_inf * (-v[5])) {
+      c->status = CF_UNBOUNDED;
+      c->stop = 1;
+    }
+  }
+}
+
+__global__ void k_outer(Ctl* c, cudaGraphConditionalHandle h) {
+  int cont = 1;
+  if (!isfinite(c->tau) || !isfinite(c->kappa)) {
+    c->status = CF_NUMERICAL;
+    c->stop = 1;
+  }
+  if (c->stop || c->k >= c->st.max_iters) cont = 0;
+  cudaGraphSetConditional(h, (unsigned)cont);
+}
+
+// ------------------------------------------------------------ setup kernels
+__global__ void k_setup_init(Ctl* c, int64_t n, float* gx, float* rhs, const float* cf) {
+  GRID_STRIDE(i, n) {
+    gx[i] = 0.f;
+    rhs[i] = cf[i];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    c->lam = 1.0;
+    c->setup_iters = 0;
+    c->k = 0;
+  }
+}
+
+// g_y += b (g_y held A g_x); h^T g = c^T g_x + b^T g_y
+__global__ void k_setup_fin(Ctl* c, int64_t n, int64_t m, const float* __restrict__ gx,
+                            float* __restrict__ gy, const float* __restrict__ bf,
+                            const float* __restrict__ cf, double* part) {
+  double v[1] = {0.0};
+  GRID_STRIDE(i, m) {
+    float gi = gy[i] + bf[i];
+    gy[i] = gi;
+    v[0] += (double)bf[i] * gi;
+  }
+  GRID_STRIDE(i, n) v[0] += (double)cf[i] * gx[i];
+  if (grid_sum<1>(v, part, &c->red_count) && threadIdx.x == 0) c->hg = v[0];
+}
+
+// ------------------------------------------------------------ outputs
+__global__ void k_output(const Ctl* c, int64_t n, int64_t m, const float* __restrict__ ux,
+                         const float* __restrict__ uy, const float* __restrict__ vs,
+                         double* __restrict__ out) {
+  const int st = c->status;
+  const double tau = c->tau;
+  double sx, sy, ss;  // multipliers for x, y, s
+  if (st == CF_INFEASIBLE) {
+    sx = NAN; ss = NAN; sy = 1.0 / (-c->by);
+  } else if (st == CF_UNBOUNDED) {
+    sx = 1.0 / (-c->cx); ss = sx; sy = NAN;
+  } else if (tau > 0.0) {
+    sx = sy = ss = 1.0 / tau;
+  } else {
+    sx = sy = ss = NAN;
+  }
+  GRID_STRIDE(i, n) out[i] = (double)ux[i] * sx;
+  GRID_STRIDE(i, m) {
+    out[n + i] = (double)uy[i] * sy;
+    out[n + m + i] = (double)vs[i] * ss;
+  }
+}
+
+__global__ void k_export_uv(const Ctl* c, int64_t n, int64_t m, const float* __restrict__ ux,
+                            const float* __restrict__ uy, const float* __restrict__ vs,
+                            double* __restrict__ uv) {
+  const int64_t N = n + m + 1;
+  GRID_STRIDE(i, n) {
+    uv[i] = ux[i];
+    uv[N + i] = 0.0;
+  }
+  GRID_STRIDE(i, m) {
+    uv[n + i] = uy[i];
+    uv[N + n + i] = vs[i];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    uv[n + m] = c->tau;
+    uv[N + n + m] = c->kappa;
+  }
+}
+
+// ------------------------------------------------------------ graph building
+namespace {
+
+struct Seg {
+  cudaStream_t s;
+  std::vector<cudaGraphNode_t> tail;
+};
+
+cf_err seg_begin(cudaStream_t s, cudaGraph_t g, const std::vector<cudaGraphNode_t>& deps) {
+  CF_CUDA(cudaStreamBeginCaptureToGraph(s, g, deps.empty() ? nullptr : deps.data(), nullptr,
+                                        deps.size(), cudaStreamCaptureModeRelaxed));
+  return CF_OK;
+}
+
+cf_err seg_end(cudaStream_t s, std::vector<cudaGraphNode_t>* tail) {
+  cudaStreamCaptureStatus st;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  cudaGraph_t g;
+  CF_CUDA(cudaStreamGetCaptureInfo(s, &st, nullptr, &g, &deps, nullptr, &nd));
+  std::vector<cudaGraphNode_t> t(deps, deps + nd);
+  cudaGraph_t out;
+  CF_CUDA(cudaStreamEndCapture(s, &out));
+  if (tail) *tail = t;
+  return CF_OK;
+}
+
+cf_err add_cond(cudaGraph_t g, const std::vector<cudaGraphNode_t>& deps,
+                cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type,
+                cudaGraphNode_t* node, cudaGraph_t* body) {
+  // zero-filled storage: the params union has no usable default constructor
+  alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)];
+  std::memset(raw, 0, sizeof(raw));
+  cudaGraphNodeParams& p = *reinterpret_cast<cudaGraphNodeParams*>(raw);
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = h;
+  p.conditional.type = type;
+  p.conditional.size = 1;
+  CF_CUDA(cudaGraphAddNode(node, g, deps.empty() ? nullptr : deps.data(), nullptr, deps.size(), &p));
+  *body = p.conditional.phGraph_out[0];
+  return CF_OK;
+}
+
+int count_kernels(cudaGraph_t g) {
+  size_t nn = 0;
+  if (cudaGraphGetNodes(g, nullptr, &nn) != cudaSuccess) return 0;
+  std::vector<cudaGraphNode_t> nodes(nn);
+  cudaGraphGetNodes(g, nodes.data(), &nn);
+  int k = 0;
+  for (auto nd : nodes) {
+    cudaGraphNodeType t;
+    if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++k;
+  }
+  return k;
+}
+
+// Buffers of one CG run on (lam I + A^T A) z = rhs.
+struct CgBufs {
+  Ctl* ctl;
+  const cf_op* A;
+  int64_t n;
+  float *z, *rhs, *r, *p, *q, *t, *ws;
+  double* part;
+};
+
+// Gram pass out = A^T A x (the CG kernels add lam x).
+void gram(const CgBufs& b, const float* x, float* out, cudaStream_t s) {
+  op_apply(b.A, false, 1.f, x, b.t, false, b.ws, s);
+  op_apply(b.A, true, 1.f, b.t, out, false, b.ws, s);
+}
+
+// CG start: r = rhs - (lam z + A^T A z), p = r, threshold, loop decision.
+void cg_start(const CgBufs& b, int mode, cudaGraphConditionalHandle h, cudaStream_t s) {
+  gram(b, b.z, b.q, s);
+  k_cg_init<<<grid_for(b.n), kThreads, 0, s>>>(b.ctl, b.n, b.rhs, b.z, b.q, b.r, b.p, b.part, mode, h);
+}
+
+// One CG step as a captured sequence (body of a WHILE node).
+void cg_step(const CgBufs& b, int mode, cudaGraphConditionalHandle h, cudaStream_t s) {
+  gram(b, b.p, b.q, s);
+  k_cg_dot<<<grid_for(b.n), kThreads, 0, s>>>(b.ctl, b.n, b.p, b.q, b.part);
+  k_cg_update<<<grid_for(b.n), kThreads, 0, s>>>(b.ctl, b.n, b.z, b.r, b.p, b.q, b.part, mode);
+  k_cg_p<<<grid_for(b.n), kThreads, 0, s>>>(b.ctl, b.n, b.r, b.p, mode, h);
+}
+
+CgBufs cg_bufs(cf_problem* P, float* z) {
+  return CgBufs{P->ctl, P->A, P->n, z, P->rhs, P->r, P->p, P->qv, P->t, P->ws, P->part};
+}
+
+cf_err build_setup_graph(cf_problem* P) {
+  cudaStream_t s = P->stream;
+  const int64_t n = P->n, m = P->m;
+  cudaGraph_t G;
+  CF_CUDA(cudaGraphCreate(&G, 0));
+  P->setup_graph = G;
+  cudaGraphConditionalHandle h;
+  CF_CUDA(cudaGraphConditionalHandleCreate(&h, G, 0, 0));
+  std::vector<cudaGraphNode_t> tail, tmp;
+  CF_TRY(seg_begin(s, G, {}));
+  k_setup_init<<<grid_for(n), kThreads, 0, s>>>(P->ctl, n, P->gx, P->rhs, P->cf);
+  op_apply(P->A, true, -1.f, P->bf, P->rhs, true, P->ws, s);  // rhs = c - A^T b
+  const CgBufs cb = cg_bufs(P, P->gx);
+  cg_start(cb, CG_SETUP, h, s);
+  CF_TRY(seg_end(s, &tail));
+  cudaGraphNode_t wn;
+  cudaGraph_t body = nullptr;
+  CF_TRY(add_cond(G, tail, h, cudaGraphCondTypeWhile, &wn, &body));
+  CF_TRY(seg_begin(s, body, {}));
+  cg_step(cb, CG_SETUP, h, s);
+  CF_TRY(seg_end(s, &tmp));
+  CF_TRY(seg_begin(s, G, {wn}));
+  op_apply(P->A, false, 1.f, P->gx, P->gy, false, P->ws, s);
+  k_setup_fin<<<grid_for(std::max(n, m)), kThreads, 0, s>>>(P->ctl, n, m, P->gx, P->gy, P->bf, P->cf,
+                                                            P->part);
+  CF_TRY(seg_end(s, &tmp));
+  CF_CUDA(cudaGetLastError());
+  P->skc.top = count_kernels(G);
+  P->skc.cg = count_kernels(body);
+  CF_CUDA(cudaGraphInstantiate(&P->setup_exec, G, 0));
+  return CF_OK;
+}
+
+cf_err build_iter_graph(cf_problem* P) {
+  cudaStream_t s = P->stream;
+  const int64_t n = P->n, m = P->m;
+  cudaGraph_t G;
+  CF_CUDA(cudaGraphCreate(&G, 0));
+  P->graph = G;
+  cudaGraphConditionalHandle h_outer;
+  CF_CUDA(cudaGraphConditionalHandleCreate(&h_outer, G, 1, cudaGraphCondAssignDefault));
+  std::vector<cudaGraphNode_t> tail, tmp;
+  // top: reset state
+  CF_TRY(seg_begin(s, G, {}));
+  k_init<<<grid_for(std::max(n, m)), kThreads, 0, s>>>(P->ctl, n, m, P->ux, P->uy, P->vs, P->zx,
+                                                       P->warm_dev);
+  CF_TRY(seg_end(s, &tail));
+  cudaGraphNode_t wn;
+  cudaGraph_t B = nullptr;
+  CF_TRY(add_cond(G, tail, h_outer, cudaGraphCondTypeWhile, &wn, &B));
+  cudaGraphConditionalHandle h_cg, h_chk;
+  CF_CUDA(cudaGraphConditionalHandleCreate(&h_cg, B, 0, 0));
+  CF_CUDA(cudaGraphConditionalHandleCreate(&h_chk, B, 0, 0));
+  // body part 1: right-hand side, CG start
+  CF_TRY(seg_begin(s, B, {}));
+  k_rhs<<<grid_for(std::max(n, m)), kThreads, 0, s>>>(P->ctl, n, m, P->ux, P->uy, P->vs, P->wy, P->rhs);
+  op_apply(P->A, true, -1.f, P->wy, P->rhs, true, P->ws, s);  // rhs = w_x - A^T w_y
+  const CgBufs cb = cg_bufs(P, P->zx);
+  cg_start(cb, CG_ITER, h_cg, s);
+  CF_TRY(seg_end(s, &tail));
+  cudaGraphNode_t cgn;
+  cudaGraph_t C = nullptr;
+  CF_TRY(add_cond(B, tail, h_cg, cudaGraphCondTypeWhile, &cgn, &C));
+  CF_TRY(seg_begin(s, C, {}));
+  cg_step(cb, CG_ITER, h_cg, s);
+  CF_TRY(seg_end(s, &tmp));
+  // body part 2: subspace step, projection, dual update
+  CF_TRY(seg_begin(s, B, {cgn}));
+  op_apply(P->A, false, 1.f, P->zx, P->zy, false, P->ws, s);  // z_y = A z_x (+ w_y in k_utau)
+  k_utau<<<grid_for(std::max(n, m)), kThreads, 0, s>>>(P->ctl, n, m, P->zx, P->zy, P->wy, P->bf, P->cf,
+                                                       P->part);
+  if (P->nchunk > 0)
+    k_soc_norm<<<(unsigned)P->nchunk, kThreads, 0, s>>>(P->ctl, 0, P->chunk_seg, P->chunk_r0, P->chunk_r1,
+                                                        P->seg_head, P->zy, P->gy, P->uy, P->vs,
+                                                        P->chunk_n2, P->seg_p0);
+  const int nlin = grid_for(n + P->z + P->l);
+  k_apply<<<(unsigned)(nlin + P->nchunk), kThreads, 0, s>>>(
+      P->ctl, n, m, P->z, P->l, nlin, P->ux, P->uy, P->vs, P->zx, P->zy, P->gx, P->gy, P->chunk_seg,
+      P->chunk_r0, P->chunk_r1, P->seg_head, P->seg_c0, P->seg_nc, P->chunk_n2, P->seg_p0, h_chk);
+  CF_TRY(seg_end(s, &tail));
+  cudaGraphNode_t ifn;
+  cudaGraph_t D = nullptr;
+  CF_TRY(add_cond(B, tail, h_chk, cudaGraphCondTypeIf, &ifn, &D));
+  CF_TRY(seg_begin(s, D, {}));
+  op_apply(P->A, false, 1.f, P->ux, P->cm, false, P->ws, s);
+  op_apply(P->A, true, 1.f, P->uy, P->cn, false, P->ws, s);
+  k_resid<<<grid_for(std::max(n, m)), kThreads, 0, s>>>(P->ctl, n, m, P->cm, P->cn, P->ux, P->uy, P->vs,
+                                                        P->bf, P->cf, P->part);
+  CF_TRY(seg_end(s, &tmp));
+  CF_TRY(seg_begin(s, B, {ifn}));
+  k_outer<<<1, 32, 0, s>>>(P->ctl, h_outer);
+  CF_TRY(seg_end(s, &tmp));
+  CF_CUDA(cudaGetLastError());
+  P->kc.top = count_kernels(G);
+  P->kc.body = count_kernels(B);
+  P->kc.cg = count_kernels(C);
+  P->kc.check = count_kernels(D);
+  CF_CUDA(cudaGraphInstantiate(&P->exec, G, 0));
+  return CF_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ state
+size_t problem_state_bytes(const cf_problem* P) {
+  const size_t n = P->n, m = P->m, N = n + m + 1;
+  auto f = [](size_t k) { return align_up(k * sizeof(float), 256); };
+  auto d = [](size_t k) { return align_up(k * sizeof(double), 256); };
+  size_t wsf = std::max(op_ws_floats(P->A, false), op_ws_floats(P->A, true));
+  size_t b = 0;
+  b += 8 * f(n);            // ux zx rhs r p q gx cn
+  b += 7 * f(m);            // uy vs wy t zy gy cm
+  b += f(wsf);
+  b += d((size_t)kMaxRedBlocks * kRedSlots);
+  b += d((size_t)std::max<int64_t>(P->nchunk, 1)) + d((size_t)std::max<int64_t>(P->nseg, 1));
+  b += 2 * d(2 * N);        // warm_dev, uv_dev
+  b += d(n + 2 * m);        // out_dev
+  b += align_up(sizeof(Ctl), 256);
+  return b;
+}
+
+cf_err ensure_state(cf_problem* P) {
+  if (P->arena) return CF_OK;
+  const size_t n = P->n, m = P->m, N = n + m + 1;
+  size_t bytes = problem_state_bytes(P);
+  void* a = nullptr;
+  cudaError_t e = cudaMalloc(&a, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(CF_E_OOM, std::string("solver state allocation failed: ") + cudaGetErrorString(e));
+  }
+  P->arena = a;
+  P->state_bytes = bytes;
+  char* cur = (char*)a;
+  auto takef = [&](size_t k) { float* r = (float*)cur; cur += align_up(k * sizeof(float), 256); return r; };
+  auto taked = [&](size_t k) { double* r = (double*)cur; cur += align_up(k * sizeof(double), 256); return r; };
+  P->ux = takef(n); P->zx = takef(n); P->rhs = takef(n); P->r = takef(n);
+  P->p = takef(n); P->qv = takef(n); P->gx = takef(n); P->cn = takef(n);
+  P->uy = takef(m); P->vs = takef(m); P->wy = takef(m); P->t = takef(m);
+  P->zy = takef(m); P->gy = takef(m); P->cm = takef(m);
+  P->ws = takef(std::max(op_ws_floats(P->A, false), op_ws_floats(P->A, true)));
+  P->part = taked((size_t)kMaxRedBlocks * kRedSlots);
+  P->chunk_n2 = taked((size_t)std::max<int64_t>(P->nchunk, 1));
+  P->seg_p0 = taked((size_t)std::max<int64_t>(P->nseg, 1));
+  P->warm_dev = taked(2 * N);
+  P->uv_dev = taked(2 * N);
+  P->out_dev = taked(n + 2 * m);
+  P->ctl = (Ctl*)cur;
+  CF_CUDA(cudaMemsetAsync(P->ctl, 0, sizeof(Ctl), P->stream));
+  CF_CUDA(cudaMemsetAsync(P->warm_dev, 0, 2 * N * sizeof(double), P->stream));
+  CF_CUDA(cudaStreamSynchronize(P->stream));
+  P->ctl_host->nb = P->nb;
+  P->ctl_host->nc = P->nc;
+  CF_CUDA(cudaMemcpy(&P->ctl->nb, &P->nb, sizeof(double), cudaMemcpyHostToDevice));
+  CF_CUDA(cudaMemcpy(&P->ctl->nc, &P->nc, sizeof(double), cudaMemcpyHostToDevice));
+  P->setup_done = false;
+  return CF_OK;
+}
+
+void release_state(cf_problem* P) {
+  if (P->exec) cudaGraphExecDestroy(P->exec);
+  if (P->graph) cudaGraphDestroy(P->graph);
+  if (P->setup_exec) cudaGraphExecDestroy(P->setup_exec);
+  if (P->setup_graph) cudaGraphDestroy(P->setup_graph);
+  P->exec = nullptr;
+  P->graph = nullptr;
+  P->setup_exec = nullptr;
+  P->setup_graph = nullptr;
+  if (P->arena) cudaFree(P->arena);
+  P->arena = nullptr;
+  P->setup_done = false;
+}
+
+bool settings_valid(const cf_settings* st, std::string* why) {
+  auto bad = [&](const char* w) { *why = w; return false; };
+  if (!(st->eps > 0)) return bad("eps must be > 0");
+  if (!(st->eps_infeas > 0)) return bad("eps_infeas must be > 0");
+  if (!(st->alpha > 0 && st->alpha < 2)) return bad("alpha must be in (0, 2)");
+  if (st->max_iters < 1) return bad("max_iters must be >= 1");
+  if (st->check_interval < 1) return bad("check_interval must be >= 1");
+  if (st->cg_max_iters < 0 || st->cg_max_iters > 100000) return bad("cg_max_iters must be in [0, 100000]");
+  if (st->cg_fixed_iters < 0 || st->cg_fixed_iters > 100000) return bad("cg_fixed_iters must be in [0, 100000]");
+  if (st->setup_cg_max_iters < 1 || st->setup_cg_max_iters > 1000000) return bad("setup_cg_max_iters must be in [1, 1e6]");
+  if (!(st->setup_cg_tol > 0)) return bad("setup_cg_tol must be > 0");
+  if (!(st->cg_tol_rel >= 0) || !(st->cg_tol_min >= 0) || !std::isfinite(st->cg_tol_exp))
+    return bad("CG tolerance parameters must be >= 0");
+  return true;
+}
+
+static void write_settings(cf_problem* P, const cf_settings* st, bool warm) {
+  Settings& s = P->ctl_host->st;
+  s.alpha = st->alpha;
+  s.eps = st->eps;
+  s.eps_inf = st->eps_infeas;
+  s.cg_tol_rel = st->cg_tol_rel;
+  s.cg_tol_exp = st->cg_tol_exp;
+  s.cg_tol_min = st->cg_tol_min;
+  s.setup_tol = st->setup_cg_tol;
+  s.max_iters = st->max_iters;
+  s.check_interval = st->check_interval;
+  s.cg_max = st->cg_max_iters;
+  s.cg_fixed = st->cg_fixed_iters;
+  s.setup_cg_max = st->setup_cg_max_iters;
+  s.warm = warm ? 1 : 0;
+}
+
+static cf_err run_setup(cf_problem* P) {
+  if (!P->setup_exec) CF_TRY(build_setup_graph(P));
+  CF_CUDA(cudaMemcpyAsync(&P->ctl->st, &P->ctl_host->st, sizeof(Settings), cudaMemcpyHostToDevice, P->stream));
+  CF_CUDA(cudaGraphLaunch(P->setup_exec, P->stream));
+  CF_CUDA(cudaMemcpyAsync(P->ctl_host, P->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, P->stream));
+  CF_CUDA(cudaStreamSynchronize(P->stream));
+  P->setup_iters_last = P->ctl_host->setup_iters;
+  P->setup_done = true;
+  return CF_OK;
+}
+
+cf_err solve_launch(cf_problem* P, const cf_settings* st_in, double* x, double* y, double* s,
+                    const double* warm_uv, double* uv_out) {
+  cf_settings st;
+  if (st_in)
+    st = *st_in;
+  else
+    cf_settings_default(&st);
+  std::string why;
+  if (!settings_valid(&st, &why)) return fail(CF_E_INVALID, "solve: " + why);
+  const int64_t t0 = now_ns();
+  CF_TRY(ensure_state(P));
+  write_settings(P, &st, warm_uv != nullptr);
+  P->ran_setup = false;
+  // order after earlier work on the context stream
+  CF_CUDA(cudaEventRecord(P->ev_in, P->ctx->stream));
+  CF_CUDA(cudaStreamWaitEvent(P->stream, P->ev_in, 0));
+  if (!P->setup_done) {
+    CF_TRY(run_setup(P));
+    P->ran_setup = true;
+    P->setup_ns_last = now_ns() - t0;
+  } else {
+    P->setup_ns_last = 0;
+  }
+  if (!P->exec) CF_TRY(build_iter_graph(P));
+  const int64_t N = P->n + P->m + 1;
+  if (warm_uv) CF_TRY(copy_any(P->warm_dev, warm_uv, 2 * N * sizeof(double), P->stream));
+  CF_CUDA(cudaMemcpyAsync(&P->ctl->st, &P->ctl_host->st, sizeof(Settings), cudaMemcpyHostToDevice, P->stream));
+  P->t_launch = now_ns();
+  CF_CUDA(cudaGraphLaunch(P->exec, P->stream));
+  P->x_out = x;
+  P->y_out = y;
+  P->s_out = s;
+  P->uv_out = uv_out;
+  if (x || y || s) {
+    k_output<<<grid_for(std::max(P->n, P->m)), kThreads, 0, P->stream>>>(P->ctl, P->n, P->m, P->ux, P->uy,
+                                                                       P->vs, P->out_dev);
+    CF_CUDA(cudaGetLastError());
+  }
+  if (uv_out) {
+    k_export_uv<<<grid_for(std::max(P->n, P->m)), kThreads, 0, P->stream>>>(P->ctl, P->n, P->m, P->ux,
+                                                                           P->uy, P->vs, P->uv_dev);
+    CF_CUDA(cudaGetLastError());
+  }
+  CF_CUDA(cudaMemcpyAsync(P->ctl_host, P->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, P->stream));
+  CF_CUDA(cudaEventRecord(P->ev_out, P->stream));
+  CF_CUDA(cudaStreamWaitEvent(P->ctx->stream, P->ev_out, 0));
+  return CF_OK;
+}
+
+cf_err solve_finish(cf_problem* P, cf_info* info) {
+  CF_CUDA(cudaStreamSynchronize(P->stream));
+  const int64_t t1 = now_ns();
+  const int64_t n = P->n, m = P->m, N = n + m + 1;
+  if (P->x_out) CF_TRY(copy_any(P->x_out, P->out_dev, n * sizeof(double), P->stream));
+  if (P->y_out) CF_TRY(copy_any(P->y_out, P->out_dev + n, m * sizeof(double), P->stream));
+  if (P->s_out) CF_TRY(copy_any(P->s_out, P->out_dev + n + m, m * sizeof(double), P->stream));
+  if (P->uv_out) CF_TRY(copy_any(P->uv_out, P->uv_dev, 2 * N * sizeof(double), P->stream));
+  CF_CUDA(cudaStreamSynchronize(P->stream));
+  const Ctl& c = *P->ctl_host;
+  if (info) {
+    std::memset(info, 0, sizeof(*info));
+    info->status = c.status;
+    info->iters = c.k;
+    info->cg_iters_total = c.cg_total;
+    info->checks = c.checks;
+    info->setup_cg_iters = P->ran_setup ? P->setup_iters_last : 0;
+    info->pri_res = c.pri;
+    info->dual_res = c.dual;
+    info->gap = c.gap;
+    const double tau = c.tau;
+    info->pobj = tau > 0 ? c.cx / tau : NAN;
+    info->dobj = tau > 0 ? -c.by / tau : NAN;
+    info->tau = c.tau;
+    info->kappa = c.kappa;
+    info->setup_ns = P->setup_ns_last;
+    info->solve_ns = t1 - P->t_launch;
+    int64_t kl = P->kc.top + (int64_t)c.k * P->kc.body + c.cg_total * P->kc.cg +
+                 (int64_t)c.checks * P->kc.check;
+    if (P->x_out || P->y_out || P->s_out) kl += 1;
+    if (P->uv_out) kl += 1;
+    if (P->ran_setup) kl += P->skc.top + (int64_t)P->setup_iters_last * P->skc.cg;
+    info->kernel_launches = kl;
+  }
+  return CF_OK;
+}
+
+// k_cg_init/update with mode CG_SETUP read their threshold and cap from the
+// setup fields; a standalone CG run sets those and the shift lam.
+__global__ void k_cg_solo_init(Ctl* c, double lam, double tol, int max_iters) {
+  c->lam = lam;
+  c->st.setup_tol = tol;
+  c->st.setup_cg_max = max_iters;
+  c->setup_iters = 0;
+  c->red_count = 0u;
+}
+
+cf_err cg_solve_impl(cf_op* A, double lam, const float* rhs_in, float* x, int32_t max_iters,
+                     double tol, int32_t* iters, double* res_norm) {
+  cf_ctx* ctx = A->ctx;
+  const int64_t n = A->n, m = A->m;
+  const size_t wsf = std::max(op_ws_floats(A, false), op_ws_floats(A, true));
+  auto f = [](size_t k) { return align_up(k * sizeof(float), 256); };
+  const size_t bytes = 5 * f(n) + f(m) + f(wsf) +
+                       align_up(sizeof(double) * kMaxRedBlocks * kRedSlots, 256) + align_up(sizeof(Ctl), 256);
+  char* arena = nullptr;
+  cudaError_t e = cudaMalloc((void**)&arena, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(CF_E_OOM, "cg_solve: allocation failed");
+  }
+  char* cur = arena;
+  auto take = [&](size_t b) { char* r = cur; cur += align_up(b, 256); return r; };
+  CgBufs b;
+  b.A = A;
+  b.n = n;
+  b.z = (float*)take(n * 4);
+  b.rhs = (float*)take(n * 4);
+  b.r = (float*)take(n * 4);
+  b.p = (float*)take(n * 4);
+  b.q = (float*)take(n * 4);
+  b.t = (float*)take(m * 4);
+  b.ws = (float*)take(wsf * 4);
+  b.part = (double*)take(sizeof(double) * kMaxRedBlocks * kRedSlots);
+  b.ctl = (Ctl*)take(sizeof(Ctl));
+  cudaStream_t s = nullptr;
+  cudaGraph_t G = nullptr;
+  cudaGraphExec_t ex = nullptr;
+  Ctl* hc = nullptr;
+  cudaEvent_t ev = nullptr;
+  auto run = [&]() -> cf_err {
+    CF_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    CF_CUDA(cudaMallocHost((void**)&hc, sizeof(Ctl)));
+    CF_CUDA(cudaMemsetAsync(b.ctl, 0, sizeof(Ctl), s));
+    CF_TRY(copy_any(b.rhs, rhs_in, n * sizeof(float), s));
+    CF_TRY(copy_any(b.z, x, n * sizeof(float), s));
+    CF_CUDA(cudaGraphCreate(&G, 0));
+    cudaGraphConditionalHandle h;
+    CF_CUDA(cudaGraphConditionalHandleCreate(&h, G, 0, 0));
+    std::vector<cudaGraphNode_t> tail, tmp;
+    CF_TRY(seg_begin(s, G, {}));
+    k_cg_solo_init<<<1, 1, 0, s>>>(b.ctl, lam, tol, max_iters);
+    cg_start(b, CG_SETUP, h, s);
+    CF_TRY(seg_end(s, &tail));
+    cudaGraphNode_t wn;
+    cudaGraph_t body = nullptr;
+    CF_TRY(add_cond(G, tail, h, cudaGraphCondTypeWhile, &wn, &body));
+    CF_TRY(seg_begin(s, body, {}));
+    cg_step(b, CG_SETUP, h, s);
+    CF_TRY(seg_end(s, &tmp));
+    CF_CUDA(cudaGetLastError());
+    CF_CUDA(cudaGraphInstantiate(&ex, G, 0));
+    CF_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    CF_CUDA(cudaEventRecord(ev, ctx->stream));
+    CF_CUDA(cudaStreamWaitEvent(s, ev, 0));
+    CF_CUDA(cudaGraphLaunch(ex, s));
+    CF_CUDA(cudaMemcpyAsync(hc, b.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+    CF_TRY(copy_any(x, b.z, n * sizeof(float), s));
+    CF_CUDA(cudaStreamSynchronize(s));
+    if (iters) *iters = hc->setup_iters;
+    if (res_norm) *res_norm = std::sqrt(hc->rr);
+    return CF_OK;
+  };
+  cf_err r = run();
+  if (ex) cudaGraphExecDestroy(ex);
+  if (G) cudaGraphDestroy(G);
+  if (s) {
+    cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+  }
+  if (hc) cudaFreeHost(hc);
+  if (ev) cudaEventDestroy(ev);
+  cudaFree(arena);
+  return r;
+}
+
+}  // namespace cf
+
+using namespace cf;
+
+// ------------------------------------------------------------------ C ABI
+extern "C" {
+
+cf_err cone_problem_create(cf_ctx* ctx, const cf_op* A, const double* b, int64_t m,
+                           const double* c, int64_t n, const cf_cone* K, cf_problem** out) {
+  if (!ctx || !A || !b || !c || !K || !out) return fail(CF_E_INVALID, "cone_problem_create: NULL argument");
+  if (A->m != m || A->n != n) return fail(CF_E_INVALID, "cone_problem_create: operator shape differs from (m, n)");
+  if (K->z < 0 || K->l < 0 || K->nq < 0 || (K->nq > 0 && !K->q))
+    return fail(CF_E_INVALID, "cone_problem_create: bad cone");
+  int64_t tot = K->z + K->l;
+  for (int64_t j = 0; j < K->nq; ++j) {
+    if (K->q[j] < 1) return fail(CF_E_INVALID, "cone_problem_create: SOC size < 1");
+    tot += K->q[j];
+  }
+  if (tot != m) return fail(CF_E_INVALID, "cone_problem_create: z + l + sum(q) != m");
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(ctx->device);
+  std::unique_ptr<cf_problem> P(new cf_problem());
+  P->ctx = ctx;
+  P->m = m;
+  P->n = n;
+  P->z = K->z;
+  P->l = K->l;
+  P->q.assign(K->q, K->q + K->nq);
+  auto run = [&]() -> cf_err {
+    std::vector<double> hb(m), hc(n);
+    CF_TRY(copy_any(hb.data(), b, m * sizeof(double), ctx->stream));
+    CF_TRY(copy_any(hc.data(), c, n * sizeof(double), ctx->stream));
+    double nb = 0, nc = 0;
+    for (double v : hb) nb += v * v;
+    for (double v : hc) nc += v * v;
+    for (double v : hb) if (!std::isfinite(v)) return fail(CF_E_INVALID, "cone_problem_create: b not finite");
+    for (double v : hc) if (!std::isfinite(v)) return fail(CF_E_INVALID, "cone_problem_create: c not finite");
+    P->nb = std::sqrt(nb);
+    P->nc = std::sqrt(nc);
+    std::vector<float> fb(hb.begin(), hb.end()), fc(hc.begin(), hc.end());
+    // cone tables
+    std::vector<int32_t> cseg, sc0, snc;
+    std::vector<int64_t> cr0, cr1, shead;
+    int64_t off = K->z + K->l;
+    for (size_t j = 0; j < P->q.size(); ++j) {
+      shead.push_back(off);
+      sc0.push_back((int32_t)cr0.size());
+      int32_t cnt = 0;
+      for (int64_t r = off; r < off + P->q[j]; r += kSocChunk) {
+        cseg.push_back((int32_t)j);
+        cr0.push_back(r);
+        cr1.push_back(std::min(r + kSocChunk, off + P->q[j]));
+        ++cnt;
+      }
+      snc.push_back(cnt);
+      off += P->q[j];
+    }
+    P->nseg = (int64_t)shead.size();
+    P->nchunk = (int64_t)cr0.size();
+    size_t bytes = align_up(m * 4, 256) + align_up(n * 4, 256) +
+                   align_up(std::max<size_t>(P->nchunk, 1) * (4 + 8 + 8), 256) +
+                   align_up(std::max<size_t>(P->nseg, 1) * (8 + 4 + 4), 256) + 1024;
+    char* base = nullptr;
+    cudaError_t e = cudaMalloc((void**)&base, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(CF_E_OOM, "cone_problem_create: allocation failed");
+    }
+    P->persist_bytes = bytes;
+    char* cur = base;
+    auto take = [&](size_t k) { char* r = cur; cur += align_up(k, 256); return r; };
+    P->bf = (float*)take(m * 4);
+    P->cf = (float*)take(n * 4);
+    const size_t nch = std::max<size_t>(P->nchunk, 1), nsg = std::max<size_t>(P->nseg, 1);
+    P->chunk_r0 = (int64_t*)take(nch * 8);
+    P->chunk_r1 = (int64_t*)take(nch * 8);
+    P->chunk_seg = (int32_t*)take(nch * 4);
+    P->seg_head = (int64_t*)take(nsg * 8);
+    P->seg_c0 = (int32_t*)take(nsg * 4);
+    P->seg_nc = (int32_t*)take(nsg * 4);
+    CF_CUDA(cudaMemcpy(P->bf, fb.data(), m * 4, cudaMemcpyHostToDevice));
+    CF_CUDA(cudaMemcpy(P->cf, fc.data(), n * 4, cudaMemcpyHostToDevice));
+    if (P->nchunk) {
+      CF_CUDA(cudaMemcpy(P->chunk_r0, cr0.data(), P->nchunk * 8, cudaMemcpyHostToDevice));
+      CF_CUDA(cudaMemcpy(P->chunk_r1, cr1.data(), P->nchunk * 8, cudaMemcpyHostToDevice));
+      CF_CUDA(cudaMemcpy(P->chunk_seg, cseg.data(), P->nchunk * 4, cudaMemcpyHostToDevice));
+      CF_CUDA(cudaMemcpy(P->seg_head, shead.data(), P->nseg * 8, cudaMemcpyHostToDevice));
+      CF_CUDA(cudaMemcpy(P->seg_c0, sc0.data(), P->nseg * 4, cudaMemcpyHostToDevice));
+      CF_CUDA(cudaMemcpy(P->seg_nc, snc.data(), P->nseg * 4, cudaMemcpyHostToDevice));
+    }
+    CF_CUDA(cudaStreamCreateWithFlags(&P->stream, cudaStreamNonBlocking));
+    CF_CUDA(cudaEventCreateWithFlags(&P->ev_in, cudaEventDisableTiming));
+    CF_CUDA(cudaEventCreateWithFlags(&P->ev_out, cudaEventDisableTiming));
+    CF_CUDA(cudaMallocHost((void**)&P->ctl_host, sizeof(Ctl)));
+    std::memset(P->ctl_host, 0, sizeof(Ctl));
+    return CF_OK;
+  };
+  cf_err r = run();
+  if (r != CF_OK) {
+    cf_problem* raw = P.release();
+    raw->A = nullptr;
+    cf_problem_destroy(raw);
+  } else {
+    op_retain(const_cast<cf_op*>(A));
+    P->A = const_cast<cf_op*>(A);
+    *out = P.release();
+  }
+  if (prev >= 0) cudaSetDevice(prev);
+  return r;
+}
+
+void cf_problem_destroy(cf_problem* P) {
+  if (!P) return;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(P->ctx->device);
+  if (P->stream) cudaStreamSynchronize(P->stream);
+  release_state(P);
+  if (P->bf) cudaFree(P->bf);  // base of the persistent block
+  if (P->ctl_host) cudaFreeHost(P->ctl_host);
+  if (P->ev_in) cudaEventDestroy(P->ev_in);
+  if (P->ev_out) cudaEventDestroy(P->ev_out);
+  if (P->stream) cudaStreamDestroy(P->stream);
+  if (P->A) cf_op_destroy(P->A);
+  delete P;
+  if (prev >= 0) cudaSetDevice(prev);
+}
+
+cf_err solve(cf_problem* P, const cf_settings* st, double* x, double* y, double* s,
+             const double* warm_uv, double* uv_out, cf_info* info) {
+  if (!P) return fail(CF_E_INVALID, "solve: NULL problem");
+  std::lock_guard<std::mutex> lk(P->mtx);
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(P->ctx->device);
+  cf_err r = solve_launch(P, st, x, y, s, warm_uv, uv_out);
+  if (r == CF_OK) r = solve_finish(P, info);
+  if (prev >= 0) cudaSetDevice(prev);
+  return r;
+}
+
+cf_err solve_batch(cf_problem* const* probs, int32_t count, const cf_settings* st,
+                   double* const* xs, double* const* ys, double* const* ss, cf_info* infos) {
+  if (count < 0 || (count > 0 && !probs)) return fail(CF_E_INVALID, "solve_batch: bad arguments");
+  for (int32_t i = 0; i < count; ++i) {
+    if (!probs[i]) return fail(CF_E_INVALID, "solve_batch: NULL problem");
+    for (int32_t j = 0; j < i; ++j)
+      if (probs[j] == probs[i]) return fail(CF_E_INVALID, "solve_batch: a problem appears twice");
+  }
+  std::vector<std::unique_lock<std::mutex>> locks;
+  for (int32_t i = 0; i < count; ++i) locks.emplace_back(probs[i]->mtx);
+  cf_err first = CF_OK;
+  std::vector<char> launched(count, 0);
+  for (int32_t i = 0; i < count; ++i) {
+    cudaSetDevice(probs[i]->ctx->device);
+    cf_err r = solve_launch(probs[i], st, xs ? xs[i] : nullptr, ys ? ys[i] : nullptr,
+                            ss ? ss[i] : nullptr, nullptr, nullptr);
+    launched[i] = r == CF_OK;
+    if (r != CF_OK && first == CF_OK) first = r;
+  }
+  for (int32_t i = 0; i < count; ++i) {
+    if (!launched[i]) continue;
+    cf_err r = solve_finish(probs[i], infos ? &infos[i] : nullptr);
+    if (r != CF_OK && first == CF_OK) first = r;
+  }
+  return first;
+}
+
+cf_err cg_solve(cf_op* A, double lam, const float* rhs, float* x, int32_t max_iters, double tol,
+                int32_t* iters, double* res_norm) {
+  if (!A || !rhs || !x || max_iters < 0 || !(tol >= 0) || !(lam >= 0))
+    return fail(CF_E_INVALID, "cg_solve: bad arguments");
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(A->ctx->device);
+  cf_err r = cg_solve_impl(A, lam, rhs, x, max_iters, tol, iters, res_norm);
+  if (prev >= 0) cudaSetDevice(prev);
+  return r;
+}
+
+}  // extern "C"

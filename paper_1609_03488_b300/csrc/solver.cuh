@@ -1,0 +1,81 @@
+// Solver state shared by the solver and the server translation units.
+#pragma once
+
+#include <mutex>
+
+#include "internal.cuh"
+
+namespace cf {
+
+enum CgMode { CG_ITER = 0, CG_SETUP = 1 };
+
+// Device control block of one problem.  The host writes the settings block
+// before each launch; everything else is written by kernels.
+struct Settings {
+  double alpha, eps, eps_inf, cg_tol_rel, cg_tol_exp, cg_tol_min, setup_tol;
+  int max_iters, check_interval, cg_max, cg_fixed, setup_cg_max, warm;
+};
+
+struct Ctl {
+  Settings st;
+  double lam;            // Gram shift: CG solves (lam I + A^T A) z = rhs
+  double hg, nb, nc;     // h^T g, ||b||, ||c||
+  double tau, kappa, w_tau, ut_tau;
+  double rr, tol2, alpha_cg, beta_cg;
+  double pri, dual, gap, cx, by;
+  long long cg_total;
+  int k, cg_it, cg_guard, checks, status, stop, cg_cont, setup_iters;
+  unsigned int red_count;
+};
+
+struct KernelCounts {
+  int top = 0, body = 0, cg = 0, check = 0;
+};
+
+}  // namespace cf
+
+struct cf_problem {
+  cf_ctx* ctx = nullptr;
+  cf_op* A = nullptr;
+  int64_t m = 0, n = 0, z = 0, l = 0;
+  std::vector<int64_t> q;
+  double nb = 0, nc = 0;
+  std::mutex mtx;  // one solve at a time per problem
+  // persistent device data
+  float *bf = nullptr, *cf = nullptr;
+  int64_t nseg = 0, nchunk = 0;
+  int32_t *chunk_seg = nullptr;
+  int64_t *chunk_r0 = nullptr, *chunk_r1 = nullptr, *seg_head = nullptr;
+  int32_t *seg_c0 = nullptr, *seg_nc = nullptr;
+  size_t persist_bytes = 0;
+  // solver state (allocated on first use, released by release_state)
+  void* arena = nullptr;
+  size_t state_bytes = 0;
+  float *ux, *uy, *vs, *zx, *rhs, *r, *p, *qv, *wy, *t, *zy, *gx, *gy, *cm, *cn, *ws;
+  double *part, *chunk_n2, *seg_p0, *warm_dev, *out_dev, *uv_dev;
+  cf::Ctl* ctl = nullptr;       // device
+  cf::Ctl* ctl_host = nullptr;  // pinned mirror
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaGraph_t graph = nullptr, setup_graph = nullptr;
+  cudaGraphExec_t exec = nullptr, setup_exec = nullptr;
+  cf::KernelCounts kc, skc;
+  bool setup_done = false;
+  int setup_iters_last = 0;
+  int64_t setup_ns_last = 0;
+  // per-call bookkeeping between launch and finish
+  double *x_out = nullptr, *y_out = nullptr, *s_out = nullptr, *uv_out = nullptr;
+  int64_t t_launch = 0;
+  bool ran_setup = false;
+};
+
+namespace cf {
+size_t problem_state_bytes(const cf_problem* p);
+cf_err ensure_state(cf_problem* p);
+void release_state(cf_problem* p);
+cf_err solve_launch(cf_problem* p, const cf_settings* st, double* x, double* y, double* s,
+                    const double* warm_uv, double* uv_out);
+cf_err solve_finish(cf_problem* p, cf_info* info);
+bool settings_valid(const cf_settings* st, std::string* why);
+int64_t now_ns();
+}  // namespace cf

@@ -1,0 +1,307 @@
+"""GPU parity of the SCS iteration (Section 5.2) against the FP64 oracle,
+through the C ABI.
+
+* trajectory: with the same fixed CG step count, the GPU's float32 iterates
+  u^k, v^k stay within 1e-5 (relative l2) of the oracle's float64 iterates for
+  the first 20 iterations;
+* solutions: the returned (x, y, s), re-checked in FP64, meet the 1e-4
+  residual tolerance, and the objective is within 1e-4 (|p - p*| / (1 + |p*|))
+  of an FP64 optimum from an independent solver or from the oracle;
+* certificates of infeasible / unbounded problems satisfy their definitions;
+* batched and served solves return bit-identical results to solo solves.
+"""
+import numpy as np
+import pytest
+import scipy.optimize as so
+
+from oracle import cones, linop, scs
+from paper_1609_03488_b300 import synth
+from tests.helpers import fp64_residuals, objective_rel_err, rel
+
+pytestmark = pytest.mark.gpu
+EPS = 1e-4
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_1609_03488_b300 import build
+    build.build()
+    from paper_1609_03488_b300 import binding
+    return binding
+
+
+@pytest.fixture(scope="module")
+def ctx(B):
+    return B.Context(0)
+
+
+def _solve(B, ctx, prob, **kw):
+    P = B.cone_problem_create(ctx, prob)
+    st = B.settings(**kw)
+    info, x, y, s = B.solve(P, st)
+    return info, x, y, s, P
+
+
+def _check_solution(prob, info, x, y, s, p_star, eps=EPS):
+    assert info["status_name"] == "solved", info
+    pri, dual, gap = fp64_residuals(prob, x, y, s)
+    assert max(pri, dual, gap) <= eps, (pri, dual, gap)
+    assert objective_rel_err(prob["c"] @ x, p_star) <= eps, (prob["c"] @ x, p_star)
+    assert cones.dist_to_cone(s, prob["cone"]) <= 1e-5 * (1 + np.linalg.norm(s))
+    assert cones.dist_to_dual_cone(y, prob["cone"]) <= 1e-5 * (1 + np.linalg.norm(y))
+
+
+# ---------------------------------------------------------------- trajectory
+@pytest.mark.parametrize("family", ["deconv", "lasso"])
+def test_first_20_iterates_match_oracle(B, ctx, family):
+    if family == "deconv":
+        prob = synth.deconv(n_x=1000, L=100, seed=synth.BASE_SEED + 1)     # the small workload
+    else:
+        prob = synth.lasso(m_d=600, p=300, seed=synth.BASE_SEED + 3)
+    ref = scs.problem_solve(prob, max_iters=20, check_interval=10 ** 6, linsys="cg", cg_fixed_steps=3,
+                            trajectory=20)
+    P = B.cone_problem_create(ctx, prob)
+    N = prob["A"]["n"] + prob["A"]["m"] + 1
+    for k in (1, 2, 3, 5, 10, 15, 20):
+        st = B.settings(max_iters=k, check_interval=10 ** 6, cg_fixed_iters=3)
+        uv = np.empty(2 * N)
+        info = B.cf_info()
+        B.check(B.lib.solve(P.h, B.C.byref(st), None, None, None, None, B._ptr(uv), B.C.byref(info)), "solve")
+        assert info.iters == k and info.cg_iters_total == 3 * k
+        eu = rel(uv[:N], ref["traj_u"][k - 1])
+        ev = rel(uv[N:], ref["traj_v"][k - 1])
+        assert eu <= 1e-5 and ev <= 1e-5, (k, eu, ev)
+
+
+# ---------------------------------------------------------------- solutions
+@pytest.mark.parametrize("n_x,L", [(300, 30), (1000, 100)])
+def test_deconv_solution(B, ctx, n_x, L):
+    prob = synth.deconv(n_x=n_x, L=L, seed=synth.BASE_SEED + 1)
+    K = linop.densify(prob["A"]["parts"][2]["parts"][0]["parts"][0])
+    _, p_star = so.nnls(K, prob["meta"]["b_obs"], maxiter=50 * n_x)
+    info, x, y, s, _ = _solve(B, ctx, prob, eps=EPS)
+    _check_solution(prob, info, x, y, s, p_star)
+
+
+@pytest.mark.parametrize("storage", ["fp32", "bf16", "fp8"])
+def test_lasso_solution(B, ctx, storage):
+    prob = synth.lasso(m_d=400, p=200, seed=synth.BASE_SEED + 3, storage=storage)
+    ref = scs.problem_solve(prob, eps=1e-9, max_iters=200000)   # on the quantised instance
+    assert ref["status"] == scs.SOLVED
+    info, x, y, s, _ = _solve(B, ctx, prob, eps=EPS)
+    _check_solution(prob, info, x, y, s, ref["pobj"])
+
+
+@pytest.mark.parametrize("storage", ["fp32", "bf16"])
+def test_sparse_lp_solution(B, ctx, storage):
+    prob = synth.lp(m_d=300, n_x=150, density=0.05, seed=synth.BASE_SEED + 4, storage=storage)
+    ref = scs.problem_solve(prob, eps=1e-9, max_iters=400000)
+    assert ref["status"] == scs.SOLVED
+    if storage == "fp32":
+        D = linop.densify(prob["A"]["parts"][0])
+        hi = so.linprog(prob["c"], A_ub=D, b_ub=prob["b"][:300], bounds=(0, None), method="highs")
+        assert objective_rel_err(ref["pobj"], hi.fun) <= 1e-7
+    info, x, y, s, _ = _solve(B, ctx, prob, eps=EPS)
+    _check_solution(prob, info, x, y, s, ref["pobj"])
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_mixed_cones_solution(B, ctx, seed):
+    rng = np.random.default_rng(400 + seed)
+    prob = synth.mixed_cone_problem(rng, n=8, soc_sizes=(3, 1, 5), z=2, l=4)
+    ref = scs.problem_solve(prob, eps=1e-10, max_iters=400000)
+    assert ref["status"] == scs.SOLVED
+    info, x, y, s, _ = _solve(B, ctx, prob, eps=EPS)
+    _check_solution(prob, info, x, y, s, ref["pobj"])
+
+
+def test_large_soc_spanning_many_chunks(B, ctx):
+    """A deconvolution whose single SOC block (9100 rows) spans several
+    projection chunks, so its norm is reduced across CTAs."""
+    prob = synth.deconv(n_x=8000, L=1100, seed=7)
+    ref = scs.problem_solve(prob, eps=EPS, max_iters=60, check_interval=10 ** 6, linsys="cg",
+                            cg_fixed_steps=2, trajectory=60)
+    P = B.cone_problem_create(ctx, prob)
+    N = prob["A"]["n"] + prob["A"]["m"] + 1
+    st = B.settings(max_iters=60, check_interval=10 ** 6, cg_fixed_iters=2)
+    uv = np.empty(2 * N)
+    info = B.cf_info()
+    B.check(B.lib.solve(P.h, B.C.byref(st), None, None, None, None, B._ptr(uv), B.C.byref(info)), "solve")
+    assert rel(uv[:N], ref["traj_u"][-1]) <= 1e-4
+    assert rel(uv[N:], ref["traj_v"][-1]) <= 1e-4
+
+
+# ---------------------------------------------------------------- certificates
+@pytest.mark.parametrize("seed", range(3))
+def test_infeasible_certificate(B, ctx, seed):
+    rng = np.random.default_rng(200 + seed)
+    D, b_d, c = synth.random_tiny_lp(rng, 3, 3, "infeasible")
+    prob = synth.dense_lp(D, b_d, c)
+    info, x, y, s, _ = _solve(B, ctx, prob, eps=1e-5, eps_infeas=1e-5)
+    assert info["status_name"] == "infeasible", info
+    A = linop.densify(prob["A"])
+    assert abs(prob["b"] @ y + 1.0) < 1e-6
+    assert cones.dist_to_dual_cone(y, prob["cone"]) <= 1e-6
+    assert np.linalg.norm(A.T @ y) <= 1e-4
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_unbounded_certificate(B, ctx, seed):
+    rng = np.random.default_rng(300 + seed)
+    D, b_d, c = synth.random_tiny_lp(rng, 3, 3, "unbounded")
+    prob = synth.dense_lp(D, b_d, c)
+    info, x, y, s, _ = _solve(B, ctx, prob, eps=1e-5, eps_infeas=1e-5)
+    assert info["status_name"] == "unbounded", info
+    A = linop.densify(prob["A"])
+    assert abs(prob["c"] @ x + 1.0) < 1e-6
+    assert np.linalg.norm(A @ x + s) <= 1e-4
+    assert cones.dist_to_cone(s, prob["cone"]) <= 1e-5
+
+
+# ---------------------------------------------------------------- edge cases
+def test_max_iters_and_warm_start_roundtrip(B, ctx):
+    prob = synth.deconv(n_x=200, L=20, seed=3)
+    P = B.cone_problem_create(ctx, prob)
+    N = prob["A"]["n"] + prob["A"]["m"] + 1
+    st = B.settings(max_iters=1)
+    info, *_ = B.solve(P, st)
+    assert info["iters"] == 1 and info["status_name"] == "max_iters" and info["checks"] == 1
+    # 7 iterations, then 5 more from the returned (u, v), equal 12 straight
+    # ones when each CG solve is exact (the CG warm start is not carried over)
+    def run(k, warm=None):
+        st = B.settings(max_iters=k, check_interval=10 ** 6, cg_fixed_iters=40)
+        uv = np.empty(2 * N)
+        info = B.cf_info()
+        B.check(B.lib.solve(P.h, B.C.byref(st), None, None, None, B._ptr(warm), B._ptr(uv),
+                            B.C.byref(info)), "solve")
+        assert info.iters == k
+        return uv
+    uv12 = run(12)
+    uv = run(5, run(7))
+    assert rel(uv, uv12) <= 1e-4
+
+
+def test_repeat_solves_are_bitwise_identical(B, ctx):
+    prob = synth.lasso(m_d=200, p=100, seed=11)
+    P = B.cone_problem_create(ctx, prob)
+    a = B.solve(P)
+    b = B.solve(P)
+    assert a[0]["iters"] == b[0]["iters"]
+    np.testing.assert_array_equal(a[1], b[1])
+    np.testing.assert_array_equal(a[2], b[2])
+
+
+def test_invalid_inputs(B, ctx):
+    prob = synth.deconv(n_x=50, L=5, seed=3)
+    op = B.build_operator(ctx, prob["A"])
+    with pytest.raises(B.CfError) as e:
+        B.Problem(ctx, op, prob["b"], prob["c"], {"z": 0, "l": 50, "q": [5]})
+    assert e.value.code == B.CF_E_INVALID
+    with pytest.raises(B.CfError):
+        B.Problem(ctx, op, prob["b"], prob["c"], {"z": 0, "l": 50, "q": [0, 55]})
+    P = B.Problem(ctx, op, prob["b"], prob["c"], prob["cone"])
+    for bad in (dict(alpha=2.5), dict(eps=0.0), dict(max_iters=0), dict(check_interval=0)):
+        with pytest.raises(B.CfError) as e:
+            B.solve(P, B.settings(**bad))
+        assert e.value.code == B.CF_E_INVALID
+    with pytest.raises(B.CfError):
+        B.operator_compose(ctx, "vstack", [B.cf_op_diag(ctx, 3), B.cf_op_diag(ctx, 4)])
+    with pytest.raises(B.CfError):
+        B.cf_op_csr(ctx, 2, 2, [0, 1, 2], [0, 5], [1.0, 1.0])
+
+
+def test_nan_data_reports_numerical(B, ctx):
+    prob = synth.deconv(n_x=50, L=5, seed=3)
+    k = prob["A"]["parts"][2]["parts"][0]["parts"][0]["kernel"].copy()
+    k[2] = np.nan
+    prob["A"]["parts"][2]["parts"][0]["parts"][0]["kernel"] = k
+    info, *_ = _solve(B, ctx, prob, max_iters=50)
+    assert info["status_name"] == "numerical", info
+
+
+# ---------------------------------------------------------------- regularized LS
+@pytest.mark.parametrize("kind", ["dense", "sparse", "conv"])
+def test_cg_solve_regularized_least_squares(B, ctx, kind):
+    """Section 5.1: x* = (lam I + A^T A)^{-1} A^T b by CG, paper's stop rule."""
+    rng = np.random.default_rng(21)
+    n, lam = 300, 0.5
+    if kind == "dense":
+        tree = synth.dense(rng.standard_normal((2 * n, n)).astype(np.float32))
+    elif kind == "sparse":
+        rp, col, val = synth.random_csr(rng, 2 * n, n, 0.01)
+        tree = synth.csr(2 * n, n, rp, col, val)
+    else:
+        tree = synth.conv1d(synth.gaussian_kernel(n, n / 10.0).astype(np.float32), n)
+    A = linop.densify(tree)
+    b = A @ rng.standard_normal(n) + 0.01 * rng.standard_normal(A.shape[0])
+    Atb = A.T @ b
+    G = lam * np.eye(n) + A.T @ A
+    x_star = np.linalg.solve(G, Atb)
+    op = B.build_operator(ctx, tree)
+    x, it, rn = B.cg_solve(op, lam, Atb.astype(np.float32), max_iters=2000, tol=1e-6)
+    assert 0 < it <= 2000
+    assert rn <= 1e-6 * np.linalg.norm(Atb.astype(np.float32)) * 1.001
+    true_res = np.linalg.norm(G @ x.astype(float) - Atb) / np.linalg.norm(Atb)
+    assert true_res <= 1e-5, true_res
+    assert rel(x, x_star) <= 1e-5 * np.linalg.cond(G), rel(x, x_star)
+
+
+# ---------------------------------------------------------------- batch / serve
+def _mix():
+    rng = np.random.default_rng(77)
+    return [synth.deconv(n_x=300, L=30, seed=1),
+            synth.lasso(m_d=300, p=150, seed=2, storage="bf16"),
+            synth.lp(m_d=200, n_x=100, density=0.05, seed=3),
+            synth.mixed_cone_problem(rng),
+            synth.deconv(n_x=1200, L=64, seed=4),
+            synth.lp(m_d=500, n_x=250, density=0.02, seed=5, storage="bf16")]
+
+
+def test_solve_batch_equals_solo(B, ctx):
+    probs = _mix()
+    Ps = [B.cone_problem_create(ctx, p) for p in probs]
+    solo = [B.solve(P) for P in Ps]
+    infos, xs, ys, ss = B.solve_batch(Ps)
+    for (i0, x0, y0, s0), i1, x1, y1, s1 in zip(solo, infos, xs, ys, ss):
+        assert i0["iters"] == i1["iters"] and i0["status"] == i1["status"]
+        np.testing.assert_array_equal(x0, x1)
+        np.testing.assert_array_equal(y0, y1)
+        np.testing.assert_array_equal(s0, s1)
+
+
+@pytest.mark.parametrize("slots,budget", [(3, 100 << 20), (8, 100 << 20), (4, 1 << 20)])
+def test_serving_equals_solo(B, ctx, slots, budget):
+    probs = _mix()
+    Ps = [B.cone_problem_create(ctx, p) for p in probs]
+    solo = [B.solve(P) for P in Ps]
+    srv = B.Server(ctx, budget, slots)
+    order = [0, 1, 2, 3, 4, 5, 4, 2, 0, 1]
+    tickets = [(i, srv.submit(Ps[i])) for i in order]
+    for i, t in tickets:
+        info, x, y, s = srv.wait(t, Ps[i])
+        assert info["iters"] == solo[i][0]["iters"]
+        np.testing.assert_array_equal(x, solo[i][1])
+        np.testing.assert_array_equal(y, solo[i][2])
+        np.testing.assert_array_equal(s, solo[i][3])
+    srv.close()
+
+
+def test_serving_rejects_oversized_and_times_out(B, ctx):
+    prob = synth.deconv(n_x=2000, L=100, seed=5)
+    P = B.cone_problem_create(ctx, prob)
+    srv = B.Server(ctx, 1 << 10, 2)
+    with pytest.raises(B.CfError) as e:
+        srv.submit(P)
+    assert e.value.code == B.CF_E_INVALID
+    srv.close()
+    srv = B.Server(ctx, 1 << 30, 1)
+    t = srv.submit(P, B.settings(max_iters=20000, eps=1e-12))
+    with pytest.raises(B.CfError) as e:
+        srv.wait(t, P, timeout_ns=1000)
+    assert e.value.code == B.CF_E_TIMEOUT
+    info, *_ = srv.wait(t, P)
+    assert info["status_name"] == "max_iters"
+    with pytest.raises(B.CfError) as e:
+        srv.wait(t, P, timeout_ns=0)
+    assert e.value.code == B.CF_E_STATE
+    srv.close()
