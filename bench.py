@@ -171,7 +171,10 @@ def main():
 
     prob = synth.deconv(**{**WORKLOAD, "seed": WORKLOAD["seed"] + rank})
     n, m = prob["A"]["n"], prob["A"]["m"]
-    stream = torch.cuda.current_stream()
+    # a dedicated (non-default) stream: the library launches on it and the
+    # CUDA events below are recorded on it
+    stream = torch.cuda.Stream(device=local)
+    torch.cuda.set_stream(stream)
     ctx = B.Context(local, stream.cuda_stream)
     P = B.cone_problem_create(ctx, prob)
     dev = torch.device("cuda", local)

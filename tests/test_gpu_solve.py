@@ -42,6 +42,12 @@ def _solve(B, ctx, prob, **kw):
     return info, x, y, s, P
 
 
+# Residuals <= 1e-4 do not by themselves put the objective within 1e-4 of the
+# optimum (the deconvolution at 1e-4 residuals is ~3e-4 off); solutions are
+# therefore computed to SOLVE_EPS and held to EPS on both counts.
+SOLVE_EPS = 1e-5
+
+
 def _check_solution(prob, info, x, y, s, p_star, eps=EPS):
     assert info["status_name"] == "solved", info
     pri, dual, gap = fp64_residuals(prob, x, y, s)
@@ -79,7 +85,7 @@ def test_deconv_solution(B, ctx, n_x, L):
     prob = synth.deconv(n_x=n_x, L=L, seed=synth.BASE_SEED + 1)
     K = linop.densify(prob["A"]["parts"][2]["parts"][0]["parts"][0])
     _, p_star = so.nnls(K, prob["meta"]["b_obs"], maxiter=50 * n_x)
-    info, x, y, s, _ = _solve(B, ctx, prob, eps=EPS)
+    info, x, y, s, _ = _solve(B, ctx, prob, eps=SOLVE_EPS)
     _check_solution(prob, info, x, y, s, p_star)
 
 
@@ -88,7 +94,7 @@ def test_lasso_solution(B, ctx, storage):
     prob = synth.lasso(m_d=400, p=200, seed=synth.BASE_SEED + 3, storage=storage)
     ref = scs.problem_solve(prob, eps=1e-9, max_iters=200000)   # on the quantised instance
     assert ref["status"] == scs.SOLVED
-    info, x, y, s, _ = _solve(B, ctx, prob, eps=EPS)
+    info, x, y, s, _ = _solve(B, ctx, prob, eps=SOLVE_EPS)
     _check_solution(prob, info, x, y, s, ref["pobj"])
 
 
@@ -101,7 +107,7 @@ def test_sparse_lp_solution(B, ctx, storage):
         D = linop.densify(prob["A"]["parts"][0])
         hi = so.linprog(prob["c"], A_ub=D, b_ub=prob["b"][:300], bounds=(0, None), method="highs")
         assert objective_rel_err(ref["pobj"], hi.fun) <= 1e-7
-    info, x, y, s, _ = _solve(B, ctx, prob, eps=EPS)
+    info, x, y, s, _ = _solve(B, ctx, prob, eps=SOLVE_EPS)
     _check_solution(prob, info, x, y, s, ref["pobj"])
 
 
@@ -111,7 +117,7 @@ def test_mixed_cones_solution(B, ctx, seed):
     prob = synth.mixed_cone_problem(rng, n=8, soc_sizes=(3, 1, 5), z=2, l=4)
     ref = scs.problem_solve(prob, eps=1e-10, max_iters=400000)
     assert ref["status"] == scs.SOLVED
-    info, x, y, s, _ = _solve(B, ctx, prob, eps=EPS)
+    info, x, y, s, _ = _solve(B, ctx, prob, eps=SOLVE_EPS)
     _check_solution(prob, info, x, y, s, ref["pobj"])
 
 
