@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--cpu-iters", type=int, default=6, help="ADMM iterations of the oracle sample")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="launch the same kernels from the host instead of one CUDA graph per solve "
+                         "(for profilers that cannot see kernels inside graph conditional nodes)")
     return ap.parse_args()
 
 
@@ -182,7 +185,7 @@ def main():
     yo = torch.empty(m, dtype=torch.float64, device=dev)
     so = torch.empty(m, dtype=torch.float64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    st = B.settings(max_iters=args.iters_per_step, eps=1e-4)
+    st = B.settings(max_iters=args.iters_per_step, eps=1e-4, host_loop=1 if args.host_loop else 0)
 
     def step():
         return B.solve(P, st, x=xo, y=yo, s=so)[0]

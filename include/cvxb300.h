@@ -103,6 +103,11 @@ typedef struct {
   double cg_tol_min;      /*   at ADMM iteration k (1e-9)                      */
   int32_t setup_cg_max_iters; /* CG cap for g = M^{-1} h at setup (2000) */
   double setup_cg_tol;        /* relative CG tolerance at setup (1e-7) */
+  int32_t host_loop;  /* 0: the whole solve is one CUDA graph whose loops run on
+                         the device (default).  1: the host launches the same
+                         kernels and reads each loop decision back (slower; for
+                         profilers that do not see kernels inside graph
+                         conditional nodes, and for debugging). */
 } cf_settings;
 
 typedef struct {

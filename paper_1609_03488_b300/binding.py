@@ -41,7 +41,8 @@ class cf_settings(C.Structure):
                 ("max_iters", C.c_int32), ("check_interval", C.c_int32),
                 ("cg_max_iters", C.c_int32), ("cg_fixed_iters", C.c_int32),
                 ("cg_tol_rel", C.c_double), ("cg_tol_exp", C.c_double), ("cg_tol_min", C.c_double),
-                ("setup_cg_max_iters", C.c_int32), ("setup_cg_tol", C.c_double)]
+                ("setup_cg_max_iters", C.c_int32), ("setup_cg_tol", C.c_double),
+                ("host_loop", C.c_int32)]
 
 
 class cf_info(C.Structure):

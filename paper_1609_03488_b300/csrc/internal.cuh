@@ -80,7 +80,7 @@ struct cf_op {
   int64_t nnz = 0;
   int32_t *rowptr = nullptr, *col = nullptr, *t_rowptr = nullptr, *t_col = nullptr;
   void *val = nullptr, *t_val = nullptr;
-  // conv1d: taps reversed and zero-padded to Lp (multiple of 8), for the
+  // conv1d: taps reversed and zero-padded to Lp (multiple of 16), for the
   // forward map and for the adjoint (whose taps are k reversed)
   int64_t L = 0, Lp = 0;
   float *w_fwd = nullptr, *w_adj = nullptr;

@@ -34,20 +34,49 @@ void launch_diag(cudaStream_t s, int64_t n, const float* d, float alpha, const f
 // ------------------------------------------------------------ 1-D convolution
 // out[i] = sum_{l < Lp} w[l] in[i + shift - l]  (in = 0 outside [0, n_in)),
 // given wrev[j] = w[Lp - 1 - j].  Forward full convolution: w = k, shift = 0;
-// adjoint (correlation): w = k reversed, shift = L - 1.
+// adjoint (correlation): w = k reversed, shift = Lp - 1.
 //
-// A CTA owns kConvTile consecutive outputs; each thread keeps kConvR
-// consecutive outputs in registers and slides a 2*kConvR input window over
-// the taps, so one 16-byte shared load feeds kConvR fused multiply-adds.
-// The shared input tile is padded by 4 floats every 32 so that the 16-byte
-// window loads of 8 neighbouring lanes (stride kConvR floats) hit distinct
-// banks.  Taps are processed in chunks of at most kConvChunk.
-constexpr int kConvThreads = 128;
-constexpr int kConvR = 8;
+// FP32 CUDA-core kernel (the operator is a matrix-vector product, not a
+// dense contraction).  A CTA owns kConvTile consecutive outputs; each thread
+// keeps kConvR consecutive outputs in registers.  For each block of kConvR
+// taps it loads kConvR new inputs (four 16-byte shared loads) into one of two
+// register windows that alternate roles, and the kConvR weights (four 16-byte
+// broadcast loads), then issues kConvR x kConvR fused multiply-adds: about 95%
+// of the issued instructions are FMAs.  Shared input element j lives at
+// j + 4 floor(j / kConvR): the 16-byte loads of 8 neighbouring lanes (stride
+// kConvR floats) then fall on distinct bank groups for every window offset.
+// Taps are processed in chunks of at most kConvChunk.
+constexpr int kConvThreads = 64;
+constexpr int kConvR = 16;
 constexpr int kConvTile = kConvThreads * kConvR;
 constexpr int kConvChunk = 2048;
 
-__device__ __forceinline__ int conv_pad(int j) { return j + ((j >> 5) << 2); }
+__host__ __device__ __forceinline__ int conv_pad(int j) { return j + ((j / kConvR) << 2); }
+
+// One block of kConvR taps: acc[r] += w[dd] * window[r + dd], where window is
+// lo[0..R) followed by hi[0..R).
+__device__ __forceinline__ void conv_block(float (&acc)[kConvR], const float (&lo)[kConvR],
+                                           const float (&hi)[kConvR], const float* __restrict__ wsm) {
+  float wv[kConvR];
+#pragma unroll
+  for (int q = 0; q < kConvR; q += 4) {
+    float4 t4 = *reinterpret_cast<const float4*>(wsm + q);
+    wv[q] = t4.x; wv[q + 1] = t4.y; wv[q + 2] = t4.z; wv[q + 3] = t4.w;
+  }
+#pragma unroll
+  for (int dd = 0; dd < kConvR; ++dd)
+#pragma unroll
+    for (int r = 0; r < kConvR; ++r)
+      acc[r] = fmaf(wv[dd], (r + dd < kConvR) ? lo[r + dd] : hi[r + dd - kConvR], acc[r]);
+}
+
+__device__ __forceinline__ void conv_load(float (&dst)[kConvR], const float* __restrict__ in_s, int j) {
+#pragma unroll
+  for (int q = 0; q < kConvR; q += 4) {
+    float4 t4 = *reinterpret_cast<const float4*>(in_s + conv_pad(j + q));
+    dst[q] = t4.x; dst[q + 1] = t4.y; dst[q + 2] = t4.z; dst[q + 3] = t4.w;
+  }
+}
 
 __global__ void __launch_bounds__(kConvThreads)
 k_conv1d(int64_t n_out, int64_t n_in, int64_t Lp, int64_t shift, const float* __restrict__ wrev,
@@ -76,31 +105,18 @@ k_conv1d(int64_t n_out, int64_t n_in, int64_t Lp, int64_t shift, const float* __
     __syncthreads();
 
     const int o = tid * kConvR;
-    float win[2 * kConvR];
-#pragma unroll
-    for (int q = 0; q < kConvR; q += 4) {
-      float4 t4 = *reinterpret_cast<const float4*>(&in_s[conv_pad(o + q)]);
-      win[q] = t4.x; win[q + 1] = t4.y; win[q + 2] = t4.z; win[q + 3] = t4.w;
+    float wa[kConvR], wb[kConvR];
+    conv_load(wa, in_s, o);
+    int mb = 0;
+    for (; mb + 2 * kConvR <= lc; mb += 2 * kConvR) {
+      conv_load(wb, in_s, o + mb + kConvR);
+      conv_block(accum, wa, wb, w_s + mb);
+      conv_load(wa, in_s, o + mb + 2 * kConvR);
+      conv_block(accum, wb, wa, w_s + mb + kConvR);
     }
-    for (int mb = 0; mb < lc; mb += kConvR) {
-#pragma unroll
-      for (int q = 0; q < kConvR; q += 4) {
-        float4 t4 = *reinterpret_cast<const float4*>(&in_s[conv_pad(o + mb + kConvR + q)]);
-        win[kConvR + q] = t4.x; win[kConvR + q + 1] = t4.y;
-        win[kConvR + q + 2] = t4.z; win[kConvR + q + 3] = t4.w;
-      }
-      float wv[kConvR];
-#pragma unroll
-      for (int q = 0; q < kConvR; q += 4) {
-        float4 t4 = *reinterpret_cast<const float4*>(&w_s[mb + q]);
-        wv[q] = t4.x; wv[q + 1] = t4.y; wv[q + 2] = t4.z; wv[q + 3] = t4.w;
-      }
-#pragma unroll
-      for (int dd = 0; dd < kConvR; ++dd)
-#pragma unroll
-        for (int r = 0; r < kConvR; ++r) accum[r] = fmaf(wv[dd], win[r + dd], accum[r]);
-#pragma unroll
-      for (int q = 0; q < kConvR; ++q) win[q] = win[kConvR + q];
+    if (mb < lc) {
+      conv_load(wb, in_s, o + mb + kConvR);
+      conv_block(accum, wa, wb, w_s + mb);
     }
   }
 #pragma unroll
@@ -116,9 +132,9 @@ k_conv1d(int64_t n_out, int64_t n_in, int64_t Lp, int64_t shift, const float* __
 void launch_conv1d(cudaStream_t s, int64_t n_out, int64_t n_in, int64_t Lp, int64_t shift,
                    const float* wrev, float alpha, const float* x, float* y, bool acc) {
   if (n_out <= 0) return;
-  int lc_max = (int)std::min<int64_t>(Lp, kConvChunk);
-  size_t smem = (size_t)(((kConvTile + lc_max + kConvR) + (((kConvTile + lc_max + kConvR) >> 5) << 2)) + 4 + lc_max) * sizeof(float);
-  int64_t grid = (n_out + kConvTile - 1) / kConvTile;
+  const int lc_max = (int)std::min<int64_t>(Lp, kConvChunk);
+  const size_t smem = (size_t)(conv_pad(kConvTile + lc_max + kConvR) + 4 + lc_max) * sizeof(float);
+  const int64_t grid = (n_out + kConvTile - 1) / kConvTile;
   k_conv1d<<<(unsigned)grid, kConvThreads, smem, s>>>(n_out, n_in, Lp, shift, wrev, alpha, x, y, acc);
 }
 

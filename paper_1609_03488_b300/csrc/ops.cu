@@ -345,7 +345,7 @@ cf_err cf_op_conv1d(cf_ctx* ctx, int64_t n, const float* kernel, int64_t L, cf_o
   CF_TRY(copy_any(k.data(), kernel, L * sizeof(float), ctx->stream));
   cf_op* op = new_op(ctx, OP_CONV1D, n + L - 1, n);
   op->L = L;
-  op->Lp = (int64_t)align_up((size_t)L, 8);
+  op->Lp = (int64_t)align_up((size_t)L, 16);
   // forward taps w = k padded with zeros to Lp; stored reversed.
   // adjoint taps w' = k reversed (w'[l] = k[L-1-l]); padding zeros at the end
   // shift nothing because the adjoint kernel is called with shift Lp - 1.

@@ -33,7 +33,8 @@ int64_t now_ns() {
       .count();
 }
 
-constexpr int kSocChunk = 2048;  // rows of a second-order cone per CTA
+constexpr int kSocChunk = 2048;        // rows of a second-order cone per CTA
+constexpr int kRefreshInterval = 50;   // ADMM iterations between exact G z_x, A z_x
 
 // ------------------------------------------------------------ reductions
 // Sum NV doubles over the block; thread 0 receives the totals.
@@ -103,16 +104,18 @@ __device__ bool grid_sum(double (&v)[NV], double* part, unsigned int* counter) {
 
 // ------------------------------------------------------------ iteration start
 __global__ void k_init(Ctl* c, int64_t n, int64_t m, float* ux, float* uy, float* vs, float* zx,
-                       const double* warm) {
+                       float* gz, float* az, const double* warm) {
   const bool w = c->st.warm != 0;
   const int64_t N = n + m + 1;
   GRID_STRIDE(i, n) {
     ux[i] = w ? (float)warm[i] : 0.f;
     zx[i] = 0.f;
+    gz[i] = 0.f;
   }
   GRID_STRIDE(i, m) {
     uy[i] = w ? (float)warm[n + i] : 0.f;
     vs[i] = w ? (float)warm[N + n + i] : 0.f;
+    az[i] = 0.f;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     c->tau = w ? warm[n + m] : 1.0;
@@ -120,6 +123,7 @@ __global__ void k_init(Ctl* c, int64_t n, int64_t m, float* ux, float* uy, float
     c->k = 0;
     c->cg_total = 0;
     c->checks = 0;
+    c->refreshes = 0;
     c->status = CF_MAX_ITERS;
     c->stop = 0;
     c->lam = 1.0;
@@ -138,15 +142,30 @@ __global__ void k_rhs(Ctl* c, int64_t n, int64_t m, const float* __restrict__ ux
 }
 
 // ------------------------------------------------------------ CG (Section 4.2)
-// r = rhs - (lam z + q) with q = A^T A z; p = r; stopping threshold.
+// CG on G z = rhs with G = lam I + A^T A.  gz holds G z for the current z and
+// az holds A z: both are carried along by the CG updates (gz += alpha G p,
+// az += alpha A p), so starting CG at the warm-start z needs no operator pass,
+// and neither does z_y = w_y + A z_x afterwards.  They are recomputed exactly
+// every kRefreshInterval ADMM iterations.
+//
+// Every kernel that decides a loop stores the decision in the control block
+// and, inside a graph, also sets the conditional node's value.
+
+// r = rhs - G z; p = r; stopping threshold.  fresh != 0: gz holds A^T A z
+// just computed, and G z = gz + lam z is formed (and kept) here.
 __global__ void k_cg_init(Ctl* c, int64_t n, const float* __restrict__ rhs,
-                          const float* __restrict__ z, const float* __restrict__ q,
+                          const float* __restrict__ z, float* __restrict__ gz,
                           float* __restrict__ r, float* __restrict__ p, double* part, int mode,
-                          cudaGraphConditionalHandle h) {
+                          int fresh, cudaGraphConditionalHandle h, int in_graph) {
   const float lam = (float)c->lam;
   double v[2] = {0.0, 0.0};
   GRID_STRIDE(i, n) {
-    float ri = rhs[i] - (lam * z[i] + q[i]);
+    float g = gz[i];
+    if (fresh) {
+      g = fmaf(lam, z[i], g);
+      gz[i] = g;
+    }
+    float ri = rhs[i] - g;
     r[i] = ri;
     p[i] = ri;
     v[0] += (double)ri * ri;
@@ -172,7 +191,8 @@ __global__ void k_cg_init(Ctl* c, int64_t n, const float* __restrict__ rhs,
     c->cg_it = 0;
     const int cont = fixed > 0 ? 1 : ((rr > c->tol2 && cap > 0) ? 1 : 0);
     c->cg_cont = cont;
-    cudaGraphSetConditional(h, (unsigned)cont);
+    c->cg_go = cont;
+    if (in_graph) cudaGraphSetConditional(h, (unsigned)cont);
   }
 }
 
@@ -192,17 +212,24 @@ __global__ void k_cg_dot(Ctl* c, int64_t n, const float* __restrict__ p, float* 
   }
 }
 
-// z += alpha p; r -= alpha q; beta = ||r_new||^2 / ||r||^2; continue test
-__global__ void k_cg_update(Ctl* c, int64_t n, float* __restrict__ z, float* __restrict__ r,
-                            const float* __restrict__ p, const float* __restrict__ q, double* part,
-                            int mode) {
+// z += alpha p; r -= alpha q; gz += alpha q; az += alpha t (t = A p; az may
+// be null); beta = ||r_new||^2 / ||r||^2; continue test
+__global__ void k_cg_update(Ctl* c, int64_t n, int64_t m, float* __restrict__ z, float* __restrict__ r,
+                            const float* __restrict__ p, const float* __restrict__ q,
+                            float* __restrict__ gz, float* __restrict__ az,
+                            const float* __restrict__ t, double* part, int mode) {
   const float a = (float)c->alpha_cg;
   double v[1] = {0.0};
   GRID_STRIDE(i, n) {
+    const float qi = q[i];
     z[i] = fmaf(a, p[i], z[i]);
-    float ri = fmaf(-a, q[i], r[i]);
+    gz[i] = fmaf(a, qi, gz[i]);
+    float ri = fmaf(-a, qi, r[i]);
     r[i] = ri;
     v[0] += (double)ri * ri;
+  }
+  if (az) {
+    GRID_STRIDE(i, m) az[i] = fmaf(a, t[i], az[i]);
   }
   if (grid_sum<1>(v, part, &c->red_count) && threadIdx.x == 0) {
     const double rr_new = v[0];
@@ -227,25 +254,32 @@ __global__ void k_cg_update(Ctl* c, int64_t n, float* __restrict__ z, float* __r
 // is advanced here by one thread, so the loop ends after at most `cap` steps
 // whatever the reductions produced.
 __global__ void k_cg_p(Ctl* c, int64_t n, const float* __restrict__ r, float* __restrict__ p,
-                       int mode, cudaGraphConditionalHandle h) {
+                       int mode, cudaGraphConditionalHandle h, int in_graph) {
   const float b = (float)c->beta_cg;
   GRID_STRIDE(i, n) p[i] = fmaf(b, p[i], r[i]);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     const int g = ++c->cg_guard;
     int cap = mode == CG_SETUP ? c->st.setup_cg_max : (c->st.cg_fixed > 0 ? c->st.cg_fixed : c->st.cg_max);
     const int cont = (c->cg_cont && g < cap) ? 1 : 0;
-    cudaGraphSetConditional(h, (unsigned)cont);
+    c->cg_go = cont;
+    if (in_graph) cudaGraphSetConditional(h, (unsigned)cont);
   }
 }
 
+// gz += lam z (after gz = A^T A z was recomputed exactly)
+__global__ void k_gz_shift(const Ctl* c, int64_t n, const float* __restrict__ z, float* __restrict__ gz) {
+  const float lam = (float)c->lam;
+  GRID_STRIDE(i, n) gz[i] = fmaf(lam, z[i], gz[i]);
+}
+
 // ------------------------------------------------------------ subspace step
-// z_y += w_y (z_y held A z_x); u~_tau = (w_tau + c^T z_x + b^T z_y) / (1 + h^T g)
+// z_y = w_y + A z_x (A z_x carried in az); u~_tau = (w_tau + c^T z_x + b^T z_y) / (1 + h^T g)
 __global__ void k_utau(Ctl* c, int64_t n, int64_t m, const float* __restrict__ zx,
-                       float* __restrict__ zy, const float* __restrict__ wy,
+                       const float* __restrict__ az, float* __restrict__ zy, const float* __restrict__ wy,
                        const float* __restrict__ bf, const float* __restrict__ cf, double* part) {
   double v[1] = {0.0};
   GRID_STRIDE(i, m) {
-    float zi = zy[i] + wy[i];
+    float zi = az[i] + wy[i];
     zy[i] = zi;
     v[0] += (double)bf[i] * zi;
   }
@@ -303,7 +337,8 @@ __global__ void k_apply(Ctl* c, int64_t n, int64_t m, int64_t z, int64_t l, int 
                         const int64_t* __restrict__ chunk_r1, const int64_t* __restrict__ seg_head,
                         const int32_t* __restrict__ seg_c0, const int32_t* __restrict__ seg_nc,
                         const double* __restrict__ chunk_n2, const double* __restrict__ seg_p0,
-                        cudaGraphConditionalHandle h_check) {
+                        cudaGraphConditionalHandle h_check, cudaGraphConditionalHandle h_refresh,
+                        int in_graph) {
   const double al = c->st.alpha;
   const float a = (float)al, a1 = (float)(1.0 - al), ut = (float)c->ut_tau;
   if ((int)blockIdx.x < nlin) {
@@ -329,7 +364,14 @@ __global__ void k_apply(Ctl* c, int64_t n, int64_t m, int64_t z, int64_t l, int 
       const int k = c->k + 1;
       c->k = k;
       const int chk = (k % c->st.check_interval == 0) || (k >= c->st.max_iters);
-      cudaGraphSetConditional(h_check, (unsigned)chk);
+      const int ref = (k % kRefreshInterval == 0) && (k < c->st.max_iters);
+      c->do_check = chk;
+      c->do_refresh = ref;
+      c->refreshes += ref;
+      if (in_graph) {
+        cudaGraphSetConditional(h_check, (unsigned)chk);
+        cudaGraphSetConditional(h_refresh, (unsigned)ref);
+      }
     }
     return;
   }
@@ -427,22 +469,26 @@ __global__ void k_resid(Ctl* c, int64_t n, int64_t m, const float* __restrict__ 
   }
 }
 
-__global__ void k_outer(Ctl* c, cudaGraphConditionalHandle h) {
+__global__ void k_outer(Ctl* c, cudaGraphConditionalHandle h, int in_graph) {
   int cont = 1;
   if (!isfinite(c->tau) || !isfinite(c->kappa)) {
     c->status = CF_NUMERICAL;
     c->stop = 1;
   }
   if (c->stop || c->k >= c->st.max_iters) cont = 0;
-  cudaGraphSetConditional(h, (unsigned)cont);
+  c->outer_go = cont;
+  if (in_graph) cudaGraphSetConditional(h, (unsigned)cont);
 }
 
 // ------------------------------------------------------------ setup kernels
-__global__ void k_setup_init(Ctl* c, int64_t n, float* gx, float* rhs, const float* cf) {
+__global__ void k_setup_init(Ctl* c, int64_t n, int64_t m, float* gx, float* gz, float* az, float* rhs,
+                             const float* cf) {
   GRID_STRIDE(i, n) {
     gx[i] = 0.f;
+    gz[i] = 0.f;
     rhs[i] = cf[i];
   }
+  GRID_STRIDE(i, m) az[i] = 0.f;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     c->lam = 1.0;
     c->setup_iters = 0;
@@ -565,9 +611,17 @@ int count_kernels(cudaGraph_t g) {
 struct CgBufs {
   Ctl* ctl;
   const cf_op* A;
-  int64_t n;
+  int64_t n, m;
   float *z, *rhs, *r, *p, *q, *t, *ws;
+  float *gz, *az;  // G z and A z carried along (az may be null)
   double* part;
+};
+
+// Loop-decision handles of the graph being captured; in_graph == 0 when the
+// kernels are launched directly by the host-driven loop.
+struct Conds {
+  cudaGraphConditionalHandle outer = 0, cg = 0, check = 0, refresh = 0;
+  int in_graph = 1;
 };
 
 // Gram pass out = A^T A x (the CG kernels add lam x).
@@ -576,49 +630,110 @@ void gram(const CgBufs& b, const float* x, float* out, cudaStream_t s) {
   op_apply(b.A, true, 1.f, b.t, out, false, b.ws, s);
 }
 
-// CG start: r = rhs - (lam z + A^T A z), p = r, threshold, loop decision.
-void cg_start(const CgBufs& b, int mode, cudaGraphConditionalHandle h, cudaStream_t s) {
-  gram(b, b.z, b.q, s);
-  k_cg_init<<<grid_for(b.n), kThreads, 0, s>>>(b.ctl, b.n, b.rhs, b.z, b.q, b.r, b.p, b.part, mode, h);
+// CG start at z with gz = G z already known (fresh = 0) or computed here
+// from scratch (fresh = 1).
+void emit_cg_start(const CgBufs& b, int mode, int fresh, const Conds& cd, cudaStream_t s) {
+  if (fresh) gram(b, b.z, b.gz, s);
+  k_cg_init<<<grid_for(b.n), kThreads, 0, s>>>(b.ctl, b.n, b.rhs, b.z, b.gz, b.r, b.p, b.part, mode, fresh,
+                                               cd.cg, cd.in_graph);
 }
 
-// One CG step as a captured sequence (body of a WHILE node).
-void cg_step(const CgBufs& b, int mode, cudaGraphConditionalHandle h, cudaStream_t s) {
+// One CG step (body of the CG WHILE node).
+void emit_cg_step(const CgBufs& b, int mode, const Conds& cd, cudaStream_t s) {
   gram(b, b.p, b.q, s);
   k_cg_dot<<<grid_for(b.n), kThreads, 0, s>>>(b.ctl, b.n, b.p, b.q, b.part);
-  k_cg_update<<<grid_for(b.n), kThreads, 0, s>>>(b.ctl, b.n, b.z, b.r, b.p, b.q, b.part, mode);
-  k_cg_p<<<grid_for(b.n), kThreads, 0, s>>>(b.ctl, b.n, b.r, b.p, mode, h);
+  k_cg_update<<<grid_for(b.n), kThreads, 0, s>>>(b.ctl, b.n, b.m, b.z, b.r, b.p, b.q, b.gz, b.az, b.t,
+                                                 b.part, mode);
+  k_cg_p<<<grid_for(b.n), kThreads, 0, s>>>(b.ctl, b.n, b.r, b.p, mode, cd.cg, cd.in_graph);
 }
 
 CgBufs cg_bufs(cf_problem* P, float* z) {
-  return CgBufs{P->ctl, P->A, P->n, z, P->rhs, P->r, P->p, P->qv, P->t, P->ws, P->part};
+  return CgBufs{P->ctl, P->A, P->n, P->m, z, P->rhs, P->r, P->p, P->qv, P->t, P->ws, P->gz, P->az, P->part};
+}
+
+// ---- the pieces of the setup and of one ADMM iteration
+void emit_setup_pre(cf_problem* P, const Conds& cd, cudaStream_t s) {
+  const int64_t n = P->n, m = P->m;
+  k_setup_init<<<grid_for(std::max(n, m)), kThreads, 0, s>>>(P->ctl, n, m, P->gx, P->gz, P->az, P->rhs, P->cf);
+  op_apply(P->A, true, -1.f, P->bf, P->rhs, true, P->ws, s);  // rhs = c - A^T b
+  emit_cg_start(cg_bufs(P, P->gx), CG_SETUP, 0, cd, s);        // g_x = 0, G g_x = 0
+}
+
+void emit_setup_post(cf_problem* P, cudaStream_t s) {
+  const int64_t n = P->n, m = P->m;
+  op_apply(P->A, false, 1.f, P->gx, P->gy, false, P->ws, s);  // exact A g_x
+  k_setup_fin<<<grid_for(std::max(n, m)), kThreads, 0, s>>>(P->ctl, n, m, P->gx, P->gy, P->bf, P->cf, P->part);
+}
+
+void emit_init(cf_problem* P, cudaStream_t s) {
+  const int64_t n = P->n, m = P->m;
+  k_init<<<grid_for(std::max(n, m)), kThreads, 0, s>>>(P->ctl, n, m, P->ux, P->uy, P->vs, P->zx, P->gz, P->az,
+                                                       P->warm_dev);
+}
+
+// w = u + v; rhs = w_x - A^T w_y; CG start at the previous z_x
+void emit_pre_cg(cf_problem* P, const Conds& cd, cudaStream_t s) {
+  const int64_t n = P->n, m = P->m;
+  k_rhs<<<grid_for(std::max(n, m)), kThreads, 0, s>>>(P->ctl, n, m, P->ux, P->uy, P->vs, P->wy, P->rhs);
+  op_apply(P->A, true, -1.f, P->wy, P->rhs, true, P->ws, s);
+  emit_cg_start(cg_bufs(P, P->zx), CG_ITER, 0, cd, s);
+}
+
+// subspace step, projection, dual update
+void emit_post_cg(cf_problem* P, const Conds& cd, cudaStream_t s) {
+  const int64_t n = P->n, m = P->m;
+  k_utau<<<grid_for(std::max(n, m)), kThreads, 0, s>>>(P->ctl, n, m, P->zx, P->az, P->zy, P->wy, P->bf, P->cf,
+                                                       P->part);
+  if (P->nchunk > 0)
+    k_soc_norm<<<(unsigned)P->nchunk, kThreads, 0, s>>>(P->ctl, 0, P->chunk_seg, P->chunk_r0, P->chunk_r1,
+                                                        P->seg_head, P->zy, P->gy, P->uy, P->vs,
+                                                        P->chunk_n2, P->seg_p0);
+  const int nlin = grid_for(n + P->z + P->l);
+  k_apply<<<(unsigned)(nlin + P->nchunk), kThreads, 0, s>>>(
+      P->ctl, n, m, P->z, P->l, nlin, P->ux, P->uy, P->vs, P->zx, P->zy, P->gx, P->gy, P->chunk_seg,
+      P->chunk_r0, P->chunk_r1, P->seg_head, P->seg_c0, P->seg_nc, P->chunk_n2, P->seg_p0, cd.check,
+      cd.refresh, cd.in_graph);
+}
+
+// residuals and certificates (every check_interval iterations)
+void emit_check(cf_problem* P, cudaStream_t s) {
+  const int64_t n = P->n, m = P->m;
+  op_apply(P->A, false, 1.f, P->ux, P->cm, false, P->ws, s);
+  op_apply(P->A, true, 1.f, P->uy, P->cn, false, P->ws, s);
+  k_resid<<<grid_for(std::max(n, m)), kThreads, 0, s>>>(P->ctl, n, m, P->cm, P->cn, P->ux, P->uy, P->vs,
+                                                        P->bf, P->cf, P->part);
+}
+
+// exact A z_x and G z_x (every kRefreshInterval iterations)
+void emit_refresh(cf_problem* P, cudaStream_t s) {
+  op_apply(P->A, false, 1.f, P->zx, P->az, false, P->ws, s);
+  op_apply(P->A, true, 1.f, P->az, P->gz, false, P->ws, s);
+  k_gz_shift<<<grid_for(P->n), kThreads, 0, s>>>(P->ctl, P->n, P->zx, P->gz);
+}
+
+void emit_outer(cf_problem* P, const Conds& cd, cudaStream_t s) {
+  k_outer<<<1, 32, 0, s>>>(P->ctl, cd.outer, cd.in_graph);
 }
 
 cf_err build_setup_graph(cf_problem* P) {
   cudaStream_t s = P->stream;
-  const int64_t n = P->n, m = P->m;
   cudaGraph_t G;
   CF_CUDA(cudaGraphCreate(&G, 0));
   P->setup_graph = G;
-  cudaGraphConditionalHandle h;
-  CF_CUDA(cudaGraphConditionalHandleCreate(&h, G, 0, 0));
+  Conds cd;
+  CF_CUDA(cudaGraphConditionalHandleCreate(&cd.cg, G, 0, 0));
   std::vector<cudaGraphNode_t> tail, tmp;
   CF_TRY(seg_begin(s, G, {}));
-  k_setup_init<<<grid_for(n), kThreads, 0, s>>>(P->ctl, n, P->gx, P->rhs, P->cf);
-  op_apply(P->A, true, -1.f, P->bf, P->rhs, true, P->ws, s);  // rhs = c - A^T b
-  const CgBufs cb = cg_bufs(P, P->gx);
-  cg_start(cb, CG_SETUP, h, s);
+  emit_setup_pre(P, cd, s);
   CF_TRY(seg_end(s, &tail));
   cudaGraphNode_t wn;
   cudaGraph_t body = nullptr;
-  CF_TRY(add_cond(G, tail, h, cudaGraphCondTypeWhile, &wn, &body));
+  CF_TRY(add_cond(G, tail, cd.cg, cudaGraphCondTypeWhile, &wn, &body));
   CF_TRY(seg_begin(s, body, {}));
-  cg_step(cb, CG_SETUP, h, s);
+  emit_cg_step(cg_bufs(P, P->gx), CG_SETUP, cd, s);
   CF_TRY(seg_end(s, &tmp));
   CF_TRY(seg_begin(s, G, {wn}));
-  op_apply(P->A, false, 1.f, P->gx, P->gy, false, P->ws, s);
-  k_setup_fin<<<grid_for(std::max(n, m)), kThreads, 0, s>>>(P->ctl, n, m, P->gx, P->gy, P->bf, P->cf,
-                                                            P->part);
+  emit_setup_post(P, s);
   CF_TRY(seg_end(s, &tmp));
   CF_CUDA(cudaGetLastError());
   P->skc.top = count_kernels(G);
@@ -629,69 +744,125 @@ cf_err build_setup_graph(cf_problem* P) {
 
 cf_err build_iter_graph(cf_problem* P) {
   cudaStream_t s = P->stream;
-  const int64_t n = P->n, m = P->m;
   cudaGraph_t G;
   CF_CUDA(cudaGraphCreate(&G, 0));
   P->graph = G;
-  cudaGraphConditionalHandle h_outer;
-  CF_CUDA(cudaGraphConditionalHandleCreate(&h_outer, G, 1, cudaGraphCondAssignDefault));
+  Conds cd;
+  CF_CUDA(cudaGraphConditionalHandleCreate(&cd.outer, G, 1, cudaGraphCondAssignDefault));
   std::vector<cudaGraphNode_t> tail, tmp;
-  // top: reset state
   CF_TRY(seg_begin(s, G, {}));
-  k_init<<<grid_for(std::max(n, m)), kThreads, 0, s>>>(P->ctl, n, m, P->ux, P->uy, P->vs, P->zx,
-                                                       P->warm_dev);
+  emit_init(P, s);
   CF_TRY(seg_end(s, &tail));
   cudaGraphNode_t wn;
   cudaGraph_t B = nullptr;
-  CF_TRY(add_cond(G, tail, h_outer, cudaGraphCondTypeWhile, &wn, &B));
-  cudaGraphConditionalHandle h_cg, h_chk;
-  CF_CUDA(cudaGraphConditionalHandleCreate(&h_cg, B, 0, 0));
-  CF_CUDA(cudaGraphConditionalHandleCreate(&h_chk, B, 0, 0));
-  // body part 1: right-hand side, CG start
+  CF_TRY(add_cond(G, tail, cd.outer, cudaGraphCondTypeWhile, &wn, &B));
+  CF_CUDA(cudaGraphConditionalHandleCreate(&cd.cg, B, 0, 0));
+  CF_CUDA(cudaGraphConditionalHandleCreate(&cd.check, B, 0, 0));
+  CF_CUDA(cudaGraphConditionalHandleCreate(&cd.refresh, B, 0, 0));
+  // body: rhs and CG start, CG loop, subspace step + projection, check,
+  // refresh, loop decision
   CF_TRY(seg_begin(s, B, {}));
-  k_rhs<<<grid_for(std::max(n, m)), kThreads, 0, s>>>(P->ctl, n, m, P->ux, P->uy, P->vs, P->wy, P->rhs);
-  op_apply(P->A, true, -1.f, P->wy, P->rhs, true, P->ws, s);  // rhs = w_x - A^T w_y
-  const CgBufs cb = cg_bufs(P, P->zx);
-  cg_start(cb, CG_ITER, h_cg, s);
+  emit_pre_cg(P, cd, s);
   CF_TRY(seg_end(s, &tail));
   cudaGraphNode_t cgn;
   cudaGraph_t C = nullptr;
-  CF_TRY(add_cond(B, tail, h_cg, cudaGraphCondTypeWhile, &cgn, &C));
+  CF_TRY(add_cond(B, tail, cd.cg, cudaGraphCondTypeWhile, &cgn, &C));
   CF_TRY(seg_begin(s, C, {}));
-  cg_step(cb, CG_ITER, h_cg, s);
+  emit_cg_step(cg_bufs(P, P->zx), CG_ITER, cd, s);
   CF_TRY(seg_end(s, &tmp));
-  // body part 2: subspace step, projection, dual update
   CF_TRY(seg_begin(s, B, {cgn}));
-  op_apply(P->A, false, 1.f, P->zx, P->zy, false, P->ws, s);  // z_y = A z_x (+ w_y in k_utau)
-  k_utau<<<grid_for(std::max(n, m)), kThreads, 0, s>>>(P->ctl, n, m, P->zx, P->zy, P->wy, P->bf, P->cf,
-                                                       P->part);
-  if (P->nchunk > 0)
-    k_soc_norm<<<(unsigned)P->nchunk, kThreads, 0, s>>>(P->ctl, 0, P->chunk_seg, P->chunk_r0, P->chunk_r1,
-                                                        P->seg_head, P->zy, P->gy, P->uy, P->vs,
-                                                        P->chunk_n2, P->seg_p0);
-  const int nlin = grid_for(n + P->z + P->l);
-  k_apply<<<(unsigned)(nlin + P->nchunk), kThreads, 0, s>>>(
-      P->ctl, n, m, P->z, P->l, nlin, P->ux, P->uy, P->vs, P->zx, P->zy, P->gx, P->gy, P->chunk_seg,
-      P->chunk_r0, P->chunk_r1, P->seg_head, P->seg_c0, P->seg_nc, P->chunk_n2, P->seg_p0, h_chk);
+  emit_post_cg(P, cd, s);
   CF_TRY(seg_end(s, &tail));
   cudaGraphNode_t ifn;
   cudaGraph_t D = nullptr;
-  CF_TRY(add_cond(B, tail, h_chk, cudaGraphCondTypeIf, &ifn, &D));
+  CF_TRY(add_cond(B, tail, cd.check, cudaGraphCondTypeIf, &ifn, &D));
   CF_TRY(seg_begin(s, D, {}));
-  op_apply(P->A, false, 1.f, P->ux, P->cm, false, P->ws, s);
-  op_apply(P->A, true, 1.f, P->uy, P->cn, false, P->ws, s);
-  k_resid<<<grid_for(std::max(n, m)), kThreads, 0, s>>>(P->ctl, n, m, P->cm, P->cn, P->ux, P->uy, P->vs,
-                                                        P->bf, P->cf, P->part);
+  emit_check(P, s);
   CF_TRY(seg_end(s, &tmp));
-  CF_TRY(seg_begin(s, B, {ifn}));
-  k_outer<<<1, 32, 0, s>>>(P->ctl, h_outer);
+  cudaGraphNode_t rfn;
+  cudaGraph_t R = nullptr;
+  CF_TRY(add_cond(B, {ifn}, cd.refresh, cudaGraphCondTypeIf, &rfn, &R));
+  CF_TRY(seg_begin(s, R, {}));
+  emit_refresh(P, s);
+  CF_TRY(seg_end(s, &tmp));
+  CF_TRY(seg_begin(s, B, {rfn}));
+  emit_outer(P, cd, s);
   CF_TRY(seg_end(s, &tmp));
   CF_CUDA(cudaGetLastError());
   P->kc.top = count_kernels(G);
   P->kc.body = count_kernels(B);
   P->kc.cg = count_kernels(C);
   P->kc.check = count_kernels(D);
+  P->kc.refresh = count_kernels(R);
   CF_CUDA(cudaGraphInstantiate(&P->exec, G, 0));
+  return CF_OK;
+}
+
+// ---- host-driven execution of the same kernels (no graph)
+struct Flags {
+  int cg_go, do_check, do_refresh, outer_go;
+};
+
+// Read the loop decisions the kernels stored (one small copy and a wait).
+cf_err read_flags(cf_problem* P, Flags* f) {
+  CF_CUDA(cudaMemcpyAsync(P->flags_host, &P->ctl->cg_go, sizeof(Flags), cudaMemcpyDeviceToHost, P->stream));
+  CF_CUDA(cudaStreamSynchronize(P->stream));
+  std::memcpy(f, P->flags_host, sizeof(Flags));
+  return CF_OK;
+}
+
+// Runs the setup CG loop from the host; the loop is also capped on the host.
+cf_err run_setup_host(cf_problem* P, int64_t* launches) {
+  cudaStream_t s = P->stream;
+  Conds cd;
+  cd.in_graph = 0;
+  const CgBufs cb = cg_bufs(P, P->gx);
+  Flags f;
+  int steps = 0;
+  emit_setup_pre(P, cd, s);
+  CF_CUDA(cudaGetLastError());
+  CF_TRY(read_flags(P, &f));
+  while (f.cg_go && steps < P->ctl_host->st.setup_cg_max) {
+    emit_cg_step(cb, CG_SETUP, cd, s);
+    CF_CUDA(cudaGetLastError());
+    CF_TRY(read_flags(P, &f));
+    ++steps;
+  }
+  emit_setup_post(P, s);
+  CF_CUDA(cudaGetLastError());
+  *launches += P->skc.top + (int64_t)steps * P->skc.cg;
+  return CF_OK;
+}
+
+// Runs the ADMM iterations from the host: identical kernels, with each loop
+// decision read back instead of evaluated by a conditional graph node.
+cf_err run_iterations_host(cf_problem* P) {
+  cudaStream_t s = P->stream;
+  Conds cd;
+  cd.in_graph = 0;
+  const CgBufs cb = cg_bufs(P, P->zx);
+  const Settings& st = P->ctl_host->st;
+  const int cg_cap = st.cg_fixed > 0 ? st.cg_fixed : st.cg_max;
+  Flags f;
+  emit_init(P, s);
+  for (int it = 0; it < st.max_iters; ++it) {
+    emit_pre_cg(P, cd, s);
+    CF_CUDA(cudaGetLastError());
+    CF_TRY(read_flags(P, &f));
+    for (int k = 0; f.cg_go && k < cg_cap; ++k) {
+      emit_cg_step(cb, CG_ITER, cd, s);
+      CF_CUDA(cudaGetLastError());
+      CF_TRY(read_flags(P, &f));
+    }
+    emit_post_cg(P, cd, s);
+    CF_TRY(read_flags(P, &f));
+    if (f.do_check) emit_check(P, s);
+    if (f.do_refresh) emit_refresh(P, s);
+    emit_outer(P, cd, s);
+    CF_CUDA(cudaGetLastError());
+    CF_TRY(read_flags(P, &f));
+    if (!f.outer_go) break;
+  }
   return CF_OK;
 }
 
@@ -704,8 +875,8 @@ size_t problem_state_bytes(const cf_problem* P) {
   auto d = [](size_t k) { return align_up(k * sizeof(double), 256); };
   size_t wsf = std::max(op_ws_floats(P->A, false), op_ws_floats(P->A, true));
   size_t b = 0;
-  b += 8 * f(n);            // ux zx rhs r p q gx cn
-  b += 7 * f(m);            // uy vs wy t zy gy cm
+  b += 9 * f(n);            // ux zx rhs r p q gx cn gz
+  b += 8 * f(m);            // uy vs wy t zy gy cm az
   b += f(wsf);
   b += d((size_t)kMaxRedBlocks * kRedSlots);
   b += d((size_t)std::max<int64_t>(P->nchunk, 1)) + d((size_t)std::max<int64_t>(P->nseg, 1));
@@ -734,6 +905,7 @@ cf_err ensure_state(cf_problem* P) {
   P->p = takef(n); P->qv = takef(n); P->gx = takef(n); P->cn = takef(n);
   P->uy = takef(m); P->vs = takef(m); P->wy = takef(m); P->t = takef(m);
   P->zy = takef(m); P->gy = takef(m); P->cm = takef(m);
+  P->gz = takef(n); P->az = takef(m);
   P->ws = takef(std::max(op_ws_floats(P->A, false), op_ws_floats(P->A, true)));
   P->part = taked((size_t)kMaxRedBlocks * kRedSlots);
   P->chunk_n2 = taked((size_t)std::max<int64_t>(P->nchunk, 1));
@@ -780,6 +952,7 @@ bool settings_valid(const cf_settings* st, std::string* why) {
   if (!(st->setup_cg_tol > 0)) return bad("setup_cg_tol must be > 0");
   if (!(st->cg_tol_rel >= 0) || !(st->cg_tol_min >= 0) || !std::isfinite(st->cg_tol_exp))
     return bad("CG tolerance parameters must be >= 0");
+  if (st->host_loop != 0 && st->host_loop != 1) return bad("host_loop must be 0 or 1");
   return true;
 }
 
@@ -800,10 +973,15 @@ static void write_settings(cf_problem* P, const cf_settings* st, bool warm) {
   s.warm = warm ? 1 : 0;
 }
 
-static cf_err run_setup(cf_problem* P) {
-  if (!P->setup_exec) CF_TRY(build_setup_graph(P));
+static cf_err run_setup(cf_problem* P, bool host_loop) {
+  if (!P->setup_exec) CF_TRY(build_setup_graph(P));  // also gives the kernel counts
   CF_CUDA(cudaMemcpyAsync(&P->ctl->st, &P->ctl_host->st, sizeof(Settings), cudaMemcpyHostToDevice, P->stream));
-  CF_CUDA(cudaGraphLaunch(P->setup_exec, P->stream));
+  if (host_loop) {
+    int64_t dummy = 0;
+    CF_TRY(run_setup_host(P, &dummy));
+  } else {
+    CF_CUDA(cudaGraphLaunch(P->setup_exec, P->stream));
+  }
   CF_CUDA(cudaMemcpyAsync(P->ctl_host, P->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, P->stream));
   CF_CUDA(cudaStreamSynchronize(P->stream));
   P->setup_iters_last = P->ctl_host->setup_iters;
@@ -828,7 +1006,7 @@ cf_err solve_launch(cf_problem* P, const cf_settings* st_in, double* x, double* 
   CF_CUDA(cudaEventRecord(P->ev_in, P->ctx->stream));
   CF_CUDA(cudaStreamWaitEvent(P->stream, P->ev_in, 0));
   if (!P->setup_done) {
-    CF_TRY(run_setup(P));
+    CF_TRY(run_setup(P, st.host_loop != 0));
     P->ran_setup = true;
     P->setup_ns_last = now_ns() - t0;
   } else {
@@ -839,7 +1017,10 @@ cf_err solve_launch(cf_problem* P, const cf_settings* st_in, double* x, double* 
   if (warm_uv) CF_TRY(copy_any(P->warm_dev, warm_uv, 2 * N * sizeof(double), P->stream));
   CF_CUDA(cudaMemcpyAsync(&P->ctl->st, &P->ctl_host->st, sizeof(Settings), cudaMemcpyHostToDevice, P->stream));
   P->t_launch = now_ns();
-  CF_CUDA(cudaGraphLaunch(P->exec, P->stream));
+  if (st.host_loop)
+    CF_TRY(run_iterations_host(P));
+  else
+    CF_CUDA(cudaGraphLaunch(P->exec, P->stream));
   P->x_out = x;
   P->y_out = y;
   P->s_out = s;
@@ -888,7 +1069,7 @@ cf_err solve_finish(cf_problem* P, cf_info* info) {
     info->setup_ns = P->setup_ns_last;
     info->solve_ns = t1 - P->t_launch;
     int64_t kl = P->kc.top + (int64_t)c.k * P->kc.body + c.cg_total * P->kc.cg +
-                 (int64_t)c.checks * P->kc.check;
+                 (int64_t)c.checks * P->kc.check + (int64_t)c.refreshes * P->kc.refresh;
     if (P->x_out || P->y_out || P->s_out) kl += 1;
     if (P->uv_out) kl += 1;
     if (P->ran_setup) kl += P->skc.top + (int64_t)P->setup_iters_last * P->skc.cg;
@@ -913,7 +1094,7 @@ cf_err cg_solve_impl(cf_op* A, double lam, const float* rhs_in, float* x, int32_
   const int64_t n = A->n, m = A->m;
   const size_t wsf = std::max(op_ws_floats(A, false), op_ws_floats(A, true));
   auto f = [](size_t k) { return align_up(k * sizeof(float), 256); };
-  const size_t bytes = 5 * f(n) + f(m) + f(wsf) +
+  const size_t bytes = 6 * f(n) + f(m) + f(wsf) +
                        align_up(sizeof(double) * kMaxRedBlocks * kRedSlots, 256) + align_up(sizeof(Ctl), 256);
   char* arena = nullptr;
   cudaError_t e = cudaMalloc((void**)&arena, bytes);
@@ -926,11 +1107,14 @@ cf_err cg_solve_impl(cf_op* A, double lam, const float* rhs_in, float* x, int32_
   CgBufs b;
   b.A = A;
   b.n = n;
+  b.m = m;
   b.z = (float*)take(n * 4);
   b.rhs = (float*)take(n * 4);
   b.r = (float*)take(n * 4);
   b.p = (float*)take(n * 4);
   b.q = (float*)take(n * 4);
+  b.gz = (float*)take(n * 4);
+  b.az = nullptr;
   b.t = (float*)take(m * 4);
   b.ws = (float*)take(wsf * 4);
   b.part = (double*)take(sizeof(double) * kMaxRedBlocks * kRedSlots);
@@ -947,18 +1131,18 @@ cf_err cg_solve_impl(cf_op* A, double lam, const float* rhs_in, float* x, int32_
     CF_TRY(copy_any(b.rhs, rhs_in, n * sizeof(float), s));
     CF_TRY(copy_any(b.z, x, n * sizeof(float), s));
     CF_CUDA(cudaGraphCreate(&G, 0));
-    cudaGraphConditionalHandle h;
-    CF_CUDA(cudaGraphConditionalHandleCreate(&h, G, 0, 0));
+    Conds cd;
+    CF_CUDA(cudaGraphConditionalHandleCreate(&cd.cg, G, 0, 0));
     std::vector<cudaGraphNode_t> tail, tmp;
     CF_TRY(seg_begin(s, G, {}));
     k_cg_solo_init<<<1, 1, 0, s>>>(b.ctl, lam, tol, max_iters);
-    cg_start(b, CG_SETUP, h, s);
+    emit_cg_start(b, CG_SETUP, 1, cd, s);
     CF_TRY(seg_end(s, &tail));
     cudaGraphNode_t wn;
     cudaGraph_t body = nullptr;
-    CF_TRY(add_cond(G, tail, h, cudaGraphCondTypeWhile, &wn, &body));
+    CF_TRY(add_cond(G, tail, cd.cg, cudaGraphCondTypeWhile, &wn, &body));
     CF_TRY(seg_begin(s, body, {}));
-    cg_step(b, CG_SETUP, h, s);
+    emit_cg_step(b, CG_SETUP, cd, s);
     CF_TRY(seg_end(s, &tmp));
     CF_CUDA(cudaGetLastError());
     CF_CUDA(cudaGraphInstantiate(&ex, G, 0));
@@ -1082,6 +1266,7 @@ cf_err cone_problem_create(cf_ctx* ctx, const cf_op* A, const double* b, int64_t
     CF_CUDA(cudaEventCreateWithFlags(&P->ev_out, cudaEventDisableTiming));
     CF_CUDA(cudaMallocHost((void**)&P->ctl_host, sizeof(Ctl)));
     std::memset(P->ctl_host, 0, sizeof(Ctl));
+    CF_CUDA(cudaMallocHost((void**)&P->flags_host, 64));
     return CF_OK;
   };
   cf_err r = run();
@@ -1107,6 +1292,7 @@ void cf_problem_destroy(cf_problem* P) {
   release_state(P);
   if (P->bf) cudaFree(P->bf);  // base of the persistent block
   if (P->ctl_host) cudaFreeHost(P->ctl_host);
+  if (P->flags_host) cudaFreeHost(P->flags_host);
   if (P->ev_in) cudaEventDestroy(P->ev_in);
   if (P->ev_out) cudaEventDestroy(P->ev_out);
   if (P->stream) cudaStreamDestroy(P->stream);

@@ -24,12 +24,14 @@ struct Ctl {
   double rr, tol2, alpha_cg, beta_cg;
   double pri, dual, gap, cx, by;
   long long cg_total;
-  int k, cg_it, cg_guard, checks, status, stop, cg_cont, setup_iters;
+  int k, cg_it, cg_guard, checks, refreshes, status, stop, cg_cont, setup_iters;
+  // loop decisions, also set as graph conditions inside a graph
+  int cg_go, do_check, do_refresh, outer_go;
   unsigned int red_count;
 };
 
 struct KernelCounts {
-  int top = 0, body = 0, cg = 0, check = 0;
+  int top = 0, body = 0, cg = 0, check = 0, refresh = 0;
 };
 
 }  // namespace cf
@@ -52,9 +54,11 @@ struct cf_problem {
   void* arena = nullptr;
   size_t state_bytes = 0;
   float *ux, *uy, *vs, *zx, *rhs, *r, *p, *qv, *wy, *t, *zy, *gx, *gy, *cm, *cn, *ws;
+  float *gz, *az;  // G z_x and A z_x, carried by the CG updates
   double *part, *chunk_n2, *seg_p0, *warm_dev, *out_dev, *uv_dev;
   cf::Ctl* ctl = nullptr;       // device
   cf::Ctl* ctl_host = nullptr;  // pinned mirror
+  void* flags_host = nullptr;   // pinned copy of the loop decisions (host-driven mode)
   cudaStream_t stream = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   cudaGraph_t graph = nullptr, setup_graph = nullptr;
