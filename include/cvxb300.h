@@ -196,6 +196,32 @@ cf_err cf_op_apply_async(cf_op* op, int32_t adjoint, float alpha, const float* x
                          int32_t accumulate, void* workspace, void* stream);
 cf_err cf_op_workspace_bytes(const cf_op* op, int32_t adjoint, size_t* bytes);
 
+/* Size of the static scratch array behind cf_op_apply_static (16 MiB). */
+#define CF_STATIC_SCRATCH_BYTES (16u << 20)
+
+/* Allocation-free apply, for callers that may not allocate GPU memory at
+ * all: code that runs inside a framework or server whose allocator owns all
+ * device memory (a raw cudaMalloc would bypass its accounting or fail against
+ * its reservation), and latency-critical loops where cudaMalloc/cudaFree would
+ * stall or synchronize the device.  The paper has no counterpart; this is an
+ * interface convenience.
+ *
+ * Same result as cf_op_apply_async (y = alpha * op(x) + (accumulate ? y : 0),
+ * x and y device float32, enqueued on `stream`, NULL = the context stream,
+ * returns without waiting), but the operator's scratch (the dense adjoint's
+ * per-row-block partial sums, product and Kronecker intermediates) comes from
+ * one file-scope device array of CF_STATIC_SCRATCH_BYTES that every GPU which
+ * loads the library holds until the process exits.  No device or host memory
+ * is allocated.  Operators needing more scratch than that are rejected with
+ * CF_E_INVALID.  The first call on a device looks up the array's device
+ * address (once per device), so make that first call before any stream
+ * capture.  All calls share the one array: calls whose GPU work overlaps
+ * (different streams, or different host threads) race and give wrong results;
+ * serialize them.  Each call writes every scratch element before reading it,
+ * so the contents left by the previous call do not matter. */
+cf_err cf_op_apply_static(cf_op* op, int32_t adjoint, float alpha, const float* x, float* y,
+                          int32_t accumulate, void* stream);
+
 /* Copy a dense leaf's stored operand out: codes receives m*n entries
  * (float32 for CF_FP32, bfloat16 bit patterns for CF_BF16, e4m3 bytes for
  * CF_FP8_E4M3), row_scale receives m float32 scales (CF_FP8_E4M3 only; may be

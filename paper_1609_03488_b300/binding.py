@@ -79,6 +79,7 @@ _sig = {
     "cf_op_dense_stored": (C.c_int, [P, P, P]),
     "cf_op_apply_async": (C.c_int, [P, C.c_int32, C.c_float, P, P, C.c_int32, P, P]),
     "cf_op_workspace_bytes": (C.c_int, [P, C.c_int32, C.POINTER(C.c_size_t)]),
+    "cf_op_apply_static": (C.c_int, [P, C.c_int32, C.c_float, P, P, C.c_int32, P]),
     "cone_problem_create": (C.c_int, [P, P, P, C.c_int64, P, C.c_int64, C.POINTER(cf_cone), PP]),
     "cf_problem_destroy": (None, [P]),
     "solve": (C.c_int, [P, C.POINTER(cf_settings), P, P, P, P, P, C.POINTER(cf_info)]),
@@ -209,6 +210,13 @@ class Operator:
         check(lib.cf_op_apply_async(self.h, 1 if adjoint else 0, float(alpha), _ptr(x), _ptr(y),
                                     1 if accumulate else 0, _ptr(workspace),
                                     C.c_void_p(stream) if stream else None), "cf_op_apply_async")
+
+    def apply_static(self, x, y, adjoint=False, alpha=1.0, accumulate=False, stream=None):
+        """cf_op_apply_static on device tensors (scratch from the library's
+        static device array; nothing is allocated)."""
+        check(lib.cf_op_apply_static(self.h, 1 if adjoint else 0, float(alpha), _ptr(x), _ptr(y),
+                                     1 if accumulate else 0, C.c_void_p(stream) if stream else None),
+              "cf_op_apply_static")
 
     def dense_stored(self, prec):
         """cf_op_dense_stored: the stored codes (and FP8 row scales)."""
