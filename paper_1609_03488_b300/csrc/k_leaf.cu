@@ -46,10 +46,13 @@ void launch_diag(cudaStream_t s, int64_t n, const float* d, float alpha, const f
 // j + 4 floor(j / kConvR): the 16-byte loads of 8 neighbouring lanes (stride
 // kConvR floats) then fall on distinct bank groups for every window offset.
 // Taps are processed in chunks of at most kConvChunk.
-constexpr int kConvThreads = 64;
+constexpr int kConvOutThreads = 64;                    // threads sharing the output tile
+constexpr int kConvGroups = 2;                         // tap groups per CTA
+constexpr int kConvThreads = kConvOutThreads * kConvGroups;
 constexpr int kConvR = 16;
-constexpr int kConvTile = kConvThreads * kConvR;
+constexpr int kConvTile = kConvOutThreads * kConvR;
 constexpr int kConvChunk = 2048;
+constexpr int kConvPadStride = kConvR + 4;             // padded floats per kConvR inputs
 
 __host__ __device__ __forceinline__ int conv_pad(int j) { return j + ((j / kConvR) << 2); }
 
@@ -70,10 +73,12 @@ __device__ __forceinline__ void conv_block(float (&acc)[kConvR], const float (&l
       acc[r] = fmaf(wv[dd], (r + dd < kConvR) ? lo[r + dd] : hi[r + dd - kConvR], acc[r]);
 }
 
-__device__ __forceinline__ void conv_load(float (&dst)[kConvR], const float* __restrict__ in_s, int j) {
+// kConvR consecutive inputs starting at a multiple of kConvR (4 contiguous
+// float4 in the padded layout).
+__device__ __forceinline__ void conv_load(float (&dst)[kConvR], const float* __restrict__ p) {
 #pragma unroll
   for (int q = 0; q < kConvR; q += 4) {
-    float4 t4 = *reinterpret_cast<const float4*>(in_s + conv_pad(j + q));
+    float4 t4 = *reinterpret_cast<const float4*>(p + q);
     dst[q] = t4.x; dst[q + 1] = t4.y; dst[q + 2] = t4.z; dst[q + 3] = t4.w;
   }
 }
@@ -83,6 +88,8 @@ k_conv1d(int64_t n_out, int64_t n_in, int64_t Lp, int64_t shift, const float* __
          float alpha, const float* __restrict__ x, float* __restrict__ y, bool acc) {
   extern __shared__ __align__(16) float sm[];
   const int tid = threadIdx.x;
+  const int grp = tid / kConvOutThreads;       // which part of the taps
+  const int t = tid % kConvOutThreads;         // which outputs
   const int64_t i0 = (int64_t)blockIdx.x * kConvTile;
   float accum[kConvR];
 #pragma unroll
@@ -104,24 +111,46 @@ k_conv1d(int64_t n_out, int64_t n_in, int64_t Lp, int64_t shift, const float* __
     for (int j = tid; j < lc; j += kConvThreads) w_s[j] = __ldg(wsrc + j);
     __syncthreads();
 
-    const int o = tid * kConvR;
+    // this group's tap blocks [b0, b1) of kConvR taps each
+    const int nblk = lc / kConvR;
+    const int b0 = (grp * nblk) / kConvGroups, b1 = ((grp + 1) * nblk) / kConvGroups;
+    // window start of output block t at tap block b: conv_pad(t R + b R) = (t + b) * (R + 4)
+    const float* ip = in_s + (t + b0) * kConvPadStride;
+    const float* wp = w_s + b0 * kConvR;
     float wa[kConvR], wb[kConvR];
-    conv_load(wa, in_s, o);
-    int mb = 0;
-    for (; mb + 2 * kConvR <= lc; mb += 2 * kConvR) {
-      conv_load(wb, in_s, o + mb + kConvR);
-      conv_block(accum, wa, wb, w_s + mb);
-      conv_load(wa, in_s, o + mb + 2 * kConvR);
-      conv_block(accum, wb, wa, w_s + mb + kConvR);
+    conv_load(wa, ip);
+    int b = b0;
+    for (; b + 2 <= b1; b += 2) {
+      conv_load(wb, ip + kConvPadStride);
+      conv_block(accum, wa, wb, wp);
+      conv_load(wa, ip + 2 * kConvPadStride);
+      conv_block(accum, wb, wa, wp + kConvR);
+      ip += 2 * kConvPadStride;
+      wp += 2 * kConvR;
     }
-    if (mb < lc) {
-      conv_load(wb, in_s, o + mb + kConvR);
-      conv_block(accum, wa, wb, w_s + mb);
+    if (b < b1) {
+      conv_load(wb, ip + kConvPadStride);
+      conv_block(accum, wa, wb, wp);
     }
   }
+  // fold the tap groups in a fixed order (group 0 adds group 1, 2, ...)
+#pragma unroll
+  for (int g = 1; g < kConvGroups; ++g) {
+    __syncthreads();
+    if (grp == g) {
+#pragma unroll
+      for (int r = 0; r < kConvR; ++r) in_s[t * (kConvR + 1) + r] = accum[r];
+    }
+    __syncthreads();
+    if (grp == 0) {
+#pragma unroll
+      for (int r = 0; r < kConvR; ++r) accum[r] += in_s[t * (kConvR + 1) + r];
+    }
+  }
+  if (grp != 0) return;
 #pragma unroll
   for (int r = 0; r < kConvR; ++r) {
-    int64_t i = i0 + tid * kConvR + r;
+    int64_t i = i0 + t * kConvR + r;
     if (i < n_out) {
       float v = alpha * accum[r];
       y[i] = acc ? y[i] + v : v;

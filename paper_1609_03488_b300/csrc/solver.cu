@@ -102,6 +102,31 @@ __device__ bool grid_sum(double (&v)[NV], double* part, unsigned int* counter) {
 #define GRID_STRIDE(i, n) \
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
 
+// Per-thread sum in compensated float32 ("double-float": hi + lo), with each
+// product taken exactly (p + e, e = fma(a, b, -p)) and each addition by
+// TwoSum.  Its accuracy is close to float64 accumulation without a float64
+// operation per element (the float64 rate of this GPU is a small fraction of
+// its float32 rate); the per-thread value feeds the float64 block and grid
+// sums.  Explicit-rounding intrinsics keep the compiler from contracting
+// the error terms away.
+struct Acc2 {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float s = __fadd_rn(hi, x);
+    const float bb = __fsub_rn(s, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(x, bb));
+    hi = s;
+    lo = __fadd_rn(lo, err);
+  }
+  __device__ __forceinline__ void add_prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    const float e = __fmaf_rn(a, b, -p);
+    add(p);
+    lo = __fadd_rn(lo, e);
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
 // ------------------------------------------------------------ iteration start
 __global__ void k_init(Ctl* c, int64_t n, int64_t m, float* ux, float* uy, float* vs, float* zx,
                        float* gz, float* az, const double* warm) {
@@ -158,19 +183,21 @@ __global__ void k_cg_init(Ctl* c, int64_t n, const float* __restrict__ rhs,
                           float* __restrict__ r, float* __restrict__ p, double* part, int mode,
                           int fresh, cudaGraphConditionalHandle h, int in_graph) {
   const float lam = (float)c->lam;
-  double v[2] = {0.0, 0.0};
+  Acc2 a0, a1;
   GRID_STRIDE(i, n) {
     float g = gz[i];
     if (fresh) {
       g = fmaf(lam, z[i], g);
       gz[i] = g;
     }
-    float ri = rhs[i] - g;
+    const float rh = rhs[i];
+    float ri = rh - g;
     r[i] = ri;
     p[i] = ri;
-    v[0] += (double)ri * ri;
-    v[1] += (double)rhs[i] * rhs[i];
+    a0.add_prod(ri, ri);
+    a1.add_prod(rh, rh);
   }
+  double v[2] = {a0.value(), a1.value()};
   if (blockIdx.x == 0 && threadIdx.x == 0) c->cg_guard = 0;
   if (grid_sum<2>(v, part, &c->red_count) && threadIdx.x == 0) {
     const double rr = v[0], nrhs = sqrt(v[1]);
@@ -200,12 +227,14 @@ __global__ void k_cg_init(Ctl* c, int64_t n, const float* __restrict__ rhs,
 __global__ void k_cg_dot(Ctl* c, int64_t n, const float* __restrict__ p, float* __restrict__ q,
                          double* part) {
   const float lam = (float)c->lam;
-  double v[1] = {0.0};
+  Acc2 a0;
   GRID_STRIDE(i, n) {
-    float qi = q[i] + lam * p[i];
+    const float pi = p[i];
+    float qi = q[i] + lam * pi;
     q[i] = qi;
-    v[0] += (double)p[i] * qi;
+    a0.add_prod(pi, qi);
   }
+  double v[1] = {a0.value()};
   if (grid_sum<1>(v, part, &c->red_count) && threadIdx.x == 0) {
     const double pq = v[0];
     c->alpha_cg = pq > 0.0 ? c->rr / pq : 0.0;
@@ -219,15 +248,16 @@ __global__ void k_cg_update(Ctl* c, int64_t n, int64_t m, float* __restrict__ z,
                             float* __restrict__ gz, float* __restrict__ az,
                             const float* __restrict__ t, double* part, int mode) {
   const float a = (float)c->alpha_cg;
-  double v[1] = {0.0};
+  Acc2 a0;
   GRID_STRIDE(i, n) {
     const float qi = q[i];
     z[i] = fmaf(a, p[i], z[i]);
     gz[i] = fmaf(a, qi, gz[i]);
     float ri = fmaf(-a, qi, r[i]);
     r[i] = ri;
-    v[0] += (double)ri * ri;
+    a0.add_prod(ri, ri);
   }
+  double v[1] = {a0.value()};
   if (az) {
     GRID_STRIDE(i, m) az[i] = fmaf(a, t[i], az[i]);
   }
@@ -277,13 +307,14 @@ __global__ void k_gz_shift(const Ctl* c, int64_t n, const float* __restrict__ z,
 __global__ void k_utau(Ctl* c, int64_t n, int64_t m, const float* __restrict__ zx,
                        const float* __restrict__ az, float* __restrict__ zy, const float* __restrict__ wy,
                        const float* __restrict__ bf, const float* __restrict__ cf, double* part) {
-  double v[1] = {0.0};
+  Acc2 a0;
   GRID_STRIDE(i, m) {
     float zi = az[i] + wy[i];
     zy[i] = zi;
-    v[0] += (double)bf[i] * zi;
+    a0.add_prod(bf[i], zi);
   }
-  GRID_STRIDE(i, n) v[0] += (double)cf[i] * zx[i];
+  GRID_STRIDE(i, n) a0.add_prod(cf[i], zx[i]);
+  double v[1] = {a0.value()};
   if (grid_sum<1>(v, part, &c->red_count) && threadIdx.x == 0)
     c->ut_tau = (c->w_tau + v[0]) / (1.0 + c->hg);
 }
@@ -312,14 +343,15 @@ __global__ void k_soc_norm(const Ctl* c, int64_t m_off, const int32_t* __restric
   const int64_t head = seg_head[sg];
   const int64_t r0 = chunk_r0[ch], r1 = chunk_r1[ch];
   const float a = (float)c->st.alpha, a1 = (float)(1.0 - c->st.alpha), ut = (float)c->ut_tau;
-  double v[1] = {0.0};
+  Acc2 a0;
   for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
     float pi = y_pre(a, a1, ut, zy[i], gy[i], uy[i], vs[i]);
     if (i == head)
       seg_p0[sg] = (double)pi;
     else
-      v[0] += (double)pi * pi;
+      a0.add_prod(pi, pi);
   }
+  double v[1] = {a0.value()};
   block_sum<1>(v);
   if (threadIdx.x == 0) chunk_n2[ch] = v[0];
 }
@@ -380,11 +412,12 @@ __global__ void k_apply(Ctl* c, int64_t n, int64_t m, int64_t z, int64_t l, int 
   const int32_t sg = chunk_seg[ch];
   const int64_t head = seg_head[sg];
   __shared__ double s_nrm;
-  if (threadIdx.x == 0) {
-    double s = 0.0;
+  {
+    double v[1] = {0.0};
     const int32_t c0 = seg_c0[sg], nc = seg_nc[sg];
-    for (int32_t k = 0; k < nc; ++k) s += chunk_n2[c0 + k];
-    s_nrm = sqrt(s);
+    for (int32_t k = threadIdx.x; k < nc; k += blockDim.x) v[0] += chunk_n2[c0 + k];
+    block_sum<1>(v);  // fixed order: same norm in every chunk of the block
+    if (threadIdx.x == 0) s_nrm = sqrt(v[0]);
   }
   __syncthreads();
   const double nrm = s_nrm, p0 = seg_p0[sg];
@@ -420,20 +453,22 @@ __global__ void k_resid(Ctl* c, int64_t n, int64_t m, const float* __restrict__ 
                         const float* __restrict__ uy, const float* __restrict__ vs,
                         const float* __restrict__ bf, const float* __restrict__ cf, double* part) {
   const double tau = c->tau;
-  double v[6] = {0, 0, 0, 0, 0, 0};
+  const float tf = (float)tau;
+  Acc2 s0, s1, s2, s3, s4, s5;
   GRID_STRIDE(i, m) {
-    double e = (double)cm[i] + (double)vs[i];
-    double d = e - (double)bf[i] * tau;
-    v[0] += d * d;
-    v[1] += e * e;
-    v[2] += (double)bf[i] * uy[i];
+    const float e = cm[i] + vs[i];
+    const float d = fmaf(-bf[i], tf, e);
+    s0.add_prod(d, d);
+    s1.add_prod(e, e);
+    s2.add_prod(bf[i], uy[i]);
   }
   GRID_STRIDE(i, n) {
-    double d = (double)cn[i] + (double)cf[i] * tau;
-    v[3] += d * d;
-    v[4] += (double)cn[i] * cn[i];
-    v[5] += (double)cf[i] * ux[i];
+    const float d = fmaf(cf[i], tf, cn[i]);
+    s3.add_prod(d, d);
+    s4.add_prod(cn[i], cn[i]);
+    s5.add_prod(cf[i], ux[i]);
   }
+  double v[6] = {s0.value(), s1.value(), s2.value(), s3.value(), s4.value(), s5.value()};
   if (grid_sum<6>(v, part, &c->red_count) && threadIdx.x == 0) {
     c->checks += 1;
     c->cx = v[5];
@@ -500,13 +535,14 @@ __global__ void k_setup_init(Ctl* c, int64_t n, int64_t m, float* gx, float* gz,
 __global__ void k_setup_fin(Ctl* c, int64_t n, int64_t m, const float* __restrict__ gx,
                             float* __restrict__ gy, const float* __restrict__ bf,
                             const float* __restrict__ cf, double* part) {
-  double v[1] = {0.0};
+  Acc2 a0;
   GRID_STRIDE(i, m) {
     float gi = gy[i] + bf[i];
     gy[i] = gi;
-    v[0] += (double)bf[i] * gi;
+    a0.add_prod(bf[i], gi);
   }
-  GRID_STRIDE(i, n) v[0] += (double)cf[i] * gx[i];
+  GRID_STRIDE(i, n) a0.add_prod(cf[i], gx[i]);
+  double v[1] = {a0.value()};
   if (grid_sum<1>(v, part, &c->red_count) && threadIdx.x == 0) c->hg = v[0];
 }
 
