@@ -32,6 +32,10 @@ WORKLOAD = dict(n_x=1_000_000, L=1000, sigma=100.0, support=0.01, noise=0.01, se
 WORKLOAD_NAME = ("large 1-D nonnegative deconvolution: n=1e6, Gaussian kernel L=1000 sigma=100, "
                  "1% nonneg support Exp(1), noise 0.01; SCS cone form n=1000001 m=2001000 (1 SOC + nonneg)")
 METRIC = "ADMM iters/s"
+# DRAM bytes (read + write) per k_conv1d launch on this workload from one ncu
+# capture (profiles/conv1d_large_deconvolution.md), valid only for the kernel
+# source it was taken on.
+CONV_NCU = {"traffic_bytes": 4029184 + 0, "src_sha256_16": "5eb743ed9e31474c"}
 FP32_LANES_PER_SM = 128
 L2_FLUSH_BYTES = 256 << 20
 
@@ -48,10 +52,29 @@ def parse():
     ap.add_argument("--cpu-iters", type=int, default=6, help="ADMM iterations of the oracle sample")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default="deconv", choices=["deconv", "lp-batch", "serve"],
+                    help="deconv (default): the large deconvolution; lp-batch: batch of sparse LPs of "
+                         "uneven size; serve: Poisson-arrival serving trace")
+    ap.add_argument("--batch-count", type=int, default=512)
+    ap.add_argument("--single-sample", type=int, default=32,
+                    help="lp-batch: LPs solved one at a time in FP32 for the single-solve comparison")
+    ap.add_argument("--requests", type=int, default=96, help="serve: trace length")
+    ap.add_argument("--rate", type=float, default=2000.0, help="serve: mean arrival rate (req/s)")
+    ap.add_argument("--slots", type=int, default=32, help="serve: concurrent solves")
+    ap.add_argument("--budget-gb", type=float, default=60.0, help="serve: device memory budget")
+    ap.add_argument("--lp-max-iters", type=int, default=50000)
     ap.add_argument("--host-loop", action="store_true",
                     help="launch the same kernels from the host instead of one CUDA graph per solve "
                          "(for profilers that cannot see kernels inside graph conditional nodes)")
     return ap.parse_args()
+
+
+def conv_src_sha():
+    import hashlib
+    src = open(os.path.join(ROOT, "paper_1609_03488_b300", "csrc", "k_leaf.cu")).read()
+    a = src.index("// ------------------------------------------------------------ 1-D convolution")
+    b = src.index("// ------------------------------------------------------------ 2-D convolution")
+    return hashlib.sha256(src[a:b].encode()).hexdigest()[:16]
 
 
 def peaks():
@@ -149,6 +172,131 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ other workloads
+def pct(v, q):
+    return float(np.percentile(np.asarray(v, dtype=np.float64), q)) if len(v) else None
+
+
+def lp_problem_residuals(prob, x, y, s):
+    from oracle import scs
+    return max(scs.residuals(scs.Operator(prob["A"]), prob["b"], prob["c"], x, y, s))
+
+
+def run_lp_batch(args, B, ctx, torch):
+    """Batch of sparse LPs (min c^T x, D x <= b, x >= 0; m ~ U{200..20000}, n = m/2,
+    density ~ U[0.5%, 2%]): the batched BF16 form (one solve_batch call, one
+    graph per LP, all concurrent) against the FP32 single-solve form (one LP at
+    a time), both to 1e-4."""
+    sizes = synth.lp_batch_sizes(count=args.batch_count)
+    t0 = time.perf_counter()
+    probs16 = [synth.lp(m_d=m, n_x=n, density=d, seed=sd, storage="bf16") for m, n, d, sd in sizes]
+    t_gen = time.perf_counter() - t0
+    nnz = sum(len(p["A"]["parts"][0]["col"]) for p in probs16)
+    st = B.settings(eps=1e-4, max_iters=args.lp_max_iters)
+    Ps = [B.cone_problem_create(ctx, p) for p in probs16]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    infos, xs, ys, ss = B.solve_batch(Ps, st)
+    t_batch = time.perf_counter() - t0
+    lat = [(i["setup_ns"] + i["solve_ns"]) / 1e6 for i in infos]
+    status = {}
+    for i in infos:
+        status[i["status_name"]] = status.get(i["status_name"], 0) + 1
+    check_idx = list(range(0, len(probs16), max(1, len(probs16) // 8)))[:8]
+    res16 = max(lp_problem_residuals(probs16[k], xs[k], ys[k], ss[k]) for k in check_idx)
+    for P in Ps:
+        P.close()
+    # FP32 single-solve form on an evenly spaced sample
+    idx = list(range(0, len(sizes), max(1, len(sizes) // args.single_sample)))[:args.single_sample]
+    t_single, single_status, res32 = 0.0, {}, 0.0
+    for k in idx:
+        m, n, d, sd = sizes[k]
+        pr = synth.lp(m_d=m, n_x=n, density=d, seed=sd, storage="fp32")
+        P = B.cone_problem_create(ctx, pr)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        info, x, y, sv = B.solve(P, st)
+        t_single += time.perf_counter() - t0
+        single_status[info["status_name"]] = single_status.get(info["status_name"], 0) + 1
+        res32 = max(res32, lp_problem_residuals(pr, x, y, sv))
+        P.close()
+    # the sample is spaced evenly over the batch's (random) sizes
+    single_rate = len(idx) / t_single
+    return {"metric": "batched solves/s", "value": len(Ps) / t_batch, "unit": "solves/s",
+            "workload": f"{len(Ps)} sparse LPs, m~U{{200..20000}}, n=m/2, density~U[0.5%,2%], total nnz {nnz}",
+            "batched_bf16": {"solves_per_s": len(Ps) / t_batch, "wall_s": t_batch, "p50_ms": pct(lat, 50),
+                             "p99_ms": pct(lat, 99), "status": status,
+                             "iters_p50": pct([i["iters"] for i in infos], 50),
+                             "iters_max": max(i["iters"] for i in infos),
+                             "gpu_launches": sum(i["kernel_launches"] for i in infos),
+                             "fp64_max_residual_sampled": res16},
+            "single_fp32": {"solves_per_s": single_rate, "sample": len(idx), "wall_s": t_single,
+                            "status": single_status, "fp64_max_residual_sampled": res32},
+            "batched_over_single": (len(Ps) / t_batch) / single_rate,
+            "generation_s": t_gen}
+
+
+def serve_trace(args, rng):
+    """A scaled Poisson trace: thirds of deconvolutions (n log-uniform in
+    [1e3, 1e5], L = n/1000 clipped to [16, 1000]), BF16 dense lassos (m_d
+    log-uniform in [1e3, 5e3], p = m_d/2) and sparse LPs (m log-uniform in
+    [1e3, 2e4], n = m/2, density 1%)."""
+    reqs = []
+    t = 0.0
+    for k in range(args.requests):
+        t += rng.exponential(1.0 / args.rate)
+        kind = k % 3
+        seed = synth.BASE_SEED + 500 + k
+        if kind == 0:
+            n = int(10 ** rng.uniform(3, 5))
+            L = int(min(1000, max(16, n // 1000)))
+            prob = synth.deconv(n_x=n, L=L, support=0.01, seed=seed)
+        elif kind == 1:
+            m = int(10 ** rng.uniform(3, np.log10(5000)))
+            prob = synth.lasso(m_d=m, p=m // 2, storage="bf16", seed=seed)
+        else:
+            m = int(10 ** rng.uniform(3, np.log10(20000)))
+            prob = synth.lp(m_d=m, n_x=m // 2, density=0.01, seed=seed)
+        reqs.append((t, prob))
+    return reqs
+
+
+def run_serve(args, B, ctx, torch):
+    rng = np.random.default_rng(synth.BASE_SEED + 77)
+    reqs = serve_trace(args, rng)
+    st = B.settings(eps=1e-4, max_iters=args.lp_max_iters)
+    Ps = [B.cone_problem_create(ctx, p) for _, p in reqs]
+    srv = B.Server(ctx, int(args.budget_gb * (1 << 30)), args.slots)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tickets = []
+    for (ta, _), P in zip(reqs, Ps):
+        now = time.perf_counter() - t0
+        if ta > now:
+            time.sleep(ta - now)
+        tickets.append((time.perf_counter(), srv.submit(P, st)))
+    lat, status = [], {}
+    results = []
+    for (ts, tk), P in zip(tickets, Ps):
+        info, x, y, sv = srv.wait(tk, P)
+        lat.append(1e3 * (info["queue_ns"] + info["setup_ns"] + info["solve_ns"]) / 1e9)
+        status[info["status_name"]] = status.get(info["status_name"], 0) + 1
+        results.append((info, x))
+    t_all = time.perf_counter() - t0
+    srv.close()
+    # the same request alone gives the same answer (first few requests)
+    same = True
+    for k in range(min(6, len(Ps))):
+        info, x, *_ = B.solve(Ps[k], st)
+        same &= bool(np.array_equal(x, results[k][1])) and info["iters"] == results[k][0]["iters"]
+    return {"metric": "served solves/s", "value": len(Ps) / t_all, "unit": "solves/s",
+            "workload": (f"{len(Ps)} requests, Poisson arrivals at {args.rate:g}/s, 1/3 each deconvolution "
+                         "n in [1e3,1e5], BF16 lasso m in [1e3,5e3], sparse LP m in [1e3,2e4] (1%)"),
+            "offered_rate": args.rate, "slots": args.slots, "budget_gb": args.budget_gb,
+            "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99), "wall_s": t_all, "status": status,
+            "alone_equals_mix_bitwise": same}
+
+
 # ------------------------------------------------------------------ ours
 def main():
     args = parse()
@@ -171,6 +319,18 @@ def main():
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize()
+
+    if args.workload != "deconv":
+        stream = torch.cuda.Stream(device=local)
+        torch.cuda.set_stream(stream)
+        ctx = B.Context(local, stream.cuda_stream)
+        run = run_lp_batch if args.workload == "lp-batch" else run_serve
+        with ClockSampler(local) as clk:
+            line = run(args, B, ctx, torch)
+        line.update({"n_gpus": world, "higher_is_better": True, "data": "synthetic", "clocks": clk.summary()})
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        return
 
     prob = synth.deconv(**{**WORKLOAD, "seed": WORKLOAD["seed"] + rank})
     n, m = prob["A"]["n"], prob["A"]["m"]
@@ -252,7 +412,9 @@ def main():
     sm_max = pk.get("sm_max_mhz", 2032.0)
     alu_peak = sm_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     roofline = {"bound": "alu", "kernel": "k_conv1d", "achieved": achieved, "peak": alu_peak,
-                "unit": "TFLOP/s", "frac": achieved / alu_peak, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / alu_peak,
+                "traffic": CONV_NCU["traffic_bytes"] if conv_src_sha() == CONV_NCU["src_sha256_16"] else None,
+                "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
                 "peak_source": f"derived: {sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x {sm_max:.0f} MHz (max SM clock of measured)",
                 "per_launch_ms": {"forward": 1e3 * t_fwd, "adjoint": 1e3 * t_adj},
                 "flops_per_launch": {"forward": flops_fwd, "adjoint": flops_adj}}

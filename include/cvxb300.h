@@ -119,7 +119,9 @@ typedef struct {
   double pri_res, dual_res, gap; /* at the last check (see eps) */
   double pobj, dobj;       /* c^T x and -b^T y at the returned point */
   double tau, kappa;       /* embedding scalars at exit */
-  int64_t setup_ns, solve_ns;    /* host wall time of setup / iterations */
+  int64_t setup_ns;        /* host time preparing the setup (0 if cached) */
+  int64_t solve_ns;        /* wall time from launch to completion (includes
+                              the setup's GPU time when it ran) */
   int64_t kernel_launches; /* kernels this call ran on the GPU */
   int64_t queue_ns;        /* serving: time from serve_submit to launch */
 } cf_info;

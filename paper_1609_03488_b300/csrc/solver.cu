@@ -33,7 +33,7 @@ int64_t now_ns() {
       .count();
 }
 
-constexpr int kSocChunk = 2048;        // rows of a second-order cone per CTA
+constexpr int kSocChunk = 512;         // rows of a second-order cone per CTA
 constexpr int kRefreshInterval = 50;   // ADMM iterations between exact G z_x, A z_x
 
 // ------------------------------------------------------------ reductions
@@ -208,7 +208,7 @@ __global__ void k_cg_init(Ctl* c, int64_t n, const float* __restrict__ rhs,
       cap = c->st.setup_cg_max;
       fixed = 0;
     } else {
-      tol = c->st.cg_tol_rel * nrhs * pow((double)c->k + 1.0, -c->st.cg_tol_exp);
+      tol = c->st.cg_tol_rel * nrhs * (double)powf((float)c->k + 1.0f, -(float)c->st.cg_tol_exp);
       tol = fmax(tol, c->st.cg_tol_min);
       cap = c->st.cg_max;
       fixed = c->st.cg_fixed;
@@ -370,7 +370,7 @@ __global__ void k_apply(Ctl* c, int64_t n, int64_t m, int64_t z, int64_t l, int 
                         const int32_t* __restrict__ seg_c0, const int32_t* __restrict__ seg_nc,
                         const double* __restrict__ chunk_n2, const double* __restrict__ seg_p0,
                         cudaGraphConditionalHandle h_check, cudaGraphConditionalHandle h_refresh,
-                        int in_graph) {
+                        cudaGraphConditionalHandle h_outer, int in_graph) {
   const double al = c->st.alpha;
   const float a = (float)al, a1 = (float)(1.0 - al), ut = (float)c->ut_tau;
   if ((int)blockIdx.x < nlin) {
@@ -400,9 +400,17 @@ __global__ void k_apply(Ctl* c, int64_t n, int64_t m, int64_t z, int64_t l, int 
       c->do_check = chk;
       c->do_refresh = ref;
       c->refreshes += ref;
+      // loop decision; a residual check run after this kernel may revise it
+      if (!isfinite(tn) || !isfinite(c->kappa)) {
+        c->status = CF_NUMERICAL;
+        c->stop = 1;
+      }
+      const int go = (!c->stop && k < c->st.max_iters) ? 1 : 0;
+      c->outer_go = go;
       if (in_graph) {
         cudaGraphSetConditional(h_check, (unsigned)chk);
         cudaGraphSetConditional(h_refresh, (unsigned)ref);
+        cudaGraphSetConditional(h_outer, (unsigned)go);
       }
     }
     return;
@@ -451,7 +459,8 @@ __global__ void k_apply(Ctl* c, int64_t n, int64_t m, int64_t z, int64_t l, int 
 __global__ void k_resid(Ctl* c, int64_t n, int64_t m, const float* __restrict__ cm,
                         const float* __restrict__ cn, const float* __restrict__ ux,
                         const float* __restrict__ uy, const float* __restrict__ vs,
-                        const float* __restrict__ bf, const float* __restrict__ cf, double* part) {
+                        const float* __restrict__ bf, const float* __restrict__ cf, double* part,
+                        cudaGraphConditionalHandle h_outer, int in_graph) {
   const double tau = c->tau;
   const float tf = (float)tau;
   Acc2 s0, s1, s2, s3, s4, s5;
@@ -478,41 +487,34 @@ __global__ void k_resid(Ctl* c, int64_t n, int64_t m, const float* __restrict__ 
     if (bad || !isfinite(tau) || !isfinite(c->kappa)) {
       c->status = CF_NUMERICAL;
       c->stop = 1;
-      return;
-    }
-    if (tau > 0.0) {
-      const double pri = sqrt(v[0]) / tau / (1.0 + c->nb);
-      const double dual = sqrt(v[3]) / tau / (1.0 + c->nc);
-      const double cx = v[5] / tau, by = v[2] / tau;
-      const double gap = fabs(cx + by) / (1.0 + fabs(cx) + fabs(by));
-      c->pri = pri;
-      c->dual = dual;
-      c->gap = gap;
-      if (pri <= c->st.eps && dual <= c->st.eps && gap <= c->st.eps) {
-        c->status = CF_SOLVED;
-        c->stop = 1;
-        return;
+    } else {
+      if (tau > 0.0) {
+        const double pri = sqrt(v[0]) / tau / (1.0 + c->nb);
+        const double dual = sqrt(v[3]) / tau / (1.0 + c->nc);
+        const double cx = v[5] / tau, by = v[2] / tau;
+        const double gap = fabs(cx + by) / (1.0 + fabs(cx) + fabs(by));
+        c->pri = pri;
+        c->dual = dual;
+        c->gap = gap;
+        if (pri <= c->st.eps && dual <= c->st.eps && gap <= c->st.eps) {
+          c->status = CF_SOLVED;
+          c->stop = 1;
+        }
+      }
+      if (!c->stop) {
+        if (-v[2] > 0.0 && sqrt(v[4]) <= c->st.eps_inf * (-v[2])) {
+          c->status = CF_INFEASIBLE;
+          c->stop = 1;
+        } else if (-v[5] > 0.0 && sqrt(v[1]) <= c->st.eps_inf * (-v[5])) {
+          c->status = CF_UNBOUNDED;
+          c->stop = 1;
+        }
       }
     }
-    if (-v[2] > 0.0 && sqrt(v[4]) <= c->st.eps_inf * (-v[2])) {
-      c->status = CF_INFEASIBLE;
-      c->stop = 1;
-    } else if (-v[5] > 0.0 && sqrt(v[1]) <= c->st.eps_inf * (-v[5])) {
-      c->status = CF_UNBOUNDED;
-      c->stop = 1;
-    }
+    const int go = (!c->stop && c->k < c->st.max_iters) ? 1 : 0;
+    c->outer_go = go;
+    if (in_graph) cudaGraphSetConditional(h_outer, (unsigned)go);
   }
-}
-
-__global__ void k_outer(Ctl* c, cudaGraphConditionalHandle h, int in_graph) {
-  int cont = 1;
-  if (!isfinite(c->tau) || !isfinite(c->kappa)) {
-    c->status = CF_NUMERICAL;
-    c->stop = 1;
-  }
-  if (c->stop || c->k >= c->st.max_iters) cont = 0;
-  c->outer_go = cont;
-  if (in_graph) cudaGraphSetConditional(h, (unsigned)cont);
 }
 
 // ------------------------------------------------------------ setup kernels
@@ -728,16 +730,16 @@ void emit_post_cg(cf_problem* P, const Conds& cd, cudaStream_t s) {
   k_apply<<<(unsigned)(nlin + P->nchunk), kThreads, 0, s>>>(
       P->ctl, n, m, P->z, P->l, nlin, P->ux, P->uy, P->vs, P->zx, P->zy, P->gx, P->gy, P->chunk_seg,
       P->chunk_r0, P->chunk_r1, P->seg_head, P->seg_c0, P->seg_nc, P->chunk_n2, P->seg_p0, cd.check,
-      cd.refresh, cd.in_graph);
+      cd.refresh, cd.outer, cd.in_graph);
 }
 
 // residuals and certificates (every check_interval iterations)
-void emit_check(cf_problem* P, cudaStream_t s) {
+void emit_check(cf_problem* P, const Conds& cd, cudaStream_t s) {
   const int64_t n = P->n, m = P->m;
   op_apply(P->A, false, 1.f, P->ux, P->cm, false, P->ws, s);
   op_apply(P->A, true, 1.f, P->uy, P->cn, false, P->ws, s);
   k_resid<<<grid_for(std::max(n, m)), kThreads, 0, s>>>(P->ctl, n, m, P->cm, P->cn, P->ux, P->uy, P->vs,
-                                                        P->bf, P->cf, P->part);
+                                                        P->bf, P->cf, P->part, cd.outer, cd.in_graph);
 }
 
 // exact A z_x and G z_x (every kRefreshInterval iterations)
@@ -747,9 +749,6 @@ void emit_refresh(cf_problem* P, cudaStream_t s) {
   k_gz_shift<<<grid_for(P->n), kThreads, 0, s>>>(P->ctl, P->n, P->zx, P->gz);
 }
 
-void emit_outer(cf_problem* P, const Conds& cd, cudaStream_t s) {
-  k_outer<<<1, 32, 0, s>>>(P->ctl, cd.outer, cd.in_graph);
-}
 
 cf_err build_setup_graph(cf_problem* P) {
   cudaStream_t s = P->stream;
@@ -795,8 +794,8 @@ cf_err build_iter_graph(cf_problem* P) {
   CF_CUDA(cudaGraphConditionalHandleCreate(&cd.cg, B, 0, 0));
   CF_CUDA(cudaGraphConditionalHandleCreate(&cd.check, B, 0, 0));
   CF_CUDA(cudaGraphConditionalHandleCreate(&cd.refresh, B, 0, 0));
-  // body: rhs and CG start, CG loop, subspace step + projection, check,
-  // refresh, loop decision
+  // body: rhs and CG start, CG loop, subspace step + projection (which also
+  // decides the loop), residual check (which may revise it), refresh
   CF_TRY(seg_begin(s, B, {}));
   emit_pre_cg(P, cd, s);
   CF_TRY(seg_end(s, &tail));
@@ -813,16 +812,13 @@ cf_err build_iter_graph(cf_problem* P) {
   cudaGraph_t D = nullptr;
   CF_TRY(add_cond(B, tail, cd.check, cudaGraphCondTypeIf, &ifn, &D));
   CF_TRY(seg_begin(s, D, {}));
-  emit_check(P, s);
+  emit_check(P, cd, s);
   CF_TRY(seg_end(s, &tmp));
   cudaGraphNode_t rfn;
   cudaGraph_t R = nullptr;
   CF_TRY(add_cond(B, {ifn}, cd.refresh, cudaGraphCondTypeIf, &rfn, &R));
   CF_TRY(seg_begin(s, R, {}));
   emit_refresh(P, s);
-  CF_TRY(seg_end(s, &tmp));
-  CF_TRY(seg_begin(s, B, {rfn}));
-  emit_outer(P, cd, s);
   CF_TRY(seg_end(s, &tmp));
   CF_CUDA(cudaGetLastError());
   P->kc.top = count_kernels(G);
@@ -892,11 +888,13 @@ cf_err run_iterations_host(cf_problem* P) {
     }
     emit_post_cg(P, cd, s);
     CF_TRY(read_flags(P, &f));
-    if (f.do_check) emit_check(P, s);
-    if (f.do_refresh) emit_refresh(P, s);
-    emit_outer(P, cd, s);
+    const int refresh = f.do_refresh;
+    if (f.do_check) {
+      emit_check(P, cd, s);
+      CF_TRY(read_flags(P, &f));
+    }
+    if (refresh) emit_refresh(P, s);
     CF_CUDA(cudaGetLastError());
-    CF_TRY(read_flags(P, &f));
     if (!f.outer_go) break;
   }
   return CF_OK;
@@ -1009,6 +1007,9 @@ static void write_settings(cf_problem* P, const cf_settings* st, bool warm) {
   s.warm = warm ? 1 : 0;
 }
 
+// Setup (g = M^{-1} h) is stream-ordered before the iterations: nothing waits
+// for it on the host, so fresh problems of a batch overlap their setups.  Its
+// CG step count arrives with the control block copied back after the solve.
 static cf_err run_setup(cf_problem* P, bool host_loop) {
   if (!P->setup_exec) CF_TRY(build_setup_graph(P));  // also gives the kernel counts
   CF_CUDA(cudaMemcpyAsync(&P->ctl->st, &P->ctl_host->st, sizeof(Settings), cudaMemcpyHostToDevice, P->stream));
@@ -1018,9 +1019,6 @@ static cf_err run_setup(cf_problem* P, bool host_loop) {
   } else {
     CF_CUDA(cudaGraphLaunch(P->setup_exec, P->stream));
   }
-  CF_CUDA(cudaMemcpyAsync(P->ctl_host, P->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, P->stream));
-  CF_CUDA(cudaStreamSynchronize(P->stream));
-  P->setup_iters_last = P->ctl_host->setup_iters;
   P->setup_done = true;
   return CF_OK;
 }
@@ -1093,6 +1091,7 @@ cf_err solve_finish(cf_problem* P, cf_info* info) {
     info->iters = c.k;
     info->cg_iters_total = c.cg_total;
     info->checks = c.checks;
+    if (P->ran_setup) P->setup_iters_last = c.setup_iters;
     info->setup_cg_iters = P->ran_setup ? P->setup_iters_last : 0;
     info->pri_res = c.pri;
     info->dual_res = c.dual;

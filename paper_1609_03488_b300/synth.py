@@ -155,11 +155,11 @@ def random_csr(rng, m, n, density):
     per_row = rng.binomial(n, density, size=m)
     rows = np.repeat(np.arange(m, dtype=np.int64), per_row)
     cols = rng.integers(0, n, size=rows.size, dtype=np.int64)
-    key = np.unique(rows * n + cols)
+    key = np.sort(rows * n + cols)
+    key = key[np.concatenate([[True], key[1:] != key[:-1]])] if key.size else key
     rows, cols = key // n, key % n
     rowptr = np.zeros(m + 1, dtype=np.int64)
-    np.add.at(rowptr, rows + 1, 1)
-    rowptr = np.cumsum(rowptr)
+    rowptr[1:] = np.cumsum(np.bincount(rows, minlength=m))
     val = rng.standard_normal(cols.size)
     return rowptr.astype(np.int32), cols.astype(np.int32), val.astype(np.float32)
 
@@ -243,11 +243,9 @@ def lp(m_d=400, n_x=200, density=0.02, storage="fp32", seed=BASE_SEED + 4):
     x0 = rng.uniform(0.0, 1.0, n_x)
     slack = rng.uniform(0.0, 1.0, m_d)
     y0 = rng.uniform(0.0, 1.0, m_d)
-    Dx0 = np.zeros(m_d)
     rows = np.repeat(np.arange(m_d), np.diff(rowptr))
-    np.add.at(Dx0, rows, val.astype(np.float64) * x0[col])
-    DTy0 = np.zeros(n_x)
-    np.add.at(DTy0, col, val.astype(np.float64) * y0[rows])
+    Dx0 = np.bincount(rows, weights=val.astype(np.float64) * x0[col], minlength=m_d)
+    DTy0 = np.bincount(col, weights=val.astype(np.float64) * y0[rows], minlength=n_x)
     b_d = Dx0 + slack
     c = -DTy0
     A = vstack([csr(m_d, n_x, rowptr, col, val, storage), scale(-1.0, eye(n_x))])
