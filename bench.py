@@ -52,10 +52,11 @@ def parse():
     ap.add_argument("--cpu-iters", type=int, default=6, help="ADMM iterations of the oracle sample")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="deconv", choices=["deconv", "lp-batch", "serve"],
+    ap.add_argument("--workload", default="deconv", choices=["deconv", "lasso", "lp-batch", "serve", "ops"],
                     help="deconv (default): the large deconvolution; lp-batch: batch of sparse LPs of "
                          "uneven size; serve: Poisson-arrival serving trace")
     ap.add_argument("--batch-count", type=int, default=512)
+    ap.add_argument("--storage", default="bf16", choices=["fp32", "bf16", "fp8"], help="lasso: operand storage")
     ap.add_argument("--single-sample", type=int, default=32,
                     help="lp-batch: LPs solved one at a time in FP32 for the single-solve comparison")
     ap.add_argument("--requests", type=int, default=96, help="serve: trace length")
@@ -233,7 +234,136 @@ def run_lp_batch(args, B, ctx, torch):
             "single_fp32": {"solves_per_s": single_rate, "sample": len(idx), "wall_s": t_single,
                             "status": single_status, "fp64_max_residual_sampled": res32},
             "batched_over_single": (len(Ps) / t_batch) / single_rate,
+            "csr_roofline": {st_: csr_roofline(B, ctx, torch, storage=st_) for st_ in ("fp32", "bf16")},
             "generation_s": t_gen}
+
+
+def time_apply(op, x, y, torch, stream, adjoint, reps=20, ws=None):
+    """Average device time of one cf_op_apply_async launch (CUDA events on
+    the launching stream)."""
+    for _ in range(3):
+        op.apply_async(x, y, adjoint=adjoint, workspace=ws, stream=stream.cuda_stream)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        op.apply_async(x, y, adjoint=adjoint, workspace=ws, stream=stream.cuda_stream)
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps / 1e3
+
+
+def hbm_peak():
+    return peaks().get("hbm_gbs", 6400.0)
+
+
+def run_lasso(args, B, ctx, torch):
+    """Dense lasso, D 20000 x 10000 i.i.d. N(0, 1/m) stored FP32 / BF16 / FP8
+    (per-row scale), x* 1% nonzero, noise 0.01, lam = 0.1 ||D^T b||_inf."""
+    stream = torch.cuda.current_stream()
+    m_d, p = 20000, 10000
+    t0 = time.perf_counter()
+    prob = synth.lasso(m_d=m_d, p=p, storage=args.storage, seed=synth.BASE_SEED + 3)
+    t_gen = time.perf_counter() - t0
+    P = B.cone_problem_create(ctx, prob)
+    n, m = prob["A"]["n"], prob["A"]["m"]
+    dev = torch.device("cuda", torch.cuda.current_device())
+    xo = torch.empty(n, dtype=torch.float64, device=dev)
+    yo = torch.empty(m, dtype=torch.float64, device=dev)
+    so = torch.empty(m, dtype=torch.float64, device=dev)
+    st = B.settings(max_iters=args.iters_per_step, eps=1e-4)
+    for _ in range(args.warmup):
+        B.solve(P, st, x=xo, y=yo, s=so)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    iters, cg, launches = 0, 0, 0
+    for k in range(args.steps):
+        ev[k][0].record(stream)
+        info = B.solve(P, st, x=xo, y=yo, s=so)[0]
+        ev[k][1].record(stream)
+        iters += info["iters"]
+        cg += info["cg_iters_total"]
+        launches += info["kernel_launches"]
+    torch.cuda.synchronize()
+    t = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+    # time to 1e-4 (fresh start, setup cached)
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    info = B.solve(P, B.settings(max_iters=20000, eps=1e-4), x=xo, y=yo, s=so)[0]
+    a1.record(stream)
+    torch.cuda.synchronize()
+    dr = dense_roofline(B, ctx, torch, args.storage, prob["meta"]["D"])
+    mat = dr["matrix_bytes"]
+    pk = hbm_peak()
+    per_iter = t / iters
+    passes = (1 + 2 * cg / iters + 0.1 * 2 + 2.0 / 50)
+    return {"metric": "ADMM iters/s", "value": iters / t, "unit": "iters/s",
+            "workload": f"dense lasso D {m_d}x{p} {args.storage}, n={n} m={m}",
+            "ms_per_iter": 1e3 * per_iter, "cg_per_iter": cg / iters, "steps": args.steps,
+            "iters_per_step": iters / args.steps, "gpu_launches": launches,
+            "time_to_1e-4": {"seconds": a0.elapsed_time(a1) / 1e3, "iters": info["iters"],
+                             "status": info["status_name"], "pri": info["pri_res"], "dual": info["dual_res"],
+                             "gap": info["gap"]},
+            "hbm_roofline_per_iter": {"operator_passes": passes,
+                                      "algorithmic_bytes": passes * mat,
+                                      "achieved_GBs": passes * mat / per_iter / 1e9, "peak_GBs": pk,
+                                      "frac": passes * mat / per_iter / 1e9 / pk},
+            "roofline": dr,
+            "generation_s": t_gen}
+
+
+def dense_roofline(B, ctx, torch, storage, D=None, m=20000, n=10000):
+    """The dense leaf alone: y = D x and x = D^T y; algorithmic bytes = the
+    stored operand (+ FP8 row scales) + the two vectors."""
+    stream = torch.cuda.current_stream()
+    if D is None:
+        D = (np.random.default_rng(3).standard_normal((m, n)) / np.sqrt(m)).astype(np.float32)
+    m, n = D.shape
+    esz = {"fp32": 4, "bf16": 2, "fp8": 1}[storage]
+    op = B.cf_op_dense(ctx, D, storage)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    xin, yin = torch.rand(n, device=dev), torch.rand(m, device=dev)
+    xout, yout = torch.empty(n, device=dev), torch.empty(m, device=dev)
+    ws = torch.empty(max(op.workspace_bytes(True) // 4, 1), device=dev)
+    t_n = time_apply(op, xin, yout, torch, stream, False)
+    t_t = time_apply(op, yin, xout, torch, stream, True, ws=ws)
+    mat = m * n * esz + (m * 4 if storage == "fp8" else 0)
+    by = mat + 4 * (m + n)
+    pk = hbm_peak()
+    return {"storage": storage, "shape": [m, n], "matrix_bytes": mat, "peak_GBs": pk,
+            "gemv_n": {"bound": "hbm", "ms": 1e3 * t_n, "achieved": by / t_n / 1e9, "unit": "GB/s",
+                       "frac": by / t_n / 1e9 / pk},
+            "gemv_t": {"bound": "hbm", "ms": 1e3 * t_t, "achieved": by / t_t / 1e9, "unit": "GB/s",
+                       "frac": by / t_t / 1e9 / pk}}
+
+
+def run_ops(args, B, ctx, torch):
+    """Operator leaves alone at the benchmark sizes (for kernel profiling)."""
+    out = {"metric": "operator HBM roofline", "value": None, "unit": "GB/s"}
+    out["csr"] = {st_: csr_roofline(B, ctx, torch, storage=st_) for st_ in ("fp32", "bf16")}
+    D = (np.random.default_rng(3).standard_normal((20000, 10000)) / np.sqrt(20000)).astype(np.float32)
+    out["dense"] = {st_: dense_roofline(B, ctx, torch, st_, D) for st_ in ("bf16", "fp8", "fp32")}
+    out["value"] = out["dense"]["bf16"]["gemv_n"]["achieved"]
+    return out
+
+
+def csr_roofline(B, ctx, torch, m=20000, n=10000, density=0.02, storage="fp32"):
+    """The largest LP's CSR operator alone: y = D x and x = D^T y."""
+    stream = torch.cuda.current_stream()
+    rng = np.random.default_rng(5)
+    rp, col, val = synth.random_csr(rng, m, n, density)
+    op = B.cf_op_csr(ctx, m, n, rp, col, val, storage)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    x, y = torch.rand(n, device=dev), torch.rand(m, device=dev)
+    xo, yo = torch.empty(n, device=dev), torch.empty(m, device=dev)
+    t_n = time_apply(op, x, yo, torch, stream, False)
+    t_t = time_apply(op, y, xo, torch, stream, True)
+    vsz = 4 if storage == "fp32" else 2
+    nnz = len(col)
+    by = nnz * (4 + vsz) + 4 * (m + 1) + 4 * (m + n)
+    pk = hbm_peak()
+    return {"nnz": nnz, "storage": storage,
+            "spmv": {"ms": 1e3 * t_n, "GBs": by / t_n / 1e9, "frac": by / t_n / 1e9 / pk},
+            "spmv_t": {"ms": 1e3 * t_t, "GBs": by / t_t / 1e9, "frac": by / t_t / 1e9 / pk},
+            "bytes_per_launch": by, "peak_GBs": pk}
 
 
 def serve_trace(args, rng):
@@ -324,7 +454,7 @@ def main():
         stream = torch.cuda.Stream(device=local)
         torch.cuda.set_stream(stream)
         ctx = B.Context(local, stream.cuda_stream)
-        run = run_lp_batch if args.workload == "lp-batch" else run_serve
+        run = {"lp-batch": run_lp_batch, "serve": run_serve, "lasso": run_lasso, "ops": run_ops}[args.workload]
         with ClockSampler(local) as clk:
             line = run(args, B, ctx, torch)
         line.update({"n_gpus": world, "higher_is_better": True, "data": "synthetic", "clocks": clk.summary()})
