@@ -67,6 +67,7 @@ enum OpKind {
 struct cf_op {
   std::atomic<int> refs{1};
   cf_ctx* ctx = nullptr;
+  int device = 0;  // the context's device, kept so that freeing never reads the context
   OpKind kind = OP_ZERO;
   int64_t m = 0, n = 0;
   std::vector<cf_op*> parts;
@@ -93,6 +94,23 @@ struct cf_op {
 };
 
 namespace cf {
+
+// Makes `dev` current for the scope and clears any error an unrelated earlier
+// runtime call left behind, so that the error checks after this library's
+// launches report only its own failures.
+struct DevGuard {
+  int prev = -1;
+  explicit DevGuard(int dev) {
+    cudaGetLastError();
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DevGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
 
 // Workspace (float count) op_apply needs for this node and below.
 size_t op_ws_floats(const cf_op* op, bool trans);

@@ -252,22 +252,21 @@ template <> struct Vec<__nv_fp8_e4m3> {
   }
 };
 
-constexpr int kGemvRows = 4;  // rows per warp in y = A x
-
-// y[i] = alpha * s_i * sum_j A[i, j] x[j]: a warp handles kGemvRows rows, so
-// each slice of x it loads is reused kGemvRows times.
-template <typename T>
+// y[i] = alpha * s_i * sum_j A[i, j] x[j]: a warp handles RW rows, so each
+// slice of x it loads is reused RW times; the RW operand loads are issued
+// before any of them is used.
+template <typename T, int RW>
 __global__ void __launch_bounds__(256)
 k_gemv_n(int64_t m, int64_t n, int64_t lda, const T* __restrict__ A, const float* __restrict__ rs,
          float alpha, const float* __restrict__ x, float* __restrict__ y, bool acc) {
   constexpr int V = Vec<T>::N;
   const int lane = threadIdx.x & 31;
-  const int64_t row0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * kGemvRows;
+  const int64_t row0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * RW;
   if (row0 >= m) return;
   const bool xal = ((reinterpret_cast<uintptr_t>(x) & 15) == 0);
-  float accv[kGemvRows];
+  float accv[RW];
 #pragma unroll
-  for (int r = 0; r < kGemvRows; ++r) accv[r] = 0.f;
+  for (int r = 0; r < RW; ++r) accv[r] = 0.f;
   for (int64_t c = (int64_t)lane * V; c < n; c += 32 * V) {
     float xv[V];
     if (xal && c + V <= n) {
@@ -280,20 +279,22 @@ k_gemv_n(int64_t m, int64_t n, int64_t lda, const T* __restrict__ A, const float
 #pragma unroll
       for (int q = 0; q < V; ++q) xv[q] = (c + q < n) ? __ldg(x + c + q) : 0.f;
     }
+    uint4 u[RW];
 #pragma unroll
-    for (int r = 0; r < kGemvRows; ++r) {
-      int64_t row = row0 + r;
-      if (row < m) {
-        uint4 u = __ldg(reinterpret_cast<const uint4*>(A + row * lda + c));
-        float av[V];
-        Vec<T>::unpack(u, av);
+    for (int r = 0; r < RW; ++r) {
+      const int64_t row = row0 + r < m ? row0 + r : m - 1;   // clamp: rows past m are not stored
+      u[r] = __ldg(reinterpret_cast<const uint4*>(A + row * lda + c));
+    }
 #pragma unroll
-        for (int q = 0; q < V; ++q) accv[r] = fmaf(av[q], xv[q], accv[r]);
-      }
+    for (int r = 0; r < RW; ++r) {
+      float av[V];
+      Vec<T>::unpack(u[r], av);
+#pragma unroll
+      for (int q = 0; q < V; ++q) accv[r] = fmaf(av[q], xv[q], accv[r]);
     }
   }
 #pragma unroll
-  for (int r = 0; r < kGemvRows; ++r) {
+  for (int r = 0; r < RW; ++r) {
     float v = accv[r];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -308,24 +309,33 @@ k_gemv_n(int64_t m, int64_t n, int64_t lda, const T* __restrict__ A, const float
 void launch_gemv_n(cudaStream_t s, cf_prec p, int64_t m, int64_t n, int64_t lda, const void* A,
                    const float* rs, float alpha, const float* x, float* y, bool acc) {
   if (m <= 0) return;
-  const int rows_per_cta = (256 / 32) * kGemvRows;
-  unsigned grid = (unsigned)((m + rows_per_cta - 1) / rows_per_cta);
-  if (p == CF_FP32)
-    k_gemv_n<float><<<grid, 256, 0, s>>>(m, n, lda, (const float*)A, rs, alpha, x, y, acc);
-  else if (p == CF_BF16)
-    k_gemv_n<__nv_bfloat16><<<grid, 256, 0, s>>>(m, n, lda, (const __nv_bfloat16*)A, rs, alpha, x, y, acc);
-  else
-    k_gemv_n<__nv_fp8_e4m3><<<grid, 256, 0, s>>>(m, n, lda, (const __nv_fp8_e4m3*)A, rs, alpha, x, y, acc);
+  if (p == CF_FP32) {
+    constexpr int RW = 4;
+    unsigned grid = (unsigned)((m + 8 * RW - 1) / (8 * RW));
+    k_gemv_n<float, RW><<<grid, 256, 0, s>>>(m, n, lda, (const float*)A, rs, alpha, x, y, acc);
+  } else if (p == CF_BF16) {
+    constexpr int RW = 4;
+    unsigned grid = (unsigned)((m + 8 * RW - 1) / (8 * RW));
+    k_gemv_n<__nv_bfloat16, RW><<<grid, 256, 0, s>>>(m, n, lda, (const __nv_bfloat16*)A, rs, alpha, x, y, acc);
+  } else {
+    constexpr int RW = 4;
+    unsigned grid = (unsigned)((m + 8 * RW - 1) / (8 * RW));
+    k_gemv_n<__nv_fp8_e4m3, RW><<<grid, 256, 0, s>>>(m, n, lda, (const __nv_fp8_e4m3*)A, rs, alpha, x, y, acc);
+  }
 }
 
 // x^T-side: part[rb, j] = sum_{i in row block rb} A[i, j] (s_i y_i); each
-// thread owns V consecutive columns, so every row is read once with 16-byte
-// coalesced loads.  A second kernel sums the row blocks in a fixed order.
-constexpr int kGemvTThreads = 256;
+// thread owns the V columns of one 16-byte load, so every row is read once
+// with coalesced loads; a CTA covers kGemvTCols columns whatever the storage
+// type (256 / 128 / 64 threads for FP32 / BF16 / FP8), and the row blocks are
+// sized for about 8 CTAs per SM.  A second kernel sums the row blocks in a
+// fixed order.
+constexpr int kGemvTCols = 1024;
 constexpr int kGemvTMaxRows = 512;
+constexpr int kGemvTUnroll = 8;
 
 template <typename T>
-__global__ void __launch_bounds__(kGemvTThreads)
+__global__ void __launch_bounds__(256)
 k_gemv_t_part(int64_t m, int64_t n, int64_t lda, int64_t rows_per_block, const T* __restrict__ A,
               const float* __restrict__ rs, const float* __restrict__ yv, float* __restrict__ part) {
   constexpr int V = Vec<T>::N;
@@ -341,12 +351,12 @@ k_gemv_t_part(int64_t m, int64_t n, int64_t lda, int64_t rows_per_block, const T
 #pragma unroll
   for (int q = 0; q < V; ++q) accv[q] = 0.f;
   int64_t i = r0;
-  for (; i + 4 <= r1; i += 4) {
-    uint4 u[4];
+  for (; i + kGemvTUnroll <= r1; i += kGemvTUnroll) {
+    uint4 u[kGemvTUnroll];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) u[k] = __ldg(reinterpret_cast<const uint4*>(A + (i + k) * lda + c0));
+    for (int k = 0; k < kGemvTUnroll; ++k) u[k] = __ldg(reinterpret_cast<const uint4*>(A + (i + k) * lda + c0));
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < kGemvTUnroll; ++k) {
       float av[V];
       Vec<T>::unpack(u[k], av);
       const float sv = sy[i + k - r0];
@@ -380,11 +390,11 @@ __global__ void k_gemv_t_reduce(int64_t n, int64_t lda, int nrb, const float* __
 }
 
 static int gemv_t_row_blocks(int64_t m, int64_t n) {
-  int64_t col_tiles = (n + kGemvTThreads * 4 - 1) / (kGemvTThreads * 4);
-  int64_t want = (4 * 148 + col_tiles - 1) / col_tiles;       // about 4 CTAs per SM
-  int64_t min_rb = (m + kGemvTMaxRows - 1) / kGemvTMaxRows;   // shared-memory cap
-  int64_t max_rb = std::max<int64_t>(1, m / 32);
-  int64_t rb = std::min(want, max_rb);
+  const int64_t col_tiles = (n + kGemvTCols - 1) / kGemvTCols;
+  const int64_t want = (8 * 148 + col_tiles - 1) / col_tiles;   // about 8 CTAs per SM
+  const int64_t min_rb = (m + kGemvTMaxRows - 1) / kGemvTMaxRows;  // shared-memory cap
+  const int64_t max_rb = std::max<int64_t>(1, m / 32);
+  const int64_t rb = std::min(want, max_rb);
   return (int)std::max<int64_t>(std::max<int64_t>(rb, min_rb), 1);
 }
 
@@ -402,13 +412,14 @@ void launch_gemv_t(cudaStream_t s, cf_prec p, int64_t m, int64_t n, int64_t lda,
   const int rb = gemv_t_row_blocks(m, n);
   const int64_t rows_per_block = (m + rb - 1) / rb;
   const int V = p == CF_FP32 ? 4 : (p == CF_BF16 ? 8 : 16);
-  dim3 grid((unsigned)((n + kGemvTThreads * V - 1) / (kGemvTThreads * V)), (unsigned)rb);
+  const int threads = kGemvTCols / V;
+  dim3 grid((unsigned)((n + kGemvTCols - 1) / kGemvTCols), (unsigned)rb);
   if (p == CF_FP32)
-    k_gemv_t_part<float><<<grid, kGemvTThreads, 0, s>>>(m, n, lda, rows_per_block, (const float*)A, rs, x, ws);
+    k_gemv_t_part<float><<<grid, threads, 0, s>>>(m, n, lda, rows_per_block, (const float*)A, rs, x, ws);
   else if (p == CF_BF16)
-    k_gemv_t_part<__nv_bfloat16><<<grid, kGemvTThreads, 0, s>>>(m, n, lda, rows_per_block, (const __nv_bfloat16*)A, rs, x, ws);
+    k_gemv_t_part<__nv_bfloat16><<<grid, threads, 0, s>>>(m, n, lda, rows_per_block, (const __nv_bfloat16*)A, rs, x, ws);
   else
-    k_gemv_t_part<__nv_fp8_e4m3><<<grid, kGemvTThreads, 0, s>>>(m, n, lda, rows_per_block, (const __nv_fp8_e4m3*)A, rs, x, ws);
+    k_gemv_t_part<__nv_fp8_e4m3><<<grid, threads, 0, s>>>(m, n, lda, rows_per_block, (const __nv_fp8_e4m3*)A, rs, x, ws);
   k_gemv_t_reduce<<<grid_for(n, 1), kThreads, 0, s>>>(n, lda, rb, ws, alpha, y, acc);
 }
 
@@ -457,7 +468,13 @@ void launch_quantize(cudaStream_t s, cf_prec p, int64_t m, int64_t n, int64_t ld
 }
 
 // ------------------------------------------------------------ CSR SpMV
-// One warp per row; lanes stride over the row's entries.
+// One warp per row; lanes stride over the row's entries, four strides at a
+// time so that each lane has four independent index -> x gathers in flight.
+template <bool BF16>
+__device__ __forceinline__ float csr_val(const void* __restrict__ val, int32_t k) {
+  return BF16 ? __bfloat162float(__ldg(((const __nv_bfloat16*)val) + k)) : __ldg(((const float*)val) + k);
+}
+
 template <bool BF16>
 __global__ void __launch_bounds__(256)
 k_csr(int64_t m, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
@@ -466,12 +483,20 @@ k_csr(int64_t m, const int32_t* __restrict__ rowptr, const int32_t* __restrict__
   const int lane = threadIdx.x & 31;
   const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (row >= m) return;
-  const int32_t b = rowptr[row], e = rowptr[row + 1];
-  float sum = 0.f;
-  for (int32_t k = b + lane; k < e; k += 32) {
-    float v = BF16 ? __bfloat162float(((const __nv_bfloat16*)val)[k]) : ((const float*)val)[k];
-    sum = fmaf(v, __ldg(x + col[k]), sum);
+  const int32_t b = __ldg(rowptr + row), e = __ldg(rowptr + row + 1);
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+  int32_t k = b + lane;
+  for (; k + 96 < e; k += 128) {
+    const int32_t c0 = __ldg(col + k), c1 = __ldg(col + k + 32), c2 = __ldg(col + k + 64), c3 = __ldg(col + k + 96);
+    const float v0 = csr_val<BF16>(val, k), v1 = csr_val<BF16>(val, k + 32);
+    const float v2 = csr_val<BF16>(val, k + 64), v3 = csr_val<BF16>(val, k + 96);
+    s0 = fmaf(v0, __ldg(x + c0), s0);
+    s1 = fmaf(v1, __ldg(x + c1), s1);
+    s2 = fmaf(v2, __ldg(x + c2), s2);
+    s3 = fmaf(v3, __ldg(x + c3), s3);
   }
+  for (; k < e; k += 32) s0 = fmaf(csr_val<BF16>(val, k), __ldg(x + __ldg(col + k)), s0);
+  float sum = (s0 + s1) + (s2 + s3);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
   if (lane == 0) {

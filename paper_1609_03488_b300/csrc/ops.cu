@@ -16,12 +16,11 @@ static void op_free(cf_op* op) {
   for (cf_op* p : op->parts) cf_op_destroy(p);
   void* bufs[] = {op->a, op->row_scale, op->rowptr, op->col, op->t_rowptr, op->t_col,
                   op->val, op->t_val, op->w_fwd, op->w_adj, op->k2_fwd, op->k2_adj, op->d};
-  int prev = -1;
-  cudaGetDevice(&prev);
-  if (op->ctx) cudaSetDevice(op->ctx->device);
-  for (void* b : bufs)
-    if (b) cudaFree(b);
-  if (prev >= 0) cudaSetDevice(prev);
+  {
+    DevGuard g(op->device);
+    for (void* b : bufs)
+      if (b) cudaFree(b);
+  }
   delete op;
 }
 
@@ -201,20 +200,10 @@ cf_err dev_alloc(T** p, size_t count, size_t* bytes) {
   return CF_OK;
 }
 
-struct DevGuard {
-  int prev = -1;
-  explicit DevGuard(int dev) {
-    cudaGetDevice(&prev);
-    cudaSetDevice(dev);
-  }
-  ~DevGuard() {
-    if (prev >= 0) cudaSetDevice(prev);
-  }
-};
-
 cf_op* new_op(cf_ctx* ctx, OpKind k, int64_t m, int64_t n) {
   cf_op* op = new cf_op();
   op->ctx = ctx;
+  op->device = ctx->device;
   op->kind = k;
   op->m = m;
   op->n = n;
@@ -539,7 +528,7 @@ cf_err cf_op_apply_async(cf_op* op, int32_t adjoint, float alpha, const float* x
     return fail(CF_E_INVALID, "cf_op_apply_async: workspace required");
   if (!is_device_ptr(x) || !is_device_ptr(y) || (workspace && !is_device_ptr(workspace)))
     return fail(CF_E_INVALID, "cf_op_apply_async: x, y and workspace must be device memory");
-  DevGuard g(op->ctx->device);
+  DevGuard g(op->device);
   cudaStream_t s = stream ? (cudaStream_t)stream : op->ctx->stream;
   op_apply(op, tr, alpha, x, y, accumulate != 0, (float*)workspace, s);
   CF_CUDA(cudaGetLastError());
@@ -548,7 +537,7 @@ cf_err cf_op_apply_async(cf_op* op, int32_t adjoint, float alpha, const float* x
 
 cf_err cf_op_dense_stored(const cf_op* op, void* codes, float* row_scale) {
   if (!op || op->kind != OP_DENSE || !codes) return fail(CF_E_INVALID, "cf_op_dense_stored: not a dense leaf");
-  DevGuard g(op->ctx->device);
+  DevGuard g(op->device);
   const size_t esz = op->prec == CF_FP32 ? 4 : (op->prec == CF_BF16 ? 2 : 1);
   // strip the row padding
   CF_CUDA(cudaMemcpy2D(codes, op->n * esz, op->a, op->lda * esz, op->n * esz, op->m, cudaMemcpyDefault));

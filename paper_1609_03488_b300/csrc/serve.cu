@@ -105,7 +105,8 @@ struct cf_server {
       r->y.resize(m);
       r->s.resize(m);
       r->t_start = now_ns();
-      r->err = solve_launch(r->p, &r->st, r->x.data(), r->y.data(), r->s.data(), nullptr, nullptr);
+      r->err = solve_launch(r->p, &r->st, r->x.data(), r->y.data(), r->s.data(), nullptr, nullptr,
+                            /*join_ctx=*/false);
       if (r->err != CF_OK) {
         r->plock.unlock();
         r->state = Q_DONE;

@@ -1024,7 +1024,7 @@ static cf_err run_setup(cf_problem* P, bool host_loop) {
 }
 
 cf_err solve_launch(cf_problem* P, const cf_settings* st_in, double* x, double* y, double* s,
-                    const double* warm_uv, double* uv_out) {
+                    const double* warm_uv, double* uv_out, bool join_ctx) {
   cf_settings st;
   if (st_in)
     st = *st_in;
@@ -1071,7 +1071,7 @@ cf_err solve_launch(cf_problem* P, const cf_settings* st_in, double* x, double* 
   }
   CF_CUDA(cudaMemcpyAsync(P->ctl_host, P->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, P->stream));
   CF_CUDA(cudaEventRecord(P->ev_out, P->stream));
-  CF_CUDA(cudaStreamWaitEvent(P->ctx->stream, P->ev_out, 0));
+  if (join_ctx) CF_CUDA(cudaStreamWaitEvent(P->ctx->stream, P->ev_out, 0));
   return CF_OK;
 }
 
@@ -1224,11 +1224,10 @@ cf_err cone_problem_create(cf_ctx* ctx, const cf_op* A, const double* b, int64_t
     tot += K->q[j];
   }
   if (tot != m) return fail(CF_E_INVALID, "cone_problem_create: z + l + sum(q) != m");
-  int prev = -1;
-  cudaGetDevice(&prev);
-  cudaSetDevice(ctx->device);
+  DevGuard guard(ctx->device);
   std::unique_ptr<cf_problem> P(new cf_problem());
   P->ctx = ctx;
+  P->device = ctx->device;
   P->m = m;
   P->n = n;
   P->z = K->z;
@@ -1314,15 +1313,12 @@ cf_err cone_problem_create(cf_ctx* ctx, const cf_op* A, const double* b, int64_t
     P->A = const_cast<cf_op*>(A);
     *out = P.release();
   }
-  if (prev >= 0) cudaSetDevice(prev);
   return r;
 }
 
 void cf_problem_destroy(cf_problem* P) {
   if (!P) return;
-  int prev = -1;
-  cudaGetDevice(&prev);
-  cudaSetDevice(P->ctx->device);
+  DevGuard guard(P->device);
   if (P->stream) cudaStreamSynchronize(P->stream);
   release_state(P);
   if (P->bf) cudaFree(P->bf);  // base of the persistent block
@@ -1333,19 +1329,15 @@ void cf_problem_destroy(cf_problem* P) {
   if (P->stream) cudaStreamDestroy(P->stream);
   if (P->A) cf_op_destroy(P->A);
   delete P;
-  if (prev >= 0) cudaSetDevice(prev);
 }
 
 cf_err solve(cf_problem* P, const cf_settings* st, double* x, double* y, double* s,
              const double* warm_uv, double* uv_out, cf_info* info) {
   if (!P) return fail(CF_E_INVALID, "solve: NULL problem");
   std::lock_guard<std::mutex> lk(P->mtx);
-  int prev = -1;
-  cudaGetDevice(&prev);
-  cudaSetDevice(P->ctx->device);
+  DevGuard guard(P->device);
   cf_err r = solve_launch(P, st, x, y, s, warm_uv, uv_out);
   if (r == CF_OK) r = solve_finish(P, info);
-  if (prev >= 0) cudaSetDevice(prev);
   return r;
 }
 
@@ -1361,13 +1353,17 @@ cf_err solve_batch(cf_problem* const* probs, int32_t count, const cf_settings* s
   for (int32_t i = 0; i < count; ++i) locks.emplace_back(probs[i]->mtx);
   cf_err first = CF_OK;
   std::vector<char> launched(count, 0);
+  DevGuard guard(count > 0 ? probs[0]->device : 0);
   for (int32_t i = 0; i < count; ++i) {
-    cudaSetDevice(probs[i]->ctx->device);
+    cudaSetDevice(probs[i]->device);
     cf_err r = solve_launch(probs[i], st, xs ? xs[i] : nullptr, ys ? ys[i] : nullptr,
-                            ss ? ss[i] : nullptr, nullptr, nullptr);
+                            ss ? ss[i] : nullptr, nullptr, nullptr, /*join_ctx=*/false);
     launched[i] = r == CF_OK;
     if (r != CF_OK && first == CF_OK) first = r;
   }
+  // every problem was enqueued before any join, so they run concurrently
+  for (int32_t i = 0; i < count; ++i)
+    if (launched[i]) cudaStreamWaitEvent(probs[i]->ctx->stream, probs[i]->ev_out, 0);
   for (int32_t i = 0; i < count; ++i) {
     if (!launched[i]) continue;
     cf_err r = solve_finish(probs[i], infos ? &infos[i] : nullptr);
@@ -1380,12 +1376,8 @@ cf_err cg_solve(cf_op* A, double lam, const float* rhs, float* x, int32_t max_it
                 int32_t* iters, double* res_norm) {
   if (!A || !rhs || !x || max_iters < 0 || !(tol >= 0) || !(lam >= 0))
     return fail(CF_E_INVALID, "cg_solve: bad arguments");
-  int prev = -1;
-  cudaGetDevice(&prev);
-  cudaSetDevice(A->ctx->device);
-  cf_err r = cg_solve_impl(A, lam, rhs, x, max_iters, tol, iters, res_norm);
-  if (prev >= 0) cudaSetDevice(prev);
-  return r;
+  DevGuard guard(A->device);
+  return cg_solve_impl(A, lam, rhs, x, max_iters, tol, iters, res_norm);
 }
 
 }  // extern "C"

@@ -38,6 +38,7 @@ struct KernelCounts {
 
 struct cf_problem {
   cf_ctx* ctx = nullptr;
+  int device = 0;
   cf_op* A = nullptr;
   int64_t m = 0, n = 0, z = 0, l = 0;
   std::vector<int64_t> q;
@@ -77,8 +78,10 @@ namespace cf {
 size_t problem_state_bytes(const cf_problem* p);
 cf_err ensure_state(cf_problem* p);
 void release_state(cf_problem* p);
+// join_ctx: make the context stream wait for this solve right away (single
+// solves); batches join after launching every problem, servers never do.
 cf_err solve_launch(cf_problem* p, const cf_settings* st, double* x, double* y, double* s,
-                    const double* warm_uv, double* uv_out);
+                    const double* warm_uv, double* uv_out, bool join_ctx = true);
 cf_err solve_finish(cf_problem* p, cf_info* info);
 bool settings_valid(const cf_settings* st, std::string* why);
 int64_t now_ns();

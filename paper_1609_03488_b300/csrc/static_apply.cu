@@ -48,7 +48,7 @@ extern "C" cf_err cf_op_apply_static(cf_op* op, int32_t adjoint, float alpha, co
     return cf::fail(CF_E_INVALID, "cf_op_apply_static: x and y must be device memory");
   int prev = -1;
   cudaGetDevice(&prev);
-  const int dev = op->ctx->device;
+  const int dev = op->device;
   if (prev != dev) cudaSetDevice(dev);
   float* scratch = nullptr;
   cf_err r = scratch_for(dev, &scratch);
@@ -56,6 +56,7 @@ extern "C" cf_err cf_op_apply_static(cf_op* op, int32_t adjoint, float alpha, co
     // Every scratch element the kernels read is written earlier in the same
     // call, so nothing needs clearing between calls.
     cudaStream_t s = stream ? (cudaStream_t)stream : op->ctx->stream;
+    cudaGetLastError();  // report only this call's launch errors below
     cf::op_apply(op, tr, alpha, x, y, accumulate != 0, scratch, s);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) r = cf::cuda_fail(e, "cf_op_apply_static launch", __FILE__, __LINE__);
