@@ -121,6 +121,25 @@ void op_apply(const cf_op* op, bool trans, float alpha, const float* x, float* y
               float* ws, cudaStream_t s);
 void op_retain(cf_op* op);
 
+// ---- elementwise segments: y = sum_k alpha_k d_k x_k (+ y if acc); no
+// terms and acc == 0 is a zero fill.  Several independent segments go out
+// in one launch.
+constexpr int kEwMaxTerms = 4;
+constexpr int kEwMaxSegs = 8;
+struct EwSeg {
+  float* y;
+  int64_t n;
+  int acc, nterm;
+  const float* x[kEwMaxTerms];
+  const float* d[kEwMaxTerms];  // nullptr: identity
+  float alpha[kEwMaxTerms];
+};
+struct EwBatch {
+  int nseg;
+  EwSeg seg[kEwMaxSegs];
+};
+void launch_ew(cudaStream_t s, const EwBatch& b);
+
 // ---- leaf launchers (kernels in k_*.cu)
 void launch_fill(cudaStream_t s, int64_t n, float v, float* y);
 void launch_diag(cudaStream_t s, int64_t n, const float* d, float alpha, const float* x, float* y,

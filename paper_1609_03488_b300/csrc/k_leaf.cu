@@ -20,6 +20,29 @@ __global__ void k_diag(int64_t n, const float* __restrict__ d, float alpha,
   }
 }
 
+// blockIdx.y selects the segment; segments are independent (the host only
+// batches operations without data hazards between them).
+__global__ void k_ew(EwBatch b) {
+  const EwSeg& g = b.seg[blockIdx.y];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float v = g.acc ? g.y[i] : 0.f;
+    for (int k = 0; k < g.nterm; ++k) {
+      const float xv = g.x[k][i];
+      v = fmaf(g.alpha[k], g.d[k] ? g.d[k][i] * xv : xv, v);
+    }
+    g.y[i] = v;
+  }
+}
+
+void launch_ew(cudaStream_t s, const EwBatch& b) {
+  if (b.nseg <= 0) return;
+  int64_t mx = 1;
+  for (int k = 0; k < b.nseg; ++k) mx = std::max(mx, b.seg[k].n);
+  dim3 grid((unsigned)grid_for(mx), (unsigned)b.nseg);
+  k_ew<<<grid, kThreads, 0, s>>>(b);
+}
+
 void launch_fill(cudaStream_t s, int64_t n, float v, float* y) {
   if (n <= 0) return;
   k_fill<<<grid_for(n), kThreads, 0, s>>>(n, v, y);

@@ -63,16 +63,89 @@ size_t op_ws_floats(const cf_op* op, bool trans) {
   return 0;
 }
 
+namespace {
+
+bool overlap(const float* a, int64_t na, const float* b, int64_t nb) {
+  return a < b + nb && b < a + na;
+}
+
+// Pending elementwise leaf operations of one tree walk, launched together.
+struct EwQueue {
+  EwBatch b{};
+  cudaStream_t s;
+  explicit EwQueue(cudaStream_t st) : s(st) { b.nseg = 0; }
+  void flush() {
+    launch_ew(s, b);
+    b.nseg = 0;
+  }
+  // y = alpha d x (+ y): nterm 0 is a zero fill.
+  void add(float* y, int64_t n, bool acc, const float* x, const float* d, float alpha, bool fill) {
+    // same output, accumulating, no reads of pending outputs: one more term
+    for (int k = 0; k < b.nseg; ++k) {
+      EwSeg& g = b.seg[k];
+      if (!fill && acc && g.y == y && g.n == n && g.nterm < kEwMaxTerms) {
+        bool hazard = false;
+        for (int j = 0; j < b.nseg; ++j) hazard |= overlap(x, n, b.seg[j].y, b.seg[j].n);
+        if (!hazard) {
+          g.x[g.nterm] = x;
+          g.d[g.nterm] = d;
+          g.alpha[g.nterm] = alpha;
+          ++g.nterm;
+          return;
+        }
+      }
+    }
+    bool hazard = b.nseg == kEwMaxSegs;
+    for (int j = 0; j < b.nseg && !hazard; ++j) {
+      const EwSeg& g = b.seg[j];
+      hazard |= overlap(y, n, g.y, g.n);                       // write after write
+      if (!fill) hazard |= overlap(x, n, g.y, g.n);            // read after write
+      for (int k = 0; k < g.nterm; ++k) hazard |= overlap(g.x[k], g.n, y, n);  // write after read
+    }
+    if (hazard) flush();
+    EwSeg& g = b.seg[b.nseg++];
+    g.y = y;
+    g.n = n;
+    g.acc = acc ? 1 : 0;
+    g.nterm = fill ? 0 : 1;
+    if (!fill) {
+      g.x[0] = x;
+      g.d[0] = d;
+      g.alpha[0] = alpha;
+    }
+  }
+};
+
+void op_apply_rec(const cf_op* op, bool trans, float alpha, const float* x, float* y, bool acc,
+                  float* ws, cudaStream_t s, EwQueue& q);
+
+}  // namespace
+
 // y = alpha * op(x) + (acc ? y : 0)
 void op_apply(const cf_op* op, bool trans, float alpha, const float* x, float* y, bool acc,
               float* ws, cudaStream_t s) {
+  EwQueue q(s);
+  op_apply_rec(op, trans, alpha, x, y, acc, ws, s, q);
+  q.flush();
+}
+
+namespace {
+
+void op_apply_rec(const cf_op* op, bool trans, float alpha, const float* x, float* y, bool acc,
+                  float* ws, cudaStream_t s, EwQueue& q) {
   const int64_t out_dim = trans ? op->n : op->m;
+  // Elementwise leaves are queued; any other leaf first launches the queue,
+  // so operations keep their order wherever they could interact.
+  if (op->kind != OP_ZERO && op->kind != OP_DIAG && op->kind != OP_SCALE && op->kind != OP_ADJOINT &&
+      op->kind != OP_VSTACK && op->kind != OP_HSTACK && op->kind != OP_BLOCKDIAG && op->kind != OP_SUM &&
+      op->kind != OP_PRODUCT)
+    q.flush();
   switch (op->kind) {
     case OP_ZERO:
-      if (!acc) launch_fill(s, out_dim, 0.f, y);
+      if (!acc) q.add(y, out_dim, false, nullptr, nullptr, 0.f, true);
       return;
     case OP_DIAG:
-      launch_diag(s, op->n, op->d, alpha, x, y, acc);
+      q.add(y, op->n, acc, x, op->d, alpha, false);
       return;
     case OP_DENSE:
       if (!trans)
@@ -104,10 +177,10 @@ void op_apply(const cf_op* op, bool trans, float alpha, const float* x, float* y
       return;
     }
     case OP_SCALE:
-      op_apply(op->parts[0], trans, (float)(alpha * op->alpha), x, y, acc, ws, s);
+      op_apply_rec(op->parts[0], trans, (float)(alpha * op->alpha), x, y, acc, ws, s, q);
       return;
     case OP_ADJOINT:
-      op_apply(op->parts[0], !trans, alpha, x, y, acc, ws, s);
+      op_apply_rec(op->parts[0], !trans, alpha, x, y, acc, ws, s, q);
       return;
     case OP_VSTACK:
     case OP_HSTACK: {
@@ -117,10 +190,10 @@ void op_apply(const cf_op* op, bool trans, float alpha, const float* x, float* y
       bool first = true;
       for (const cf_op* p : op->parts) {
         if (split_out) {
-          op_apply(p, trans, alpha, x, y + off, acc, ws, s);
+          op_apply_rec(p, trans, alpha, x, y + off, acc, ws, s, q);
           off += trans ? p->n : p->m;
         } else {
-          op_apply(p, trans, alpha, x + off, y, first ? acc : true, ws, s);
+          op_apply_rec(p, trans, alpha, x + off, y, first ? acc : true, ws, s, q);
           off += trans ? p->m : p->n;
           first = false;
         }
@@ -131,7 +204,7 @@ void op_apply(const cf_op* op, bool trans, float alpha, const float* x, float* y
       int64_t ro = 0, co = 0;
       for (const cf_op* p : op->parts) {
         const int64_t din = trans ? p->m : p->n, dout = trans ? p->n : p->m;
-        op_apply(p, trans, alpha, x + ro, y + co, acc, ws, s);
+        op_apply_rec(p, trans, alpha, x + ro, y + co, acc, ws, s, q);
         ro += din;
         co += dout;
       }
@@ -140,7 +213,7 @@ void op_apply(const cf_op* op, bool trans, float alpha, const float* x, float* y
     case OP_SUM: {
       bool first = true;
       for (const cf_op* p : op->parts) {
-        op_apply(p, trans, alpha, x, y, first ? acc : true, ws, s);
+        op_apply_rec(p, trans, alpha, x, y, first ? acc : true, ws, s, q);
         first = false;
       }
       return;
@@ -157,7 +230,7 @@ void op_apply(const cf_op* op, bool trans, float alpha, const float* x, float* y
         const cf_op* p = trans ? op->parts[step] : op->parts[k - 1 - step];
         const bool last = step + 1 == k;
         float* dst = last ? y : buf[step & 1];
-        op_apply(p, trans, last ? alpha : 1.f, cur, dst, last ? acc : false, rest, s);
+        op_apply_rec(p, trans, last ? alpha : 1.f, cur, dst, last ? acc : false, rest, s, q);
         cur = dst;
       }
       return;
@@ -179,6 +252,8 @@ void op_apply(const cf_op* op, bool trans, float alpha, const float* x, float* y
     }
   }
 }
+
+}  // namespace
 
 }  // namespace cf
 
