@@ -46,6 +46,15 @@ inline int grid_for(int64_t n, int per_thread = 4) {
   return (int)g;
 }
 
+// Grids of kernels that end in a grid-wide sum: 2 CTAs per SM.  Every CTA
+// pays a fence and an atomic ticket on one counter, which on this two-die
+// GPU costs more than the extra elements per thread do.
+constexpr int kRedGrid = 296;
+inline int red_grid(int64_t n) {
+  int g = grid_for(n);
+  return g < kRedGrid ? g : kRedGrid;
+}
+
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 }  // namespace cf

@@ -33,7 +33,7 @@ int64_t now_ns() {
       .count();
 }
 
-constexpr int kSocChunk = 512;         // rows of a second-order cone per CTA
+constexpr int kSocChunk = 2048;        // rows of a second-order cone per CTA
 constexpr int kRefreshInterval = 50;   // ADMM iterations between exact G z_x, A z_x
 
 // ------------------------------------------------------------ reductions
@@ -102,6 +102,22 @@ __device__ bool grid_sum(double (&v)[NV], double* part, unsigned int* counter) {
 #define GRID_STRIDE(i, n) \
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
 
+// Vector kernels walk float4 groups (the solver's vectors start on 256-byte
+// boundaries of their arena) and then the scalar tail, so that a thread's
+// loads for four elements go out as one 16-byte access.
+#define VEC4_LOOP(v, n4) \
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < (n4); v += (int64_t)gridDim.x * blockDim.x)
+#define TAIL_LOOP(i, n)                                                                  \
+  for (int64_t i = ((n) & ~(int64_t)3) + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; \
+       i < (n); i += (int64_t)gridDim.x * blockDim.x)
+
+__device__ __forceinline__ float4 ld4(const float* p, int64_t v) {
+  return reinterpret_cast<const float4*>(p)[v];
+}
+__device__ __forceinline__ void st4(float* p, int64_t v, float4 a) { reinterpret_cast<float4*>(p)[v] = a; }
+__device__ __forceinline__ float& el(float4& a, int k) { return (&a.x)[k]; }
+__device__ __forceinline__ float elc(const float4& a, int k) { return (&a.x)[k]; }
+
 // Per-thread sum in compensated float32 ("double-float": hi + lo), with each
 // product taken exactly (p + e, e = fma(a, b, -p)) and each addition by
 // TwoSum.  Its accuracy is close to float64 accumulation without a float64
@@ -161,8 +177,13 @@ __global__ void k_init(Ctl* c, int64_t n, int64_t m, float* ux, float* uy, float
 __global__ void k_rhs(Ctl* c, int64_t n, int64_t m, const float* __restrict__ ux,
                       const float* __restrict__ uy, const float* __restrict__ vs,
                       float* __restrict__ wy, float* __restrict__ rhs) {
-  GRID_STRIDE(i, m) wy[i] = uy[i] + vs[i];
-  GRID_STRIDE(i, n) rhs[i] = ux[i];
+  VEC4_LOOP(v, m >> 2) {
+    const float4 a = ld4(uy, v), b = ld4(vs, v);
+    st4(wy, v, make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w));
+  }
+  TAIL_LOOP(i, m) wy[i] = uy[i] + vs[i];
+  VEC4_LOOP(v, n >> 2) st4(rhs, v, ld4(ux, v));
+  TAIL_LOOP(i, n) rhs[i] = ux[i];
   if (blockIdx.x == 0 && threadIdx.x == 0) c->w_tau = c->tau + c->kappa;
 }
 
@@ -184,7 +205,26 @@ __global__ void k_cg_init(Ctl* c, int64_t n, const float* __restrict__ rhs,
                           int fresh, cudaGraphConditionalHandle h, int in_graph) {
   const float lam = (float)c->lam;
   Acc2 a0, a1;
-  GRID_STRIDE(i, n) {
+  VEC4_LOOP(v, n >> 2) {
+    float4 g = ld4(gz, v);
+    const float4 rh = ld4(rhs, v);
+    if (fresh) {
+      const float4 zz = ld4(z, v);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) el(g, k) = fmaf(lam, elc(zz, k), el(g, k));
+      st4(gz, v, g);
+    }
+    float4 rr;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      el(rr, k) = elc(rh, k) - elc(g, k);
+      a0.add_prod(elc(rr, k), elc(rr, k));
+      a1.add_prod(elc(rh, k), elc(rh, k));
+    }
+    st4(r, v, rr);
+    st4(p, v, rr);
+  }
+  TAIL_LOOP(i, n) {
     float g = gz[i];
     if (fresh) {
       g = fmaf(lam, z[i], g);
@@ -228,7 +268,17 @@ __global__ void k_cg_dot(Ctl* c, int64_t n, const float* __restrict__ p, float* 
                          double* part) {
   const float lam = (float)c->lam;
   Acc2 a0;
-  GRID_STRIDE(i, n) {
+  VEC4_LOOP(w, n >> 2) {
+    const float4 pp = ld4(p, w);
+    float4 qq = ld4(q, w);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      el(qq, k) = el(qq, k) + lam * elc(pp, k);
+      a0.add_prod(elc(pp, k), elc(qq, k));
+    }
+    st4(q, w, qq);
+  }
+  TAIL_LOOP(i, n) {
     const float pi = p[i];
     float qi = q[i] + lam * pi;
     q[i] = qi;
@@ -249,7 +299,21 @@ __global__ void k_cg_update(Ctl* c, int64_t n, int64_t m, float* __restrict__ z,
                             const float* __restrict__ t, double* part, int mode) {
   const float a = (float)c->alpha_cg;
   Acc2 a0;
-  GRID_STRIDE(i, n) {
+  VEC4_LOOP(v, n >> 2) {
+    const float4 qq = ld4(q, v), pp = ld4(p, v);
+    float4 zz = ld4(z, v), gg = ld4(gz, v), rr = ld4(r, v);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      el(zz, k) = fmaf(a, elc(pp, k), el(zz, k));
+      el(gg, k) = fmaf(a, elc(qq, k), el(gg, k));
+      el(rr, k) = fmaf(-a, elc(qq, k), el(rr, k));
+      a0.add_prod(elc(rr, k), elc(rr, k));
+    }
+    st4(z, v, zz);
+    st4(gz, v, gg);
+    st4(r, v, rr);
+  }
+  TAIL_LOOP(i, n) {
     const float qi = q[i];
     z[i] = fmaf(a, p[i], z[i]);
     gz[i] = fmaf(a, qi, gz[i]);
@@ -259,7 +323,14 @@ __global__ void k_cg_update(Ctl* c, int64_t n, int64_t m, float* __restrict__ z,
   }
   double v[1] = {a0.value()};
   if (az) {
-    GRID_STRIDE(i, m) az[i] = fmaf(a, t[i], az[i]);
+    VEC4_LOOP(w, m >> 2) {
+      const float4 tt = ld4(t, w);
+      float4 aa = ld4(az, w);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) el(aa, k) = fmaf(a, elc(tt, k), el(aa, k));
+      st4(az, w, aa);
+    }
+    TAIL_LOOP(i, m) az[i] = fmaf(a, t[i], az[i]);
   }
   if (grid_sum<1>(v, part, &c->red_count) && threadIdx.x == 0) {
     const double rr_new = v[0];
@@ -286,7 +357,14 @@ __global__ void k_cg_update(Ctl* c, int64_t n, int64_t m, float* __restrict__ z,
 __global__ void k_cg_p(Ctl* c, int64_t n, const float* __restrict__ r, float* __restrict__ p,
                        int mode, cudaGraphConditionalHandle h, int in_graph) {
   const float b = (float)c->beta_cg;
-  GRID_STRIDE(i, n) p[i] = fmaf(b, p[i], r[i]);
+  VEC4_LOOP(v, n >> 2) {
+    const float4 rr = ld4(r, v);
+    float4 pp = ld4(p, v);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) el(pp, k) = fmaf(b, el(pp, k), elc(rr, k));
+    st4(p, v, pp);
+  }
+  TAIL_LOOP(i, n) p[i] = fmaf(b, p[i], r[i]);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     const int g = ++c->cg_guard;
     int cap = mode == CG_SETUP ? c->st.setup_cg_max : (c->st.cg_fixed > 0 ? c->st.cg_fixed : c->st.cg_max);
@@ -308,12 +386,27 @@ __global__ void k_utau(Ctl* c, int64_t n, int64_t m, const float* __restrict__ z
                        const float* __restrict__ az, float* __restrict__ zy, const float* __restrict__ wy,
                        const float* __restrict__ bf, const float* __restrict__ cf, double* part) {
   Acc2 a0;
-  GRID_STRIDE(i, m) {
+  VEC4_LOOP(w, m >> 2) {
+    const float4 aa = ld4(az, w), ww = ld4(wy, w), bb = ld4(bf, w);
+    float4 zz;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      el(zz, k) = elc(aa, k) + elc(ww, k);
+      a0.add_prod(elc(bb, k), elc(zz, k));
+    }
+    st4(zy, w, zz);
+  }
+  TAIL_LOOP(i, m) {
     float zi = az[i] + wy[i];
     zy[i] = zi;
     a0.add_prod(bf[i], zi);
   }
-  GRID_STRIDE(i, n) a0.add_prod(cf[i], zx[i]);
+  VEC4_LOOP(w, n >> 2) {
+    const float4 cc = ld4(cf, w), xx = ld4(zx, w);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) a0.add_prod(elc(cc, k), elc(xx, k));
+  }
+  TAIL_LOOP(i, n) a0.add_prod(cf[i], zx[i]);
   double v[1] = {a0.value()};
   if (grid_sum<1>(v, part, &c->red_count) && threadIdx.x == 0)
     c->ut_tau = (c->w_tau + v[0]) / (1.0 + c->hg);
@@ -331,13 +424,14 @@ __device__ __forceinline__ float y_pre(float a, float a1, float ut, float zy, fl
 
 // Per-chunk squared norm of the tail of each second-order cone block of the
 // pre-projection point; the chunk holding a block's head row stores p_head.
-__global__ void k_soc_norm(const Ctl* c, int64_t m_off, const int32_t* __restrict__ chunk_seg,
+__global__ void k_soc_norm(const Ctl* c, const int32_t* __restrict__ chunk_seg,
                            const int64_t* __restrict__ chunk_r0, const int64_t* __restrict__ chunk_r1,
-                           const int64_t* __restrict__ seg_head, const float* __restrict__ zy,
+                           const int64_t* __restrict__ seg_head, const int32_t* __restrict__ seg_c0,
+                           const int32_t* __restrict__ seg_nc, const float* __restrict__ zy,
                            const float* __restrict__ gy, const float* __restrict__ uy,
                            const float* __restrict__ vs, double* __restrict__ chunk_n2,
-                           double* __restrict__ seg_p0) {
-  (void)m_off;
+                           double* __restrict__ seg_p0, double* __restrict__ seg_nrm,
+                           unsigned int* __restrict__ seg_cnt) {
   const int64_t ch = blockIdx.x;
   const int32_t sg = chunk_seg[ch];
   const int64_t head = seg_head[sg];
@@ -353,7 +447,25 @@ __global__ void k_soc_norm(const Ctl* c, int64_t m_off, const int32_t* __restric
   }
   double v[1] = {a0.value()};
   block_sum<1>(v);
-  if (threadIdx.x == 0) chunk_n2[ch] = v[0];
+  // the last chunk of the segment to finish forms the segment's norm once,
+  // adding the chunk partials in chunk order
+  __shared__ int s_last;
+  if (threadIdx.x == 0) {
+    chunk_n2[ch] = v[0];
+    __threadfence();
+    s_last = atomicAdd(&seg_cnt[sg], 1u) == (unsigned)seg_nc[sg] - 1u;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const int32_t c0 = seg_c0[sg], nc = seg_nc[sg];
+  double t[1] = {0.0};
+  for (int32_t k = threadIdx.x; k < nc; k += blockDim.x) t[0] += __ldcg(chunk_n2 + c0 + k);
+  block_sum<1>(t);
+  if (threadIdx.x == 0) {
+    seg_nrm[sg] = sqrt(t[0]);
+    seg_cnt[sg] = 0u;
+  }
 }
 
 // Projection and dual update.  Blocks [0, nlin) cover x (free) and the zero
@@ -367,25 +479,46 @@ __global__ void k_apply(Ctl* c, int64_t n, int64_t m, int64_t z, int64_t l, int 
                         const float* __restrict__ gx, const float* __restrict__ gy,
                         const int32_t* __restrict__ chunk_seg, const int64_t* __restrict__ chunk_r0,
                         const int64_t* __restrict__ chunk_r1, const int64_t* __restrict__ seg_head,
-                        const int32_t* __restrict__ seg_c0, const int32_t* __restrict__ seg_nc,
-                        const double* __restrict__ chunk_n2, const double* __restrict__ seg_p0,
+                        const double* __restrict__ seg_nrm, const double* __restrict__ seg_p0,
                         cudaGraphConditionalHandle h_check, cudaGraphConditionalHandle h_refresh,
                         cudaGraphConditionalHandle h_outer, int in_graph) {
   const double al = c->st.alpha;
   const float a = (float)al, a1 = (float)(1.0 - al), ut = (float)c->ut_tau;
   if ((int)blockIdx.x < nlin) {
-    const int64_t nl = n + z + l;
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t stride = (int64_t)nlin * blockDim.x;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nl; i += stride) {
-      if (i < n) {
-        ux[i] = __fadd_rn(__fmul_rn(a, __fsub_rn(zx[i], __fmul_rn(ut, gx[i]))), __fmul_rn(a1, ux[i]));
-      } else {
-        const int64_t j = i - n;
-        float pj = y_pre(a, a1, ut, zy[j], gy[j], uy[j], vs[j]);
-        float uj = j < z ? pj : fmaxf(pj, 0.f);
-        uy[j] = uj;
-        vs[j] = __fsub_rn(uj, pj);
+    // x (free): u_x = alpha (z_x - u~_tau g_x) + (1 - alpha) u_x
+    for (int64_t v = tid; v < (n >> 2); v += stride) {
+      const float4 zz = ld4(zx, v), gg = ld4(gx, v);
+      float4 uu = ld4(ux, v);
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        el(uu, k) = __fadd_rn(__fmul_rn(a, __fsub_rn(elc(zz, k), __fmul_rn(ut, elc(gg, k)))),
+                              __fmul_rn(a1, el(uu, k)));
+      st4(ux, v, uu);
+    }
+    for (int64_t i = (n & ~(int64_t)3) + tid; i < n; i += stride)
+      ux[i] = __fadd_rn(__fmul_rn(a, __fsub_rn(zx[i], __fmul_rn(ut, gx[i]))), __fmul_rn(a1, ux[i]));
+    // zero rows (dual: free) and nonnegative rows of y
+    const int64_t nl = z + l;
+    for (int64_t v = tid; v < (nl >> 2); v += stride) {
+      const float4 zz = ld4(zy, v), gg = ld4(gy, v);
+      float4 uu = ld4(uy, v), ss = ld4(vs, v);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float pj = y_pre(a, a1, ut, elc(zz, k), elc(gg, k), el(uu, k), el(ss, k));
+        const float uj = (4 * v + k) < z ? pj : fmaxf(pj, 0.f);
+        el(uu, k) = uj;
+        el(ss, k) = __fsub_rn(uj, pj);
       }
+      st4(uy, v, uu);
+      st4(vs, v, ss);
+    }
+    for (int64_t j = (nl & ~(int64_t)3) + tid; j < nl; j += stride) {
+      float pj = y_pre(a, a1, ut, zy[j], gy[j], uy[j], vs[j]);
+      float uj = j < z ? pj : fmaxf(pj, 0.f);
+      uy[j] = uj;
+      vs[j] = __fsub_rn(uj, pj);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       const double uhat = al * c->ut_tau + (1.0 - al) * c->tau;
@@ -415,20 +548,12 @@ __global__ void k_apply(Ctl* c, int64_t n, int64_t m, int64_t z, int64_t l, int 
     }
     return;
   }
-  // second-order cone chunk
+  // second-order cone chunk: its segment's norm and head value come from
+  // k_soc_norm
   const int64_t ch = blockIdx.x - nlin;
   const int32_t sg = chunk_seg[ch];
   const int64_t head = seg_head[sg];
-  __shared__ double s_nrm;
-  {
-    double v[1] = {0.0};
-    const int32_t c0 = seg_c0[sg], nc = seg_nc[sg];
-    for (int32_t k = threadIdx.x; k < nc; k += blockDim.x) v[0] += chunk_n2[c0 + k];
-    block_sum<1>(v);  // fixed order: same norm in every chunk of the block
-    if (threadIdx.x == 0) s_nrm = sqrt(v[0]);
-  }
-  __syncthreads();
-  const double nrm = s_nrm, p0 = seg_p0[sg];
+  const double nrm = seg_nrm[sg], p0 = seg_p0[sg];
   // 0: keep, 1: zero, 2: scale onto the boundary
   const int mode = nrm <= p0 ? 0 : (nrm <= -p0 ? 1 : 2);
   const double ah = 0.5 * (p0 + nrm);
@@ -672,15 +797,15 @@ void gram(const CgBufs& b, const float* x, float* out, cudaStream_t s) {
 // from scratch (fresh = 1).
 void emit_cg_start(const CgBufs& b, int mode, int fresh, const Conds& cd, cudaStream_t s) {
   if (fresh) gram(b, b.z, b.gz, s);
-  k_cg_init<<<grid_for(b.n), kThreads, 0, s>>>(b.ctl, b.n, b.rhs, b.z, b.gz, b.r, b.p, b.part, mode, fresh,
+  k_cg_init<<<red_grid(b.n), kThreads, 0, s>>>(b.ctl, b.n, b.rhs, b.z, b.gz, b.r, b.p, b.part, mode, fresh,
                                                cd.cg, cd.in_graph);
 }
 
 // One CG step (body of the CG WHILE node).
 void emit_cg_step(const CgBufs& b, int mode, const Conds& cd, cudaStream_t s) {
   gram(b, b.p, b.q, s);
-  k_cg_dot<<<grid_for(b.n), kThreads, 0, s>>>(b.ctl, b.n, b.p, b.q, b.part);
-  k_cg_update<<<grid_for(b.n), kThreads, 0, s>>>(b.ctl, b.n, b.m, b.z, b.r, b.p, b.q, b.gz, b.az, b.t,
+  k_cg_dot<<<red_grid(b.n), kThreads, 0, s>>>(b.ctl, b.n, b.p, b.q, b.part);
+  k_cg_update<<<red_grid(b.n), kThreads, 0, s>>>(b.ctl, b.n, b.m, b.z, b.r, b.p, b.q, b.gz, b.az, b.t,
                                                  b.part, mode);
   k_cg_p<<<grid_for(b.n), kThreads, 0, s>>>(b.ctl, b.n, b.r, b.p, mode, cd.cg, cd.in_graph);
 }
@@ -700,7 +825,7 @@ void emit_setup_pre(cf_problem* P, const Conds& cd, cudaStream_t s) {
 void emit_setup_post(cf_problem* P, cudaStream_t s) {
   const int64_t n = P->n, m = P->m;
   op_apply(P->A, false, 1.f, P->gx, P->gy, false, P->ws, s);  // exact A g_x
-  k_setup_fin<<<grid_for(std::max(n, m)), kThreads, 0, s>>>(P->ctl, n, m, P->gx, P->gy, P->bf, P->cf, P->part);
+  k_setup_fin<<<red_grid(std::max(n, m)), kThreads, 0, s>>>(P->ctl, n, m, P->gx, P->gy, P->bf, P->cf, P->part);
 }
 
 void emit_init(cf_problem* P, cudaStream_t s) {
@@ -720,17 +845,18 @@ void emit_pre_cg(cf_problem* P, const Conds& cd, cudaStream_t s) {
 // subspace step, projection, dual update
 void emit_post_cg(cf_problem* P, const Conds& cd, cudaStream_t s) {
   const int64_t n = P->n, m = P->m;
-  k_utau<<<grid_for(std::max(n, m)), kThreads, 0, s>>>(P->ctl, n, m, P->zx, P->az, P->zy, P->wy, P->bf, P->cf,
+  k_utau<<<red_grid(std::max(n, m)), kThreads, 0, s>>>(P->ctl, n, m, P->zx, P->az, P->zy, P->wy, P->bf, P->cf,
                                                        P->part);
   if (P->nchunk > 0)
-    k_soc_norm<<<(unsigned)P->nchunk, kThreads, 0, s>>>(P->ctl, 0, P->chunk_seg, P->chunk_r0, P->chunk_r1,
-                                                        P->seg_head, P->zy, P->gy, P->uy, P->vs,
-                                                        P->chunk_n2, P->seg_p0);
-  const int nlin = grid_for(n + P->z + P->l);
+    k_soc_norm<<<(unsigned)P->nchunk, kThreads, 0, s>>>(P->ctl, P->chunk_seg, P->chunk_r0, P->chunk_r1,
+                                                        P->seg_head, P->seg_c0, P->seg_nc, P->zy, P->gy,
+                                                        P->uy, P->vs, P->chunk_n2, P->seg_p0, P->seg_nrm,
+                                                        P->seg_cnt);
+  const int nlin = grid_for(std::max<int64_t>(n, P->z + P->l));
   k_apply<<<(unsigned)(nlin + P->nchunk), kThreads, 0, s>>>(
       P->ctl, n, m, P->z, P->l, nlin, P->ux, P->uy, P->vs, P->zx, P->zy, P->gx, P->gy, P->chunk_seg,
-      P->chunk_r0, P->chunk_r1, P->seg_head, P->seg_c0, P->seg_nc, P->chunk_n2, P->seg_p0, cd.check,
-      cd.refresh, cd.outer, cd.in_graph);
+      P->chunk_r0, P->chunk_r1, P->seg_head, P->seg_nrm, P->seg_p0, cd.check, cd.refresh, cd.outer,
+      cd.in_graph);
 }
 
 // residuals and certificates (every check_interval iterations)
@@ -738,7 +864,7 @@ void emit_check(cf_problem* P, const Conds& cd, cudaStream_t s) {
   const int64_t n = P->n, m = P->m;
   op_apply(P->A, false, 1.f, P->ux, P->cm, false, P->ws, s);
   op_apply(P->A, true, 1.f, P->uy, P->cn, false, P->ws, s);
-  k_resid<<<grid_for(std::max(n, m)), kThreads, 0, s>>>(P->ctl, n, m, P->cm, P->cn, P->ux, P->uy, P->vs,
+  k_resid<<<red_grid(std::max(n, m)), kThreads, 0, s>>>(P->ctl, n, m, P->cm, P->cn, P->ux, P->uy, P->vs,
                                                         P->bf, P->cf, P->part, cd.outer, cd.in_graph);
 }
 
@@ -913,7 +1039,7 @@ size_t problem_state_bytes(const cf_problem* P) {
   b += 8 * f(m);            // uy vs wy t zy gy cm az
   b += f(wsf);
   b += d((size_t)kMaxRedBlocks * kRedSlots);
-  b += d((size_t)std::max<int64_t>(P->nchunk, 1)) + d((size_t)std::max<int64_t>(P->nseg, 1));
+  b += d((size_t)std::max<int64_t>(P->nchunk, 1)) + 3 * d((size_t)std::max<int64_t>(P->nseg, 1));
   b += 2 * d(2 * N);        // warm_dev, uv_dev
   b += d(n + 2 * m);        // out_dev
   b += align_up(sizeof(Ctl), 256);
@@ -944,11 +1070,14 @@ cf_err ensure_state(cf_problem* P) {
   P->part = taked((size_t)kMaxRedBlocks * kRedSlots);
   P->chunk_n2 = taked((size_t)std::max<int64_t>(P->nchunk, 1));
   P->seg_p0 = taked((size_t)std::max<int64_t>(P->nseg, 1));
+  P->seg_nrm = taked((size_t)std::max<int64_t>(P->nseg, 1));
+  P->seg_cnt = (unsigned int*)taked((size_t)std::max<int64_t>(P->nseg, 1));
   P->warm_dev = taked(2 * N);
   P->uv_dev = taked(2 * N);
   P->out_dev = taked(n + 2 * m);
   P->ctl = (Ctl*)cur;
   CF_CUDA(cudaMemsetAsync(P->ctl, 0, sizeof(Ctl), P->stream));
+  CF_CUDA(cudaMemsetAsync(P->seg_cnt, 0, sizeof(double) * std::max<int64_t>(P->nseg, 1), P->stream));
   CF_CUDA(cudaMemsetAsync(P->warm_dev, 0, 2 * N * sizeof(double), P->stream));
   CF_CUDA(cudaStreamSynchronize(P->stream));
   P->ctl_host->nb = P->nb;

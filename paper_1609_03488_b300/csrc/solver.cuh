@@ -56,7 +56,8 @@ struct cf_problem {
   size_t state_bytes = 0;
   float *ux, *uy, *vs, *zx, *rhs, *r, *p, *qv, *wy, *t, *zy, *gx, *gy, *cm, *cn, *ws;
   float *gz, *az;  // G z_x and A z_x, carried by the CG updates
-  double *part, *chunk_n2, *seg_p0, *warm_dev, *out_dev, *uv_dev;
+  double *part, *chunk_n2, *seg_p0, *seg_nrm, *warm_dev, *out_dev, *uv_dev;
+  unsigned int* seg_cnt = nullptr;  // per-segment tickets of the SOC norm
   cf::Ctl* ctl = nullptr;       // device
   cf::Ctl* ctl_host = nullptr;  // pinned mirror
   void* flags_host = nullptr;   // pinned copy of the loop decisions (host-driven mode)
