@@ -32,6 +32,9 @@ os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 from paper_1609_03488_b300 import synth  # noqa: E402
 
 WORKLOAD = dict(n_x=1_000_000, L=1000, sigma=100.0, support=0.01, noise=0.01, seed=synth.BASE_SEED + 2)
+WORKLOAD_SMALL = dict(n_x=1000, L=100, sigma=10.0, support=0.05, noise=0.01, seed=synth.BASE_SEED + 1)
+WORKLOAD_SMALL_NAME = ("small 1-D nonnegative deconvolution: n=1000, Gaussian kernel L=100 sigma=10, 5% nonneg "
+                       "support Exp(1), noise 0.01; SCS cone form n=1001 m=2100; a step is a full solve to 1e-4")
 WORKLOAD_NAME = ("large 1-D nonnegative deconvolution: n=1e6, Gaussian kernel L=1000 sigma=100, "
                  "1% nonneg support Exp(1), noise 0.01; SCS cone form n=1000001 m=2001000 (1 SOC + nonneg)")
 METRIC = "ADMM iters/s"
@@ -55,7 +58,7 @@ def parse():
     ap.add_argument("--cpu-iters", type=int, default=6, help="ADMM iterations of the oracle sample")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="deconv", choices=["deconv", "lasso", "lp-batch", "serve", "ops"],
+    ap.add_argument("--workload", default="deconv", choices=["deconv", "deconv-small", "lasso", "lp-batch", "serve", "ops"],
                     help="deconv (default): the large deconvolution; lp-batch: batch of sparse LPs of "
                          "uneven size; serve: Poisson-arrival serving trace")
     ap.add_argument("--batch-count", type=int, default=512)
@@ -138,13 +141,13 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ oracle
-def cpu_sample(prob, iters):
+def cpu_sample(prob, iters, label):
     """The FP64 oracle (matrix-free, CG linear solves) on the same instance
     for a bounded number of ADMM iterations on the host cores."""
     from oracle import scs
     r = scs.problem_solve(prob, eps=1e-4, max_iters=iters, linsys="cg")
     return {"value": r["iters"] / r["t_iter"], "unit": METRIC, "cores": 1, "kind": "oracle",
-            "sample": (f"{r['iters']} ADMM iterations of the same n=1e6 instance (FP64, matrix-free "
+            "sample": (f"{r['iters']} ADMM iterations of the same {label} instance (FP64, matrix-free "
                        f"numpy.convolve operators, CG subspace solves; setup {r['t_setup']:.1f} s excluded, "
                        f"iterations {r['t_iter']:.1f} s; single-threaded numpy.convolve dominates)"),
             "affinity_cores": len(os.sched_getaffinity(0))}
@@ -453,7 +456,10 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    if args.workload != "deconv":
+    small = args.workload == "deconv-small"
+    if small:
+        args.iters_per_step = max(args.iters_per_step, 20000)
+    if args.workload not in ("deconv", "deconv-small"):
         stream = torch.cuda.Stream(device=local)
         torch.cuda.set_stream(stream)
         ctx = B.Context(local, stream.cuda_stream)
@@ -465,7 +471,8 @@ def main():
             print(json.dumps(line), flush=True)
         return
 
-    prob = synth.deconv(**{**WORKLOAD, "seed": WORKLOAD["seed"] + rank})
+    W = WORKLOAD_SMALL if small else WORKLOAD
+    prob = synth.deconv(**{**W, "seed": W["seed"] + rank})
     n, m = prob["A"]["n"], prob["A"]["m"]
     # a dedicated (non-default) stream: the library launches on it and the
     # CUDA events below are recorded on it
@@ -514,10 +521,10 @@ def main():
     value = it_total / (t_max / 1e3)
 
     # ---- dominant kernel: the 1-D convolution, timed live on the same stream
-    conv = B.cf_op_conv1d(ctx, prob["meta"]["kernel"], WORKLOAD["n_x"])
-    L = WORKLOAD["L"]
-    xin = torch.rand(WORKLOAD["n_x"], device=dev)
-    yin = torch.rand(WORKLOAD["n_x"] + L - 1, device=dev)
+    conv = B.cf_op_conv1d(ctx, prob["meta"]["kernel"], W["n_x"])
+    L = W["L"]
+    xin = torch.rand(W["n_x"], device=dev)
+    yin = torch.rand(W["n_x"] + L - 1, device=dev)
     xout = torch.empty_like(xin)
     yout = torch.empty_like(yin)
     for _ in range(3):
@@ -537,8 +544,8 @@ def main():
     torch.cuda.synchronize()
     t_fwd = e0.elapsed_time(e1) / reps / 1e3
     t_adj = e2.elapsed_time(e3) / reps / 1e3
-    flops_fwd = 2.0 * L * (WORKLOAD["n_x"] + L - 1)
-    flops_adj = 2.0 * L * WORKLOAD["n_x"]
+    flops_fwd = 2.0 * L * (W["n_x"] + L - 1)
+    flops_adj = 2.0 * L * W["n_x"]
     achieved = (flops_fwd + flops_adj) / (t_fwd + t_adj) / 1e12
     pk = peaks()
     sm_count = ctx.sm_count
@@ -546,7 +553,8 @@ def main():
     alu_peak = sm_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     roofline = {"bound": "alu", "kernel": "k_conv1d", "achieved": achieved, "peak": alu_peak,
                 "unit": "TFLOP/s", "frac": achieved / alu_peak,
-                "traffic": CONV_NCU["traffic_bytes"] if conv_src_sha() == CONV_NCU["src_sha256_16"] else None,
+                "traffic": (CONV_NCU["traffic_bytes"] if conv_src_sha() == CONV_NCU["src_sha256_16"] and not small
+                            else None),
                 "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
                 "peak_source": f"derived: {sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x {sm_max:.0f} MHz (max SM clock of measured)",
                 "per_launch_ms": {"forward": 1e3 * t_fwd, "adjoint": 1e3 * t_adj},
@@ -593,13 +601,13 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu:
-        cpu = cpu_sample(prob, args.cpu_iters)
+        cpu = cpu_sample(prob, max(args.cpu_iters, 20000) if small else args.cpu_iters, "n=1000" if small else "n=1e6")
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": WORKLOAD_NAME, "n": n, "m": m,
+                "config": {"workload": WORKLOAD_SMALL_NAME if small else WORKLOAD_NAME, "n": n, "m": m,
                            "step": f"one solve from u=v=(0,0,1), capped at {args.iters_per_step} ADMM iterations, "
                                    "eps 1e-4 checked every 10 iterations",
                            "l2": "flushed between steps (256 MB write)",
