@@ -108,7 +108,46 @@ typedef struct {
                          kernels and reads each loop decision back (slower; for
                          profilers that do not see kernels inside graph
                          conditional nodes, and for debugging). */
+  int32_t engine;     /* cf_engine: which of the two solver programs runs the
+                         iterations (CF_ENGINE_AUTO). */
 } cf_settings;
+
+/* The solver has two programs for the same iteration:
+ *  - the graph engine: one CUDA graph per solve whose kernels each spread
+ *    one step over the whole GPU (large problems);
+ *  - the team engine: one persistent kernel in which a team of CTAs (one CTA,
+ *    or a thread-block cluster) runs a problem's whole solve, synchronising
+ *    with barriers instead of kernel boundaries, and a batch is one launch
+ *    whose teams take problems from a longest-first work queue (small and
+ *    medium problems, batches, serving).
+ * Both compute the same iteration; their float32 rounding differs (other
+ * reduction partitions).  The team engine supports operator trees of dense,
+ * CSR, 1-D convolution (<= 2048 taps), diagonal and zero leaves under vstack,
+ * hstack, blockdiag, sum, scale and adjoint, with at most 4 second-order
+ * cones and dense leaves of at most 16384 columns. */
+typedef enum {
+  CF_ENGINE_AUTO = 0,  /* team engine when the problem is supported and one
+                          operator pass is at most the schedule's
+                          auto_max_bytes; graph engine otherwise */
+  CF_ENGINE_GRAPH = 1, /* always the graph engine */
+  CF_ENGINE_TEAM = 2   /* always the team engine (CF_E_INVALID if the
+                          problem is not supported) */
+} cf_engine;
+
+/* Launch schedule of the team engine, held by the context.  A problem's
+ * iterates depend on the schedule it ran with (it fixes the reduction
+ * partitions), never on the other problems of a batch. */
+typedef struct {
+  int32_t cluster;         /* CTAs per cluster team: 1, 2, 4 or 8 (4) */
+  int32_t threads;         /* threads per CTA: 256, 512 or 1024 (512) */
+  int32_t csr_nnz_per_lane;/* CSR rows get 2^k lanes (1..32), the power of two
+                              nearest avg nnz per row / this (4) */
+  int32_t reserved;
+  double team_bytes;       /* problems whose operator pass reads at least this
+                              many bytes run on a whole cluster team; smaller
+                              ones on one CTA (4e6) */
+  double auto_max_bytes;   /* CF_ENGINE_AUTO limit (48e6) */
+} cf_schedule;
 
 typedef struct {
   int32_t status;          /* cf_status */
@@ -248,11 +287,47 @@ void cf_problem_destroy(cf_problem* p);
 cf_err solve(cf_problem* p, const cf_settings* settings, double* x, double* y, double* s,
              const double* warm_uv, double* uv_out, cf_info* info);
 
-/* Solve count problems concurrently (one CUDA stream each).  xs/ys/ss may be
+/* Solve count problems concurrently: the team-engine problems in one
+ * persistent launch (longest first), each graph-engine problem on a CUDA
+ * stream of its own.  xs/ys/ss may be
  * NULL or arrays of count pointers (entries may be NULL); infos may be NULL.
  * Returns the first error; every problem is attempted. */
 cf_err solve_batch(cf_problem* const* probs, int32_t count, const cf_settings* settings,
                    double* const* xs, double* const* ys, double* const* ss, cf_info* infos);
+
+/* The team engine's view of a problem: *supported = 1 when the team engine
+ * can run it (else 0, and why -- when not NULL -- receives the reason,
+ * NUL-terminated, at most why_len bytes); *pass_bytes = the bytes (and
+ * flop-equivalents of convolutions) one forward operator pass reads, the size
+ * that cf_schedule's team_bytes and auto_max_bytes are compared with.  Any
+ * output pointer may be NULL. */
+cf_err cf_problem_team_info(const cf_problem* p, int32_t* supported, double* pass_bytes, char* why,
+                            size_t why_len);
+
+/* The context's team-engine schedule (see cf_schedule).  Setting it
+ * validates every field (CF_E_INVALID) and applies to later solves. */
+cf_err cf_ctx_get_schedule(const cf_ctx* ctx, cf_schedule* out);
+cf_err cf_ctx_set_schedule(cf_ctx* ctx, const cf_schedule* sched);
+
+typedef struct {
+  int32_t candidates;  /* schedules timed */
+  int32_t problems;    /* team-engine problems of the batch that were timed */
+  double seconds;      /* wall time of the tuning */
+  double default_ms;   /* batch time of the schedule held before tuning */
+  double best_ms;      /* batch time of the chosen schedule */
+  cf_schedule best;    /* now held by the context */
+} cf_tune_info;
+
+/* Autotuner of the team engine (a schedule search; the paper has no
+ * counterpart -- it solves one problem at a time): times `iters` ADMM
+ * iterations (2 CG steps each, no residual checks) of the batch's
+ * team-engine problems under candidate schedules -- threads per CTA and CSR
+ * lanes per row first, then the cluster size and the size threshold between
+ * cluster teams and one-CTA teams -- and stores the fastest in the problems'
+ * context.  The problems must share one context; their iterates are
+ * overwritten and their setup is redone at the next solve.  info may be
+ * NULL. */
+cf_err solve_batch_tune(cf_problem* const* probs, int32_t count, int32_t iters, cf_tune_info* info);
 
 /* Regularized least squares (Section 5.1): x = (lam I + A^T A)^{-1} rhs by CG
  * from x's initial contents, stopping when ||r|| <= tol ||rhs|| (the paper's

@@ -42,7 +42,29 @@ class cf_settings(C.Structure):
                 ("cg_max_iters", C.c_int32), ("cg_fixed_iters", C.c_int32),
                 ("cg_tol_rel", C.c_double), ("cg_tol_exp", C.c_double), ("cg_tol_min", C.c_double),
                 ("setup_cg_max_iters", C.c_int32), ("setup_cg_tol", C.c_double),
-                ("host_loop", C.c_int32)]
+                ("host_loop", C.c_int32), ("engine", C.c_int32)]
+
+
+CF_ENGINE_AUTO, CF_ENGINE_GRAPH, CF_ENGINE_TEAM = 0, 1, 2
+ENGINE = {"auto": CF_ENGINE_AUTO, "graph": CF_ENGINE_GRAPH, "team": CF_ENGINE_TEAM}
+
+
+class cf_schedule(C.Structure):
+    _fields_ = [("cluster", C.c_int32), ("threads", C.c_int32), ("csr_nnz_per_lane", C.c_int32),
+                ("reserved", C.c_int32), ("team_bytes", C.c_double), ("auto_max_bytes", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+class cf_tune_info(C.Structure):
+    _fields_ = [("candidates", C.c_int32), ("problems", C.c_int32), ("seconds", C.c_double),
+                ("default_ms", C.c_double), ("best_ms", C.c_double), ("best", cf_schedule)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "best"}
+        d["best"] = self.best.as_dict()
+        return d
 
 
 class cf_info(C.Structure):
@@ -84,6 +106,11 @@ _sig = {
     "cf_problem_destroy": (None, [P]),
     "solve": (C.c_int, [P, C.POINTER(cf_settings), P, P, P, P, P, C.POINTER(cf_info)]),
     "solve_batch": (C.c_int, [PP, C.c_int32, C.POINTER(cf_settings), PP, PP, PP, C.POINTER(cf_info)]),
+    "solve_batch_tune": (C.c_int, [PP, C.c_int32, C.c_int32, C.POINTER(cf_tune_info)]),
+    "cf_ctx_get_schedule": (C.c_int, [P, C.POINTER(cf_schedule)]),
+    "cf_ctx_set_schedule": (C.c_int, [P, C.POINTER(cf_schedule)]),
+    "cf_problem_team_info": (C.c_int, [P, C.POINTER(C.c_int32), C.POINTER(C.c_double), C.c_char_p,
+                                       C.c_size_t]),
     "cg_solve": (C.c_int, [P, C.c_double, P, P, C.c_int32, C.c_double, C.POINTER(C.c_int32),
                            C.POINTER(C.c_double)]),
     "serve_create": (C.c_int, [P, C.c_size_t, C.c_int32, PP]),
@@ -153,8 +180,28 @@ def settings(**kw):
     for k, v in kw.items():
         if not hasattr(s, k):
             raise KeyError(k)
+        if k == "engine" and isinstance(v, str):
+            v = ENGINE[v]
         setattr(s, k, v)
     return s
+
+
+def get_schedule(ctx):
+    s = cf_schedule()
+    check(lib.cf_ctx_get_schedule(ctx.h, C.byref(s)), "cf_ctx_get_schedule")
+    return s.as_dict()
+
+
+def set_schedule(ctx, **kw):
+    """Change fields of the context's team-engine schedule."""
+    s = cf_schedule()
+    check(lib.cf_ctx_get_schedule(ctx.h, C.byref(s)), "cf_ctx_get_schedule")
+    for k, v in kw.items():
+        if k == "reserved" or not hasattr(s, k):
+            raise KeyError(k)
+        setattr(s, k, v)
+    check(lib.cf_ctx_set_schedule(ctx.h, C.byref(s)), "cf_ctx_set_schedule")
+    return s.as_dict()
 
 
 class Context:
@@ -362,6 +409,22 @@ def solve_batch(problems, st=None):
     infos = (cf_info * k)()
     check(lib.solve_batch(hs, k, C.byref(st) if st is not None else None, px, py, ps, infos), "solve_batch")
     return [i.as_dict() for i in infos], xs, ys, ss
+
+
+def team_info(problem):
+    """(supported, pass_bytes, why) of the team engine for a problem."""
+    ok, nb = C.c_int32(), C.c_double()
+    buf = C.create_string_buffer(256)
+    check(lib.cf_problem_team_info(problem.h, C.byref(ok), C.byref(nb), buf, 256), "cf_problem_team_info")
+    return bool(ok.value), nb.value, buf.value.decode()
+
+
+def solve_batch_tune(problems, iters=20):
+    k = len(problems)
+    hs = (C.c_void_p * k)(*[p.h.value for p in problems])
+    info = cf_tune_info()
+    check(lib.solve_batch_tune(hs, k, int(iters), C.byref(info)), "solve_batch_tune")
+    return info.as_dict()
 
 
 def cg_solve(op, lam, rhs, x0=None, max_iters=1000, tol=1e-8):

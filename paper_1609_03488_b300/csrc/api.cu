@@ -62,6 +62,7 @@ void cf_settings_default(cf_settings* s) {
   s->cg_tol_min = 1e-9;
   s->setup_cg_max_iters = 2000;
   s->setup_cg_tol = 1e-7;
+  s->engine = CF_ENGINE_AUTO;
 }
 
 cf_err cf_ctx_create(int device, void* cuda_stream, cf_ctx** out) {
@@ -89,6 +90,7 @@ cf_err cf_ctx_create(int device, void* cuda_stream, cf_ctx** out) {
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
   c->sm_count = sms;
+  c->sched = default_schedule();
   *out = c;
   return CF_OK;
 }
@@ -103,6 +105,22 @@ void cf_ctx_destroy(cf_ctx* c) {
 }
 
 int cf_ctx_sm_count(const cf_ctx* c) { return c ? c->sm_count : 0; }
+
+cf_err cf_ctx_get_schedule(const cf_ctx* c, cf_schedule* out) {
+  if (!c || !out) return fail(CF_E_INVALID, "cf_ctx_get_schedule: NULL argument");
+  std::lock_guard<std::mutex> lk(const_cast<cf_ctx*>(c)->sched_mu);
+  *out = c->sched;
+  return CF_OK;
+}
+
+cf_err cf_ctx_set_schedule(cf_ctx* c, const cf_schedule* s) {
+  if (!c || !s) return fail(CF_E_INVALID, "cf_ctx_set_schedule: NULL argument");
+  std::string why;
+  if (!schedule_valid(*s, &why)) return fail(CF_E_INVALID, "cf_ctx_set_schedule: " + why);
+  std::lock_guard<std::mutex> lk(c->sched_mu);
+  c->sched = *s;
+  return CF_OK;
+}
 
 const char* cf_last_error(void) { return g_last_error.c_str(); }
 

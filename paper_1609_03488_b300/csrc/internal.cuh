@@ -6,6 +6,7 @@
 #include <cuda_fp8.h>
 
 #include <atomic>
+#include <mutex>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -57,6 +58,10 @@ inline int red_grid(int64_t n) {
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// Team-engine schedule held by a new context.
+cf_schedule default_schedule();
+bool schedule_valid(const cf_schedule& s, std::string* why);
+
 }  // namespace cf
 
 // ----------------------------------------------------------------- context
@@ -65,6 +70,8 @@ struct cf_ctx {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   int sm_count = 148;
+  std::mutex sched_mu;   // guards sched
+  cf_schedule sched{};   // team-engine launch schedule
 };
 
 // ---------------------------------------------------------------- operators

@@ -1,6 +1,6 @@
 // Leaf kernels of the structured operators (Section 3.1): every kernel
 // computes y = alpha * op(x) + (acc ? y : 0).
-#include "internal.cuh"
+#include "devutil.cuh"
 
 namespace cf {
 
@@ -236,44 +236,6 @@ void launch_conv2d(cudaStream_t s, int64_t Ho, int64_t Wo, int64_t Hi, int64_t W
 }
 
 // ------------------------------------------------------------ dense GEMV
-// 16-byte loads of the stored operand, unpacked to float32.
-template <typename T> struct Vec;
-template <> struct Vec<float> {
-  static constexpr int N = 4;
-  __device__ static void unpack(const uint4& u, float* f) {
-    f[0] = __uint_as_float(u.x); f[1] = __uint_as_float(u.y);
-    f[2] = __uint_as_float(u.z); f[3] = __uint_as_float(u.w);
-  }
-};
-template <> struct Vec<__nv_bfloat16> {
-  static constexpr int N = 8;
-  __device__ static void unpack(const uint4& u, float* f) {
-    const uint32_t w[4] = {u.x, u.y, u.z, u.w};
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      f[2 * k] = __uint_as_float(w[k] << 16);
-      f[2 * k + 1] = __uint_as_float(w[k] & 0xffff0000u);
-    }
-  }
-};
-template <> struct Vec<__nv_fp8_e4m3> {
-  static constexpr int N = 16;
-  __device__ static void unpack(const uint4& u, float* f) {
-    const uint32_t w[4] = {u.x, u.y, u.z, u.w};
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-#pragma unroll
-      for (int b = 0; b < 4; b += 2) {
-        __nv_fp8x2_storage_t pair = (__nv_fp8x2_storage_t)((w[k] >> (8 * b)) & 0xffff);
-        __half2_raw h2 = __nv_cvt_fp8x2_to_halfraw2(pair, __NV_E4M3);
-        __half2 hh = *reinterpret_cast<__half2*>(&h2);
-        float2 ff = __half22float2(hh);
-        f[4 * k + b] = ff.x;
-        f[4 * k + b + 1] = ff.y;
-      }
-    }
-  }
-};
 
 // y[i] = alpha * s_i * sum_j A[i, j] x[j]: a warp handles RW rows, so each
 // slice of x it loads is reused RW times; the RW operand loads are issued

@@ -23,6 +23,7 @@
 #include <cstring>
 #include <memory>
 
+#include "devutil.cuh"
 #include "solver.cuh"
 
 namespace cf {
@@ -110,38 +111,6 @@ __device__ bool grid_sum(double (&v)[NV], double* part, unsigned int* counter) {
 #define TAIL_LOOP(i, n)                                                                  \
   for (int64_t i = ((n) & ~(int64_t)3) + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; \
        i < (n); i += (int64_t)gridDim.x * blockDim.x)
-
-__device__ __forceinline__ float4 ld4(const float* p, int64_t v) {
-  return reinterpret_cast<const float4*>(p)[v];
-}
-__device__ __forceinline__ void st4(float* p, int64_t v, float4 a) { reinterpret_cast<float4*>(p)[v] = a; }
-__device__ __forceinline__ float& el(float4& a, int k) { return (&a.x)[k]; }
-__device__ __forceinline__ float elc(const float4& a, int k) { return (&a.x)[k]; }
-
-// Per-thread sum in compensated float32 ("double-float": hi + lo), with each
-// product taken exactly (p + e, e = fma(a, b, -p)) and each addition by
-// TwoSum.  Its accuracy is close to float64 accumulation without a float64
-// operation per element (the float64 rate of this GPU is a small fraction of
-// its float32 rate); the per-thread value feeds the float64 block and grid
-// sums.  Explicit-rounding intrinsics keep the compiler from contracting
-// the error terms away.
-struct Acc2 {
-  float hi = 0.f, lo = 0.f;
-  __device__ __forceinline__ void add(float x) {
-    const float s = __fadd_rn(hi, x);
-    const float bb = __fsub_rn(s, hi);
-    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(x, bb));
-    hi = s;
-    lo = __fadd_rn(lo, err);
-  }
-  __device__ __forceinline__ void add_prod(float a, float b) {
-    const float p = __fmul_rn(a, b);
-    const float e = __fmaf_rn(a, b, -p);
-    add(p);
-    lo = __fadd_rn(lo, e);
-  }
-  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
-};
 
 // ------------------------------------------------------------ iteration start
 __global__ void k_init(Ctl* c, int64_t n, int64_t m, float* ux, float* uy, float* vs, float* zx,
@@ -410,16 +379,6 @@ __global__ void k_utau(Ctl* c, int64_t n, int64_t m, const float* __restrict__ z
   double v[1] = {a0.value()};
   if (grid_sum<1>(v, part, &c->red_count) && threadIdx.x == 0)
     c->ut_tau = (c->w_tau + v[0]) / (1.0 + c->hg);
-}
-
-// The point projected onto K* for row i of y:
-//   p_i = (alpha (z_y - u~_tau g_y) + (1 - alpha) u_y) - v_s
-// evaluated with explicit roundings so both kernels that need it agree bit
-// for bit.
-__device__ __forceinline__ float y_pre(float a, float a1, float ut, float zy, float gy, float uy,
-                                       float vs) {
-  float uhat = __fadd_rn(__fmul_rn(a, __fsub_rn(zy, __fmul_rn(ut, gy))), __fmul_rn(a1, uy));
-  return __fsub_rn(uhat, vs);
 }
 
 // Per-chunk squared norm of the tail of each second-order cone block of the
@@ -1038,6 +997,7 @@ size_t problem_state_bytes(const cf_problem* P) {
   b += 9 * f(n);            // ux zx rhs r p q gx cn gz
   b += 8 * f(m);            // uy vs wy t zy gy cm az
   b += f(wsf);
+  b += f(std::max<size_t>(team::scratch_floats(P), 1));
   b += d((size_t)kMaxRedBlocks * kRedSlots);
   b += d((size_t)std::max<int64_t>(P->nchunk, 1)) + 3 * d((size_t)std::max<int64_t>(P->nseg, 1));
   b += 2 * d(2 * N);        // warm_dev, uv_dev
@@ -1067,6 +1027,7 @@ cf_err ensure_state(cf_problem* P) {
   P->zy = takef(m); P->gy = takef(m); P->cm = takef(m);
   P->gz = takef(n); P->az = takef(m);
   P->ws = takef(std::max(op_ws_floats(P->A, false), op_ws_floats(P->A, true)));
+  P->team_scratch = takef(std::max<size_t>(team::scratch_floats(P), 1));
   P->part = taked((size_t)kMaxRedBlocks * kRedSlots);
   P->chunk_n2 = taked((size_t)std::max<int64_t>(P->nchunk, 1));
   P->seg_p0 = taked((size_t)std::max<int64_t>(P->nseg, 1));
@@ -1099,6 +1060,7 @@ void release_state(cf_problem* P) {
   P->setup_graph = nullptr;
   if (P->arena) cudaFree(P->arena);
   P->arena = nullptr;
+  P->team_scratch = nullptr;
   P->setup_done = false;
 }
 
@@ -1116,10 +1078,13 @@ bool settings_valid(const cf_settings* st, std::string* why) {
   if (!(st->cg_tol_rel >= 0) || !(st->cg_tol_min >= 0) || !std::isfinite(st->cg_tol_exp))
     return bad("CG tolerance parameters must be >= 0");
   if (st->host_loop != 0 && st->host_loop != 1) return bad("host_loop must be 0 or 1");
+  if (st->engine != CF_ENGINE_AUTO && st->engine != CF_ENGINE_GRAPH && st->engine != CF_ENGINE_TEAM)
+    return bad("engine must be CF_ENGINE_AUTO, CF_ENGINE_GRAPH or CF_ENGINE_TEAM");
+  if (st->host_loop && st->engine == CF_ENGINE_TEAM) return bad("host_loop runs the graph engine's kernels");
   return true;
 }
 
-static void write_settings(cf_problem* P, const cf_settings* st, bool warm) {
+void write_settings(cf_problem* P, const cf_settings* st, bool warm) {
   Settings& s = P->ctl_host->st;
   s.alpha = st->alpha;
   s.eps = st->eps;
@@ -1141,6 +1106,7 @@ static void write_settings(cf_problem* P, const cf_settings* st, bool warm) {
 // CG step count arrives with the control block copied back after the solve.
 static cf_err run_setup(cf_problem* P, bool host_loop) {
   if (!P->setup_exec) CF_TRY(build_setup_graph(P));  // also gives the kernel counts
+  P->setup_sig = 1;
   CF_CUDA(cudaMemcpyAsync(&P->ctl->st, &P->ctl_host->st, sizeof(Settings), cudaMemcpyHostToDevice, P->stream));
   if (host_loop) {
     int64_t dummy = 0;
@@ -1162,13 +1128,25 @@ cf_err solve_launch(cf_problem* P, const cf_settings* st_in, double* x, double* 
   std::string why;
   if (!settings_valid(&st, &why)) return fail(CF_E_INVALID, "solve: " + why);
   const int64_t t0 = now_ns();
+  int engine = CF_ENGINE_GRAPH;
+  CF_TRY(pick_engine(P, &st, &engine));
   CF_TRY(ensure_state(P));
   write_settings(P, &st, warm_uv != nullptr);
   P->ran_setup = false;
+  if (engine == CF_ENGINE_TEAM) {
+    P->x_out = x;
+    P->y_out = y;
+    P->s_out = s;
+    P->uv_out = uv_out;
+    CF_TRY(team::solo_launch(P, &st, warm_uv, join_ctx));
+    P->setup_ns_last = P->ran_setup ? now_ns() - t0 : 0;
+    return CF_OK;
+  }
+  P->last_engine = CF_ENGINE_GRAPH;
   // order after earlier work on the context stream
   CF_CUDA(cudaEventRecord(P->ev_in, P->ctx->stream));
   CF_CUDA(cudaStreamWaitEvent(P->stream, P->ev_in, 0));
-  if (!P->setup_done) {
+  if (!P->setup_done || P->setup_sig != 1) {
     CF_TRY(run_setup(P, st.host_loop != 0));
     P->ran_setup = true;
     P->setup_ns_last = now_ns() - t0;
@@ -1232,12 +1210,16 @@ cf_err solve_finish(cf_problem* P, cf_info* info) {
     info->kappa = c.kappa;
     info->setup_ns = P->setup_ns_last;
     info->solve_ns = t1 - P->t_launch;
-    int64_t kl = P->kc.top + (int64_t)c.k * P->kc.body + c.cg_total * P->kc.cg +
-                 (int64_t)c.checks * P->kc.check + (int64_t)c.refreshes * P->kc.refresh;
-    if (P->x_out || P->y_out || P->s_out) kl += 1;
-    if (P->uv_out) kl += 1;
-    if (P->ran_setup) kl += P->skc.top + (int64_t)P->setup_iters_last * P->skc.cg;
-    info->kernel_launches = kl;
+    if (P->last_engine == CF_ENGINE_TEAM) {
+      info->kernel_launches = P->team_launches;  // the whole solve is one persistent launch
+    } else {
+      int64_t kl = P->kc.top + (int64_t)c.k * P->kc.body + c.cg_total * P->kc.cg +
+                   (int64_t)c.checks * P->kc.check + (int64_t)c.refreshes * P->kc.refresh;
+      if (P->x_out || P->y_out || P->s_out) kl += 1;
+      if (P->uv_out) kl += 1;
+      if (P->ran_setup) kl += P->skc.top + (int64_t)P->setup_iters_last * P->skc.cg;
+      info->kernel_launches = kl;
+    }
   }
   return CF_OK;
 }
@@ -1440,6 +1422,11 @@ cf_err cone_problem_create(cf_ctx* ctx, const cf_op* A, const double* b, int64_t
   } else {
     op_retain(const_cast<cf_op*>(A));
     P->A = const_cast<cf_op*>(A);
+    r = team::plan_problem(P.get());
+    if (r != CF_OK) {
+      cf_problem_destroy(P.release());
+      return r;
+    }
     *out = P.release();
   }
   return r;
@@ -1450,6 +1437,7 @@ void cf_problem_destroy(cf_problem* P) {
   DevGuard guard(P->device);
   if (P->stream) cudaStreamSynchronize(P->stream);
   release_state(P);
+  team::release(P);
   if (P->bf) cudaFree(P->bf);  // base of the persistent block
   if (P->ctl_host) cudaFreeHost(P->ctl_host);
   if (P->flags_host) cudaFreeHost(P->flags_host);
@@ -1483,11 +1471,47 @@ cf_err solve_batch(cf_problem* const* probs, int32_t count, const cf_settings* s
   cf_err first = CF_OK;
   std::vector<char> launched(count, 0);
   DevGuard guard(count > 0 ? probs[0]->device : 0);
+  cf_settings sv;
+  if (st)
+    sv = *st;
+  else
+    cf_settings_default(&sv);
+  std::string why;
+  if (!settings_valid(&sv, &why)) return fail(CF_E_INVALID, "solve_batch: " + why);
+  // team-engine problems, grouped by context: one persistent launch each
+  std::vector<std::pair<cf_ctx*, std::vector<int32_t>>> groups;
   for (int32_t i = 0; i < count; ++i) {
-    cudaSetDevice(probs[i]->device);
-    cf_err r = solve_launch(probs[i], st, xs ? xs[i] : nullptr, ys ? ys[i] : nullptr,
-                            ss ? ss[i] : nullptr, nullptr, nullptr, /*join_ctx=*/false);
+    cf_problem* P = probs[i];
+    int engine = CF_ENGINE_GRAPH;
+    cudaSetDevice(P->device);
+    cf_err r = pick_engine(P, &sv, &engine);
+    if (r == CF_OK && engine == CF_ENGINE_TEAM) {
+      r = ensure_state(P);
+      if (r == CF_OK) {
+        write_settings(P, &sv, false);
+        P->x_out = xs ? xs[i] : nullptr;
+        P->y_out = ys ? ys[i] : nullptr;
+        P->s_out = ss ? ss[i] : nullptr;
+        P->uv_out = nullptr;
+        size_t g = 0;
+        while (g < groups.size() && groups[g].first != P->ctx) ++g;
+        if (g == groups.size()) groups.push_back({P->ctx, {}});
+        groups[g].second.push_back(i);
+        continue;
+      }
+    }
+    if (r == CF_OK)
+      r = solve_launch(P, &sv, xs ? xs[i] : nullptr, ys ? ys[i] : nullptr, ss ? ss[i] : nullptr, nullptr,
+                       nullptr, /*join_ctx=*/false);
     launched[i] = r == CF_OK;
+    if (r != CF_OK && first == CF_OK) first = r;
+  }
+  for (auto& g : groups) {
+    std::vector<cf_problem*> ps;
+    for (int32_t i : g.second) ps.push_back(probs[i]);
+    cudaSetDevice(g.first->device);
+    cf_err r = team::batch_launch(ps, &sv);
+    for (int32_t i : g.second) launched[i] = r == CF_OK;
     if (r != CF_OK && first == CF_OK) first = r;
   }
   // every problem was enqueued before any join, so they run concurrently

@@ -4,6 +4,7 @@
 #include <mutex>
 
 #include "internal.cuh"
+#include "team.cuh"
 
 namespace cf {
 
@@ -73,6 +74,15 @@ struct cf_problem {
   double *x_out = nullptr, *y_out = nullptr, *s_out = nullptr, *uv_out = nullptr;
   int64_t t_launch = 0;
   bool ran_setup = false;
+  // team engine
+  cf::team::Plan plan;            // flattened operator (plan.ok: supported)
+  cf::team::Term* team_terms = nullptr;  // device copy of plan.fwd, adj, adj_m
+  float* team_scratch = nullptr;  // adjoint dense partials (in the state arena)
+  void* team_buf = nullptr;       // device launch table of solo launches
+  void* team_buf_host = nullptr;  // pinned staging of that table
+  int setup_sig = 0;              // program that computed g: 0 none, 1 graph, >= 2 team
+  int last_engine = 0;            // CF_ENGINE_GRAPH or CF_ENGINE_TEAM
+  int64_t team_launches = 0;      // kernels attributed to this problem's last solve
 };
 
 namespace cf {
@@ -85,5 +95,20 @@ cf_err solve_launch(cf_problem* p, const cf_settings* st, double* x, double* y, 
                     const double* warm_uv, double* uv_out, bool join_ctx = true);
 cf_err solve_finish(cf_problem* p, cf_info* info);
 bool settings_valid(const cf_settings* st, std::string* why);
+void write_settings(cf_problem* p, const cf_settings* st, bool warm);
+// Engine a solve of p with st runs on (CF_ENGINE_GRAPH or CF_ENGINE_TEAM), or
+// CF_E_INVALID when st asks for the team engine and p is not supported.
+cf_err pick_engine(cf_problem* p, const cf_settings* st, int* engine);
+namespace team {
+// Flattens p's operator (at problem creation) and uploads the term lists.
+cf_err plan_problem(cf_problem* p);
+size_t scratch_floats(const cf_problem* p);
+cf_err solo_launch(cf_problem* p, const cf_settings* st, const double* warm_uv, bool join_ctx);
+// Launches every problem of `probs` (all on the team engine, one context) in
+// one persistent kernel; each problem's stream is made to wait for it and
+// then copies the control block back and records ev_out.
+cf_err batch_launch(const std::vector<cf_problem*>& probs, const cf_settings* st);
+void release(cf_problem* p);
+}  // namespace team
 int64_t now_ns();
 }  // namespace cf

@@ -1,0 +1,1623 @@
+// The team engine: the SCS iteration of solver.cu (Section 5.2, following the
+// published SCS method the paper cites) run by one persistent kernel in
+// which a team of CTAs carries a problem through its whole solve.
+//
+// A team is one CTA, or one thread-block cluster whose CTAs synchronise with
+// the cluster barrier and add their partial sums through distributed shared
+// memory.  Phases that the graph engine separates by kernel boundaries are
+// separated here by team barriers, so a small problem's iteration costs
+// barriers instead of launches.  A batch is one launch: cluster teams take
+// the large problems and then every CTA takes small problems by itself, both
+// from work queues ordered longest first; a finished problem retires and its
+// team takes the next one.
+//
+// Partitions.  Vector phases give float4 group v of every vector to team
+// thread v mod (team threads) and the scalar tail to the next threads in
+// order, the same map for every vector, so a thread rereads only what it
+// wrote.  Operator terms partition their outputs otherwise (rows to lane
+// groups, tiles to CTAs); a team barrier separates them from the vector
+// phases.  Vectors written in the solve are read with L2-only loads
+// (ld.global.cg): the CTA that wrote them may sit on another SM.
+//
+// Reductions are deterministic: compensated float32 per thread, float64
+// across the CTA, then every CTA of the team adds the CTAs' partials in rank
+// order, so all CTAs hold the same total and take the same loop decisions.
+// Every loop is bounded by counters (max_iters, the CG caps, the queues); the
+// kernel has no spin-waits.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "devutil.cuh"
+#include "solver.cuh"
+
+namespace cgr = cooperative_groups;
+
+namespace cf {
+namespace team {
+
+// ------------------------------------------------------------ table entry
+struct __align__(16) Prob {
+  Settings st;
+  Ctl* ctl;
+  const Term *fwd, *adj, *adj_m;
+  int32_t nfwd, nadj, nadj_m, nseg;
+  int32_t lanes;     // CSR lanes per row
+  int32_t do_setup;  // compute g = M^{-1} h first
+  int32_t tune;      // timing run: g = 0, no setup, no outputs
+  int32_t want_out, want_uv, pad0;
+  int64_t n, m, z, l;
+  int64_t seg_head[kMaxSeg], seg_end[kMaxSeg];
+  double nb, nc;
+  const float *bf, *cf;
+  float *ux, *uy, *vs, *zx, *rhs, *r, *p, *q, *gx, *gy, *wy, *t, *zy, *cm, *cn, *gz, *az, *scratch;
+  const double* warm;
+  double *out, *uv;
+};
+static_assert(sizeof(Prob) % 16 == 0, "Prob is copied as 16-byte words");
+
+struct Team {
+  int C;     // CTAs in the team (1: this CTA alone)
+  int rank;  // this CTA's rank in the team
+  int tt;    // thread index in the team
+  int TT;    // threads in the team
+};
+
+struct __align__(16) Shared {
+  Prob P;              // the problem being solved
+  double bs[8][32];    // block-sum scratch, one column per warp
+  double part[2][8];   // this CTA's partials, double-buffered across sums
+  double res[8];       // team totals
+  int item;            // work-queue slot taken by the team's rank 0
+};
+
+__device__ __forceinline__ void tsync(const Team& tm) {
+  if (tm.C > 1)
+    cgr::this_cluster().sync();
+  else
+    __syncthreads();
+}
+
+__device__ __forceinline__ float4 cg4(const float* p, int64_t v) {
+  return __ldcg(reinterpret_cast<const float4*>(p) + v);
+}
+__device__ __forceinline__ float cg1(const float* p, int64_t i) { return __ldcg(p + i); }
+
+#define TV4(v, n) for (int64_t v = tm.tt; v < ((n) >> 2); v += tm.TT)
+#define TTAIL(i, n) for (int64_t i = ((n) & ~(int64_t)3) + tm.tt; i < (n); i += tm.TT)
+
+// f(i) for every index of [0, n) this thread owns under the vector partition.
+template <class F>
+__device__ __forceinline__ void each(const Team& tm, int64_t n, F&& f) {
+  for (int64_t v = tm.tt; v < (n >> 2); v += tm.TT) {
+    f(4 * v);
+    f(4 * v + 1);
+    f(4 * v + 2);
+    f(4 * v + 3);
+  }
+  TTAIL(i, n) f(i);
+}
+
+// Team-wide deterministic sum of NV doubles; every thread receives the totals.
+template <int NV>
+__device__ void team_sum(const Team& tm, Shared& sh, int& ph, double (&v)[NV]) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int j = 0; j < NV; ++j) {
+    double t = v[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) sh.bs[j][wid] = t;
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+      double t = lane < nw ? sh.bs[j][lane] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (lane == 0) sh.part[ph][j] = t;
+    }
+  }
+  if (tm.C > 1) {
+    cgr::cluster_group cl = cgr::this_cluster();
+    cl.sync();
+    if (threadIdx.x < NV) {
+      double s = 0.0;
+      for (int r = 0; r < tm.C; ++r) s += *cl.map_shared_rank(&sh.part[ph][threadIdx.x], r);
+      sh.res[threadIdx.x] = s;
+    }
+  } else {
+    __syncthreads();
+    if (threadIdx.x < NV) sh.res[threadIdx.x] = sh.part[ph][threadIdx.x];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < NV; ++j) v[j] = sh.res[j];
+  ph ^= 1;
+}
+
+// ------------------------------------------------------------ operator terms
+__device__ void term_diag(const Team& tm, const Term& t, const float* x, float* y) {
+  const float* d = (const float*)t.a;
+  for (int64_t i = tm.tt; i < t.rows; i += tm.TT) {
+    const float xv = cg1(x, t.xo + i);
+    float* yp = y + t.yo + i;
+    *yp = fmaf(t.alpha, d ? __ldg(d + i) * xv : xv, t.acc ? __ldcg(yp) : 0.f);
+  }
+}
+
+template <bool BF16>
+__device__ __forceinline__ float tval(const void* __restrict__ val, int32_t k) {
+  return BF16 ? __bfloat162float(__ldg(((const __nv_bfloat16*)val) + k)) : __ldg(((const float*)val) + k);
+}
+
+// Rows to groups of L lanes (L a power of two); each group walks its row with
+// four gathers in flight and adds across its lanes by shuffles.
+template <bool BF16>
+__device__ void term_csr(const Team& tm, const Term& t, const float* x, float* y, int L) {
+  const int lane = threadIdx.x & 31;
+  const int rpw = 32 / L;
+  const int sub = lane / L, l = lane & (L - 1);
+  const int64_t warp = tm.tt >> 5, nwarps = tm.TT >> 5;
+  const int32_t* __restrict__ rp = t.rowptr;
+  const int32_t* __restrict__ col = t.col;
+  const void* __restrict__ val = t.a;
+  const float* xb = x + t.xo;
+  for (int64_t rb = warp * rpw; rb < t.rows; rb += nwarps * rpw) {
+    const int64_t r = rb + sub;
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+    if (r < t.rows) {
+      const int32_t b = __ldg(rp + r), e = __ldg(rp + r + 1);
+      int32_t k = b + l;
+      for (; k + 3 * L < e; k += 4 * L) {
+        const int32_t c0 = __ldg(col + k), c1 = __ldg(col + k + L), c2 = __ldg(col + k + 2 * L),
+                      c3 = __ldg(col + k + 3 * L);
+        const float v0 = tval<BF16>(val, k), v1 = tval<BF16>(val, k + L);
+        const float v2 = tval<BF16>(val, k + 2 * L), v3 = tval<BF16>(val, k + 3 * L);
+        s0 = fmaf(v0, cg1(xb, c0), s0);
+        s1 = fmaf(v1, cg1(xb, c1), s1);
+        s2 = fmaf(v2, cg1(xb, c2), s2);
+        s3 = fmaf(v3, cg1(xb, c3), s3);
+      }
+      for (; k < e; k += L) s0 = fmaf(tval<BF16>(val, k), cg1(xb, __ldg(col + k)), s0);
+    }
+    float s = (s0 + s1) + (s2 + s3);
+    for (int o = L >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (l == 0 && r < t.rows) {
+      const float out = t.alpha * s;
+      float* yp = y + t.yo + r;
+      *yp = t.acc ? __ldcg(yp) + out : out;
+    }
+  }
+}
+
+// y = alpha D x, D row-major (rows x cols, leading dimension lda): x is staged
+// in each CTA's shared memory, a warp takes four rows at a time and its lanes
+// read 16-byte pieces of them.
+template <typename TS>
+__device__ void term_dense_n(const Team& tm, const Term& t, const float* x, float* y, float* dsm) {
+  constexpr int V = Vec<TS>::N;
+  constexpr int RW = 4;
+  const int64_t n = t.cols, m = t.rows, lda = t.lda;
+  const int64_t npad = (n + 15) & ~(int64_t)15;
+  __syncthreads();  // earlier users of the shared buffer are done
+  for (int64_t i = threadIdx.x; i < npad; i += blockDim.x) dsm[i] = i < n ? cg1(x, t.xo + i) : 0.f;
+  __syncthreads();
+  const TS* A = (const TS*)t.a;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = tm.tt >> 5, nw = tm.TT >> 5;
+  for (int64_t r0 = warp * RW; r0 < m; r0 += nw * RW) {
+    float acc[RW];
+#pragma unroll
+    for (int rr = 0; rr < RW; ++rr) acc[rr] = 0.f;
+    for (int64_t k = (int64_t)lane * V; k < n; k += 32 * V) {
+      float xv[V];
+#pragma unroll
+      for (int q = 0; q < V; q += 4) {
+        const float4 f4 = *reinterpret_cast<const float4*>(dsm + k + q);
+        xv[q] = f4.x; xv[q + 1] = f4.y; xv[q + 2] = f4.z; xv[q + 3] = f4.w;
+      }
+      uint4 u[RW];
+#pragma unroll
+      for (int rr = 0; rr < RW; ++rr)
+        if (r0 + rr < m) u[rr] = __ldg(reinterpret_cast<const uint4*>(A + (r0 + rr) * lda + k));
+#pragma unroll
+      for (int rr = 0; rr < RW; ++rr) {
+        if (r0 + rr < m) {
+          float f[V];
+          Vec<TS>::unpack(u[rr], f);
+          // padding columns (>= n) meet x = 0 and are finite (zero-filled)
+#pragma unroll
+          for (int q = 0; q < V; ++q) acc[rr] = fmaf(f[q], xv[q], acc[rr]);
+        }
+      }
+    }
+#pragma unroll
+    for (int rr = 0; rr < RW; ++rr) {
+      float s = acc[rr];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      acc[rr] = s;
+    }
+    if (lane < RW && r0 + lane < m) {
+      float s = acc[0];
+#pragma unroll
+      for (int rr = 1; rr < RW; ++rr)
+        if (lane == rr) s = acc[rr];
+      const int64_t r = r0 + lane;
+      float out = t.alpha * (t.scale ? __ldg(t.scale + r) * s : s);
+      float* yp = y + t.yo + r;
+      *yp = t.acc ? __ldcg(yp) + out : out;
+    }
+  }
+}
+
+// y = alpha D^T x: warps take (column piece, row group) items; with several
+// row groups the partials go to scratch and are added in group order after a
+// team barrier.
+template <typename TS>
+__device__ void term_dense_t(const Team& tm, const Term& t, const float* x, float* y, float* scratch) {
+  constexpr int V = Vec<TS>::N;
+  const int64_t nout = t.rows, nin = t.cols, lda = t.lda;
+  const int64_t piece = 32 * V;
+  const int64_t npc = (nout + piece - 1) / piece;
+  const int64_t nw = tm.TT >> 5, warp = tm.tt >> 5;
+  int64_t R = nw / npc;
+  R = R < 1 ? 1 : (R > kDenseTGroups ? kDenseTGroups : R);
+  if (R > 1) tsync(tm);  // an earlier term's readers of the scratch are done
+  const TS* A = (const TS*)t.a;
+  const int lane = threadIdx.x & 31;
+  for (int64_t it = warp; it < npc * R; it += nw) {
+    const int64_t c = it % npc, g = it / npc;
+    const int64_t r0 = g * nin / R, r1 = (g + 1) * nin / R;
+    const int64_t col0 = c * piece + (int64_t)lane * V;
+    float acc[V];
+#pragma unroll
+    for (int q = 0; q < V; ++q) acc[q] = 0.f;
+    if (col0 < nout) {
+      int64_t i = r0;
+      for (; i + 4 <= r1; i += 4) {
+        uint4 u[4];
+        float xi[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          u[j] = __ldg(reinterpret_cast<const uint4*>(A + (i + j) * lda + col0));
+          xi[j] = cg1(x, t.xo + i + j);
+          if (t.scale) xi[j] *= __ldg(t.scale + i + j);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          float f[V];
+          Vec<TS>::unpack(u[j], f);
+#pragma unroll
+          for (int q = 0; q < V; ++q) acc[q] = fmaf(xi[j], f[q], acc[q]);
+        }
+      }
+      for (; i < r1; ++i) {
+        const uint4 u = __ldg(reinterpret_cast<const uint4*>(A + i * lda + col0));
+        float xi = cg1(x, t.xo + i);
+        if (t.scale) xi *= __ldg(t.scale + i);
+        float f[V];
+        Vec<TS>::unpack(u, f);
+#pragma unroll
+        for (int q = 0; q < V; ++q) acc[q] = fmaf(xi, f[q], acc[q]);
+      }
+#pragma unroll
+      for (int q = 0; q < V; ++q) {
+        const int64_t j = col0 + q;
+        if (j < nout) {
+          if (R == 1) {
+            float* yp = y + t.yo + j;
+            const float out = t.alpha * acc[q];
+            *yp = t.acc ? __ldcg(yp) + out : out;
+          } else {
+            scratch[g * nout + j] = acc[q];
+          }
+        }
+      }
+    }
+  }
+  if (R > 1) {
+    tsync(tm);
+    for (int64_t j = tm.tt; j < nout; j += tm.TT) {
+      float s = 0.f;
+      for (int64_t g = 0; g < R; ++g) s += cg1(scratch, g * nout + j);
+      float* yp = y + t.yo + j;
+      const float out = t.alpha * s;
+      *yp = t.acc ? __ldcg(yp) + out : out;
+    }
+  }
+}
+
+// out[i] = sum_{j < Lp} wrev[j] x[i + shift - (Lp - 1) + j] (x = 0 outside
+// [0, cols)): output tiles go to the team's CTAs in turn; each tile's input
+// window and the taps sit in shared memory.
+__device__ void term_conv(const Team& tm, const Term& t, const float* x, float* y, float* dsm) {
+  const int64_t n_out = t.rows, n_in = t.cols, Lp = t.Lp;
+  float* w_s = dsm;
+  float* in_s = dsm + Lp;
+  __syncthreads();  // earlier users of the shared buffer are done
+  for (int64_t j = threadIdx.x; j < Lp; j += blockDim.x) w_s[j] = __ldg((const float*)t.a + j);
+  const int64_t ntile = (n_out + kConvTile - 1) / kConvTile;
+  for (int64_t tile = tm.rank; tile < ntile; tile += tm.C) {
+    const int64_t o0 = tile * kConvTile;
+    const int64_t cnt = (n_out - o0) < kConvTile ? (n_out - o0) : (int64_t)kConvTile;
+    const int64_t base = o0 + t.shift - (Lp - 1);
+    __syncthreads();
+    for (int64_t j = threadIdx.x; j < cnt + Lp - 1; j += blockDim.x) {
+      const int64_t g = base + j;
+      in_s[j] = (g >= 0 && g < n_in) ? cg1(x, t.xo + g) : 0.f;
+    }
+    __syncthreads();
+    for (int64_t o = threadIdx.x; o < cnt; o += blockDim.x) {
+      float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+      const float* win = in_s + o;
+      for (int64_t j = 0; j < Lp; j += 4) {  // Lp is a multiple of 16
+        s0 = fmaf(w_s[j], win[j], s0);
+        s1 = fmaf(w_s[j + 1], win[j + 1], s1);
+        s2 = fmaf(w_s[j + 2], win[j + 2], s2);
+        s3 = fmaf(w_s[j + 3], win[j + 3], s3);
+      }
+      const float out = t.alpha * ((s0 + s1) + (s2 + s3));
+      float* yp = y + t.yo + o0 + o;
+      *yp = t.acc ? __ldcg(yp) + out : out;
+    }
+  }
+}
+
+// y = the flattened operator applied to x (terms in order).
+__device__ void apply(const Team& tm, const Term* terms, int nt, const float* x, float* y,
+                      float* scratch, float* dsm, int lanes) {
+  for (int k = 0; k < nt; ++k) {
+    const Term& t = terms[k];
+    if (t.sync) tsync(tm);
+    switch (t.kind) {
+      case T_FILL:
+        for (int64_t i = tm.tt; i < t.rows; i += tm.TT) y[t.yo + i] = 0.f;
+        break;
+      case T_DIAG:
+        term_diag(tm, t, x, y);
+        break;
+      case T_CSR:
+        if (t.prec == CF_BF16)
+          term_csr<true>(tm, t, x, y, lanes);
+        else
+          term_csr<false>(tm, t, x, y, lanes);
+        break;
+      case T_DENSE_N:
+        if (t.prec == CF_BF16)
+          term_dense_n<__nv_bfloat16>(tm, t, x, y, dsm);
+        else if (t.prec == CF_FP8_E4M3)
+          term_dense_n<__nv_fp8_e4m3>(tm, t, x, y, dsm);
+        else
+          term_dense_n<float>(tm, t, x, y, dsm);
+        break;
+      case T_DENSE_T:
+        if (t.prec == CF_BF16)
+          term_dense_t<__nv_bfloat16>(tm, t, x, y, scratch);
+        else if (t.prec == CF_FP8_E4M3)
+          term_dense_t<__nv_fp8_e4m3>(tm, t, x, y, scratch);
+        else
+          term_dense_t<float>(tm, t, x, y, scratch);
+        break;
+      case T_CONV:
+        term_conv(tm, t, x, y, dsm);
+        break;
+    }
+  }
+}
+
+// ------------------------------------------------------------ CG (Section 4.2)
+// CG on (lam I + A^T A) z = rhs from the z held (gz = G z carried, fresh
+// start not needed: setup starts at z = 0, iterations warm-start with the
+// carried G z).  mode CG_ITER also carries az = A z.  Returns the steps run.
+__device__ int cg_run(const Team& tm, Shared& sh, int& ph, float* dsm, int mode, float* z, int k_outer) {
+  const Prob& P = sh.P;
+  const Settings& st = P.st;
+  const int64_t n = P.n, m = P.m;
+  const float lamf = 1.f;
+  float *r = P.r, *p = P.p, *q = P.q, *gz = P.gz, *az = P.az, *t = P.t;
+  const float* rhs = P.rhs;
+  Acc2 a0, a1;
+  TV4(v, n) {
+    const float4 g = cg4(gz, v), rh = cg4(rhs, v);
+    float4 rv;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      el(rv, k) = elc(rh, k) - elc(g, k);
+      a0.add_prod(elc(rv, k), elc(rv, k));
+      a1.add_prod(elc(rh, k), elc(rh, k));
+    }
+    st4(r, v, rv);
+    st4(p, v, rv);
+  }
+  TTAIL(i, n) {
+    const float rh = cg1(rhs, i);
+    const float ri = rh - cg1(gz, i);
+    r[i] = ri;
+    p[i] = ri;
+    a0.add_prod(ri, ri);
+    a1.add_prod(rh, rh);
+  }
+  double v2[2] = {a0.value(), a1.value()};
+  team_sum<2>(tm, sh, ph, v2);
+  double rr = v2[0];
+  const double nrhs = sqrt(v2[1]);
+  double tol;
+  int cap, fixed;
+  if (mode == CG_SETUP) {
+    tol = st.setup_tol * nrhs;
+    cap = st.setup_cg_max;
+    fixed = 0;
+  } else {
+    tol = st.cg_tol_rel * nrhs * (double)powf((float)k_outer + 1.0f, -(float)st.cg_tol_exp);
+    tol = fmax(tol, st.cg_tol_min);
+    cap = st.cg_max;
+    fixed = st.cg_fixed;
+  }
+  const double tol2 = tol * tol;
+  const int cap2 = mode == CG_SETUP ? st.setup_cg_max : (fixed > 0 ? fixed : st.cg_max);
+  bool cont = fixed > 0 ? true : (rr > tol2 && cap > 0);
+  int it = 0, guard = 0;
+  while (cont) {
+    // p (vector partition, followed by a sum or a barrier) -> t = A p -> q = A^T t
+    apply(tm, P.fwd, P.nfwd, p, t, P.scratch, dsm, P.lanes);
+    tsync(tm);
+    apply(tm, P.adj, P.nadj, t, q, P.scratch, dsm, P.lanes);
+    tsync(tm);
+    Acc2 b0;
+    TV4(v, n) {
+      const float4 pp = cg4(p, v);
+      float4 qq = cg4(q, v);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        el(qq, k) = el(qq, k) + lamf * elc(pp, k);
+        b0.add_prod(elc(pp, k), elc(qq, k));
+      }
+      st4(q, v, qq);
+    }
+    TTAIL(i, n) {
+      const float pi = cg1(p, i);
+      const float qi = cg1(q, i) + lamf * pi;
+      q[i] = qi;
+      b0.add_prod(pi, qi);
+    }
+    double v1[1] = {b0.value()};
+    team_sum<1>(tm, sh, ph, v1);
+    const double pq = v1[0];
+    const double alpha = pq > 0.0 ? rr / pq : 0.0;
+    const float a = (float)alpha;
+    Acc2 c0;
+    TV4(v, n) {
+      const float4 qq = cg4(q, v), pp = cg4(p, v);
+      float4 zz = cg4(z, v), gg = cg4(gz, v), rv = cg4(r, v);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        el(zz, k) = fmaf(a, elc(pp, k), el(zz, k));
+        el(gg, k) = fmaf(a, elc(qq, k), el(gg, k));
+        el(rv, k) = fmaf(-a, elc(qq, k), el(rv, k));
+        c0.add_prod(elc(rv, k), elc(rv, k));
+      }
+      st4(z, v, zz);
+      st4(gz, v, gg);
+      st4(r, v, rv);
+    }
+    TTAIL(i, n) {
+      const float qi = cg1(q, i);
+      z[i] = fmaf(a, cg1(p, i), cg1(z, i));
+      gz[i] = fmaf(a, qi, cg1(gz, i));
+      const float ri = fmaf(-a, qi, cg1(r, i));
+      r[i] = ri;
+      c0.add_prod(ri, ri);
+    }
+    if (mode == CG_ITER) {
+      TV4(v, m) {
+        const float4 tv = cg4(t, v);
+        float4 aa = cg4(az, v);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) el(aa, k) = fmaf(a, elc(tv, k), el(aa, k));
+        st4(az, v, aa);
+      }
+      TTAIL(i, m) az[i] = fmaf(a, cg1(t, i), cg1(az, i));
+    }
+    double v3[1] = {c0.value()};
+    team_sum<1>(tm, sh, ph, v3);
+    const double rr_new = v3[0];
+    const double beta = rr > 0.0 ? rr_new / rr : 0.0;
+    rr = rr_new;
+    ++it;
+    const bool more = fixed > 0 ? (it < fixed) : (rr_new > tol2 && it < cap);
+    const float b = (float)beta;
+    TV4(v, n) {
+      const float4 rv = cg4(r, v);
+      float4 pp = cg4(p, v);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) el(pp, k) = fmaf(b, el(pp, k), elc(rv, k));
+      st4(p, v, pp);
+    }
+    TTAIL(i, n) p[i] = fmaf(b, cg1(p, i), cg1(r, i));
+    ++guard;
+    cont = more && guard < cap2;
+    if (cont) tsync(tm);  // the next forward term reads p under its own partition
+  }
+  return it;
+}
+
+// ------------------------------------------------------------ one solve
+__device__ __forceinline__ int seg_of(const Prob& P, int64_t i) {
+  int s = 0;
+  while (s + 1 < P.nseg && i >= P.seg_end[s]) ++s;
+  return s;
+}
+
+__device__ void solve_one(const Team& tm, Shared& sh, float* dsm) {
+  const Prob& P = sh.P;
+  const Settings& st = P.st;
+  const int64_t n = P.n, m = P.m, N = n + m + 1;
+  const double lam = 1.0;
+  int ph = 0;
+  double hg = 0.0;
+  int setup_iters = 0;
+
+  // ---- setup: g = M^{-1} h, h^T g
+  if (P.tune) {
+    each(tm, n, [&](int64_t i) { P.gx[i] = 0.f; });
+    each(tm, m, [&](int64_t i) { P.gy[i] = 0.f; });
+  } else if (P.do_setup) {
+    each(tm, n, [&](int64_t i) {
+      P.gx[i] = 0.f;
+      P.gz[i] = 0.f;
+      P.rhs[i] = __ldg(P.cf + i);
+    });
+    tsync(tm);
+    apply(tm, P.adj_m, P.nadj_m, P.bf, P.rhs, P.scratch, dsm, P.lanes);  // rhs = c - A^T b
+    tsync(tm);
+    setup_iters = cg_run(tm, sh, ph, dsm, CG_SETUP, P.gx, 0);
+    tsync(tm);
+    apply(tm, P.fwd, P.nfwd, P.gx, P.gy, P.scratch, dsm, P.lanes);  // A g_x
+    tsync(tm);
+    Acc2 a;
+    each(tm, m, [&](int64_t i) {
+      const float bi = __ldg(P.bf + i);
+      const float gi = cg1(P.gy, i) + bi;
+      P.gy[i] = gi;
+      a.add_prod(bi, gi);
+    });
+    each(tm, n, [&](int64_t i) { a.add_prod(__ldg(P.cf + i), cg1(P.gx, i)); });
+    double v[1] = {a.value()};
+    team_sum<1>(tm, sh, ph, v);
+    hg = v[0];
+  } else {
+    hg = __ldcg(&P.ctl->hg);
+  }
+
+  // ---- initial point u = v = (0, 0, 1) or the warm start
+  const bool warm = st.warm != 0 && !P.tune;
+  each(tm, n, [&](int64_t i) {
+    P.ux[i] = warm ? (float)P.warm[i] : 0.f;
+    P.zx[i] = 0.f;
+    P.gz[i] = 0.f;
+  });
+  each(tm, m, [&](int64_t i) {
+    P.uy[i] = warm ? (float)P.warm[n + i] : 0.f;
+    P.vs[i] = warm ? (float)P.warm[N + n + i] : 0.f;
+    P.az[i] = 0.f;
+  });
+  double tau = warm ? P.warm[n + m] : 1.0;
+  double kappa = warm ? P.warm[N + n + m] : 1.0;
+  int k = 0, checks = 0, refreshes = 0, status = CF_MAX_ITERS;
+  long long cg_total = 0;
+  double pri = INFINITY, dual = INFINITY, gap = INFINITY, cx = 0.0, by = 0.0;
+  const double al = st.alpha;
+  const float af = (float)al, a1 = (float)(1.0 - al);
+  const int64_t z = P.z, nl = P.z + P.l;
+
+  for (int guard = 0; guard < st.max_iters; ++guard) {
+    // ---- w = u + v; rhs = w_x - A^T w_y
+    TV4(v, m) {
+      const float4 a = cg4(P.uy, v), b = cg4(P.vs, v);
+      st4(P.wy, v, make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w));
+    }
+    TTAIL(i, m) P.wy[i] = cg1(P.uy, i) + cg1(P.vs, i);
+    TV4(v, n) st4(P.rhs, v, cg4(P.ux, v));
+    TTAIL(i, n) P.rhs[i] = cg1(P.ux, i);
+    const double w_tau = tau + kappa;
+    tsync(tm);
+    apply(tm, P.adj_m, P.nadj_m, P.wy, P.rhs, P.scratch, dsm, P.lanes);
+    tsync(tm);
+    // ---- z_x by CG, warm-started at the previous z_x
+    cg_total += cg_run(tm, sh, ph, dsm, CG_ITER, P.zx, k);
+    // ---- z_y = w_y + A z_x (carried); u~_tau
+    double ut;
+    {
+      Acc2 a;
+      TV4(v, m) {
+        const float4 aa = cg4(P.az, v), ww = cg4(P.wy, v), bb = __ldg(reinterpret_cast<const float4*>(P.bf) + v);
+        float4 zz;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          el(zz, j) = elc(aa, j) + elc(ww, j);
+          a.add_prod(elc(bb, j), elc(zz, j));
+        }
+        st4(P.zy, v, zz);
+      }
+      TTAIL(i, m) {
+        const float zi = cg1(P.az, i) + cg1(P.wy, i);
+        P.zy[i] = zi;
+        a.add_prod(__ldg(P.bf + i), zi);
+      }
+      TV4(v, n) {
+        const float4 cc = __ldg(reinterpret_cast<const float4*>(P.cf) + v), xx = cg4(P.zx, v);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) a.add_prod(elc(cc, j), elc(xx, j));
+      }
+      TTAIL(i, n) a.add_prod(__ldg(P.cf + i), cg1(P.zx, i));
+      double v[1] = {a.value()};
+      team_sum<1>(tm, sh, ph, v);
+      ut = (w_tau + v[0]) / (1.0 + hg);
+    }
+    const float utf = (float)ut;
+    // ---- second-order cones: head value and tail norm of each block
+    double sv[2 * kMaxSeg];
+    if (P.nseg > 0) {
+      Acc2 acc[kMaxSeg];
+      double p0[kMaxSeg];
+#pragma unroll
+      for (int s = 0; s < kMaxSeg; ++s) p0[s] = 0.0;
+      each(tm, m, [&](int64_t i) {
+        if (i < nl) return;
+        const float pi = y_pre(af, a1, utf, cg1(P.zy, i), cg1(P.gy, i), cg1(P.uy, i), cg1(P.vs, i));
+        const int s = seg_of(P, i);
+#pragma unroll
+        for (int j = 0; j < kMaxSeg; ++j) {
+          if (j == s) {
+            if (i == P.seg_head[j])
+              p0[j] = (double)pi;
+            else
+              acc[j].add_prod(pi, pi);
+          }
+        }
+      });
+#pragma unroll
+      for (int s = 0; s < kMaxSeg; ++s) {
+        sv[2 * s] = p0[s];
+        sv[2 * s + 1] = acc[s].value();
+      }
+      team_sum<2 * kMaxSeg>(tm, sh, ph, sv);
+    }
+    // ---- projection onto C and dual update (u+ = Pi(u_hat - v), v+ = v - u_hat + u+)
+    TV4(v, n) {
+      const float4 zz = cg4(P.zx, v), gg = cg4(P.gx, v);
+      float4 uu = cg4(P.ux, v);
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        el(uu, j) = __fadd_rn(__fmul_rn(af, __fsub_rn(elc(zz, j), __fmul_rn(utf, elc(gg, j)))),
+                              __fmul_rn(a1, el(uu, j)));
+      st4(P.ux, v, uu);
+    }
+    TTAIL(i, n) P.ux[i] = __fadd_rn(__fmul_rn(af, __fsub_rn(cg1(P.zx, i), __fmul_rn(utf, cg1(P.gx, i)))),
+                                    __fmul_rn(a1, cg1(P.ux, i)));
+    each(tm, m, [&](int64_t i) {
+      const float pi = y_pre(af, a1, utf, cg1(P.zy, i), cg1(P.gy, i), cg1(P.uy, i), cg1(P.vs, i));
+      float ui;
+      if (i < z) {
+        ui = pi;
+      } else if (i < nl) {
+        ui = fmaxf(pi, 0.f);
+      } else {
+        const int s = seg_of(P, i);
+        const double nrm = sqrt(sv[2 * s + 1]), p0 = sv[2 * s];
+        if (nrm <= p0) {
+          ui = pi;
+        } else if (nrm <= -p0) {
+          ui = 0.f;
+        } else {
+          const double ah = 0.5 * (p0 + nrm);
+          ui = (i == P.seg_head[s]) ? (float)ah : __fmul_rn((float)(ah / nrm), pi);
+        }
+      }
+      P.uy[i] = ui;
+      P.vs[i] = __fsub_rn(ui, pi);
+    });
+    {
+      const double uhat = al * ut + (1.0 - al) * tau;
+      const double pt = uhat - kappa;
+      const double tn = pt > 0.0 ? pt : 0.0;
+      tau = tn;
+      kappa = tn - pt;
+    }
+    ++k;
+    const bool chk = (k % st.check_interval == 0) || (k >= st.max_iters);
+    const bool ref = (k % 50 == 0) && (k < st.max_iters);
+    bool stop = false;
+    if (!isfinite(tau) || !isfinite(kappa)) {
+      status = CF_NUMERICAL;
+      stop = true;
+    }
+    // ---- residuals and certificates
+    if (chk && !stop) {
+      tsync(tm);
+      apply(tm, P.fwd, P.nfwd, P.ux, P.cm, P.scratch, dsm, P.lanes);
+      apply(tm, P.adj, P.nadj, P.uy, P.cn, P.scratch, dsm, P.lanes);
+      tsync(tm);
+      const float tf = (float)tau;
+      Acc2 s0, s1, s2, s3, s4, s5;
+      each(tm, m, [&](int64_t i) {
+        const float bi = __ldg(P.bf + i);
+        const float e = cg1(P.cm, i) + cg1(P.vs, i);
+        const float d = fmaf(-bi, tf, e);
+        s0.add_prod(d, d);
+        s1.add_prod(e, e);
+        s2.add_prod(bi, cg1(P.uy, i));
+      });
+      each(tm, n, [&](int64_t i) {
+        const float ci = __ldg(P.cf + i), cn = cg1(P.cn, i);
+        const float d = fmaf(ci, tf, cn);
+        s3.add_prod(d, d);
+        s4.add_prod(cn, cn);
+        s5.add_prod(ci, cg1(P.ux, i));
+      });
+      double v[6] = {s0.value(), s1.value(), s2.value(), s3.value(), s4.value(), s5.value()};
+      team_sum<6>(tm, sh, ph, v);
+      ++checks;
+      cx = v[5];
+      by = v[2];
+      bool bad = false;
+      for (int j = 0; j < 6; ++j) bad |= !isfinite(v[j]);
+      if (bad) {
+        status = CF_NUMERICAL;
+        stop = true;
+      } else {
+        if (tau > 0.0) {
+          pri = sqrt(v[0]) / tau / (1.0 + P.nb);
+          dual = sqrt(v[3]) / tau / (1.0 + P.nc);
+          const double cxt = v[5] / tau, byt = v[2] / tau;
+          gap = fabs(cxt + byt) / (1.0 + fabs(cxt) + fabs(byt));
+          if (pri <= st.eps && dual <= st.eps && gap <= st.eps) {
+            status = CF_SOLVED;
+            stop = true;
+          }
+        }
+        if (!stop) {
+          if (-v[2] > 0.0 && sqrt(v[4]) <= st.eps_inf * (-v[2])) {
+            status = CF_INFEASIBLE;
+            stop = true;
+          } else if (-v[5] > 0.0 && sqrt(v[1]) <= st.eps_inf * (-v[5])) {
+            status = CF_UNBOUNDED;
+            stop = true;
+          }
+        }
+      }
+    }
+    const bool go = !stop && k < st.max_iters;
+    if (!go) break;
+    // ---- exact A z_x and G z_x every 50 iterations
+    if (ref) {
+      ++refreshes;
+      tsync(tm);
+      apply(tm, P.fwd, P.nfwd, P.zx, P.az, P.scratch, dsm, P.lanes);
+      tsync(tm);
+      apply(tm, P.adj, P.nadj, P.az, P.gz, P.scratch, dsm, P.lanes);
+      tsync(tm);
+      each(tm, n, [&](int64_t i) { P.gz[i] = fmaf((float)lam, cg1(P.zx, i), cg1(P.gz, i)); });
+    }
+  }
+
+  // ---- outputs
+  if (!P.tune) {
+    if (P.want_out) {
+      double sx, sy, ss;
+      if (status == CF_INFEASIBLE) {
+        sx = NAN; ss = NAN; sy = 1.0 / (-by);
+      } else if (status == CF_UNBOUNDED) {
+        sx = 1.0 / (-cx); ss = sx; sy = NAN;
+      } else if (tau > 0.0) {
+        sx = sy = ss = 1.0 / tau;
+      } else {
+        sx = sy = ss = NAN;
+      }
+      each(tm, n, [&](int64_t i) { P.out[i] = (double)cg1(P.ux, i) * sx; });
+      each(tm, m, [&](int64_t i) {
+        P.out[n + i] = (double)cg1(P.uy, i) * sy;
+        P.out[n + m + i] = (double)cg1(P.vs, i) * ss;
+      });
+    }
+    if (P.want_uv) {
+      each(tm, n, [&](int64_t i) {
+        P.uv[i] = cg1(P.ux, i);
+        P.uv[N + i] = 0.0;
+      });
+      each(tm, m, [&](int64_t i) {
+        P.uv[n + i] = cg1(P.uy, i);
+        P.uv[N + n + i] = cg1(P.vs, i);
+      });
+      if (tm.tt == 0) {
+        P.uv[n + m] = tau;
+        P.uv[N + n + m] = kappa;
+      }
+    }
+  }
+  if (tm.tt == 0) {
+    Ctl* c = P.ctl;
+    c->lam = lam;
+    c->hg = hg;
+    c->tau = tau;
+    c->kappa = kappa;
+    c->pri = pri;
+    c->dual = dual;
+    c->gap = gap;
+    c->cx = cx;
+    c->by = by;
+    c->cg_total = cg_total;
+    c->k = k;
+    c->checks = checks;
+    c->refreshes = refreshes;
+    c->status = status;
+    c->stop = 1;
+    if (P.do_setup && !P.tune) c->setup_iters = setup_iters;
+  }
+}
+
+__device__ void load_prob(Shared& sh, const Prob* src) {
+  const int4* s = reinterpret_cast<const int4*>(src);
+  int4* d = reinterpret_cast<int4*>(&sh.P);
+  for (int i = threadIdx.x; i < (int)(sizeof(Prob) / 16); i += blockDim.x) d[i] = __ldg(s + i);
+  __syncthreads();
+}
+
+// Persistent kernel: cluster teams take problems order[0, nbig), then every
+// CTA takes problems order[nbig, nbig + nsmall) alone.
+template <int MaxT>
+__global__ void __launch_bounds__(MaxT) k_team(const Prob* __restrict__ probs, const int32_t* __restrict__ order,
+                                               int32_t nbig, int32_t nsmall, unsigned int* counters,
+                                               int32_t cluster) {
+  extern __shared__ __align__(16) float dsm[];
+  __shared__ Shared sh;
+  Team tm;
+  if (cluster > 1) {
+    cgr::cluster_group cl = cgr::this_cluster();
+    tm.C = cluster;
+    tm.rank = (int)cl.block_rank();
+    tm.TT = cluster * (int)blockDim.x;
+    tm.tt = tm.rank * (int)blockDim.x + (int)threadIdx.x;
+    for (;;) {
+      if (tm.rank == 0 && threadIdx.x == 0) sh.item = (int)atomicAdd(&counters[0], 1u);
+      cl.sync();
+      const int it = *cl.map_shared_rank(&sh.item, 0);
+      cl.sync();
+      if (it >= nbig) break;
+      load_prob(sh, probs + order[it]);
+      solve_one(tm, sh, dsm);
+    }
+  }
+  tm.C = 1;
+  tm.rank = 0;
+  tm.TT = (int)blockDim.x;
+  tm.tt = (int)threadIdx.x;
+  for (;;) {
+    if (threadIdx.x == 0) sh.item = (int)atomicAdd(&counters[1], 1u);
+    __syncthreads();
+    const int it = sh.item;
+    __syncthreads();
+    if (it >= nsmall) break;
+    load_prob(sh, probs + order[nbig + it]);
+    solve_one(tm, sh, dsm);
+  }
+}
+
+// ------------------------------------------------------------ host: planning
+namespace {
+
+int64_t out_len(const cf_op* op, bool trans) { return trans ? op->n : op->m; }
+
+// Mirrors op_apply_rec (ops.cu): the same walk, emitting terms instead of
+// launches.
+bool flatten(const cf_op* op, bool trans, float alpha, int64_t xo, int64_t yo, bool acc,
+             std::vector<Term>& out, std::string* why) {
+  Term t{};
+  t.alpha = alpha;
+  t.acc = acc ? 1 : 0;
+  t.xo = xo;
+  t.yo = yo;
+  switch (op->kind) {
+    case OP_ZERO:
+      if (!acc) {
+        t.kind = T_FILL;
+        t.rows = out_len(op, trans);
+        out.push_back(t);
+      }
+      return true;
+    case OP_DIAG:
+      t.kind = T_DIAG;
+      t.rows = t.cols = op->n;
+      t.a = op->d;
+      out.push_back(t);
+      return true;
+    case OP_DENSE:
+      if (!trans && op->n > kDenseMaxCols) {
+        *why = "dense leaf wider than " + std::to_string(kDenseMaxCols) + " columns";
+        return false;
+      }
+      t.kind = trans ? T_DENSE_T : T_DENSE_N;
+      t.prec = op->prec;
+      t.rows = trans ? op->n : op->m;
+      t.cols = trans ? op->m : op->n;
+      t.a = op->a;
+      t.scale = op->row_scale;
+      t.lda = op->lda;
+      out.push_back(t);
+      return true;
+    case OP_CSR:
+      t.kind = T_CSR;
+      t.prec = op->prec;
+      t.rows = trans ? op->n : op->m;
+      t.cols = trans ? op->m : op->n;
+      t.rowptr = trans ? op->t_rowptr : op->rowptr;
+      t.col = trans ? op->t_col : op->col;
+      t.a = trans ? op->t_val : op->val;
+      out.push_back(t);
+      return true;
+    case OP_CONV1D:
+      if (op->Lp > kConvMaxLp) {
+        *why = "convolution longer than " + std::to_string(kConvMaxLp) + " taps";
+        return false;
+      }
+      t.kind = T_CONV;
+      t.rows = trans ? op->n : op->m;
+      t.cols = trans ? op->m : op->n;
+      t.Lp = op->Lp;
+      t.shift = trans ? op->Lp - 1 : 0;
+      t.a = trans ? op->w_adj : op->w_fwd;
+      out.push_back(t);
+      return true;
+    case OP_CONV2D:
+      *why = "2-D convolution leaf";
+      return false;
+    case OP_SCALE:
+      return flatten(op->parts[0], trans, (float)(alpha * op->alpha), xo, yo, acc, out, why);
+    case OP_ADJOINT:
+      return flatten(op->parts[0], !trans, alpha, xo, yo, acc, out, why);
+    case OP_VSTACK:
+    case OP_HSTACK: {
+      const bool split_out = (op->kind == OP_VSTACK) != trans;
+      int64_t off = 0;
+      bool first = true;
+      for (const cf_op* p : op->parts) {
+        if (split_out) {
+          if (!flatten(p, trans, alpha, xo, yo + off, acc, out, why)) return false;
+          off += trans ? p->n : p->m;
+        } else {
+          if (!flatten(p, trans, alpha, xo + off, yo, first ? acc : true, out, why)) return false;
+          off += trans ? p->m : p->n;
+          first = false;
+        }
+      }
+      return true;
+    }
+    case OP_BLOCKDIAG: {
+      int64_t ro = 0, co = 0;
+      for (const cf_op* p : op->parts) {
+        const int64_t din = trans ? p->m : p->n, dout = trans ? p->n : p->m;
+        if (!flatten(p, trans, alpha, xo + ro, yo + co, acc, out, why)) return false;
+        ro += din;
+        co += dout;
+      }
+      return true;
+    }
+    case OP_SUM: {
+      bool first = true;
+      for (const cf_op* p : op->parts) {
+        if (!flatten(p, trans, alpha, xo, yo, first ? acc : true, out, why)) return false;
+        first = false;
+      }
+      return true;
+    }
+    case OP_PRODUCT:
+      *why = "operator product";
+      return false;
+    case OP_KRON:
+      *why = "Kronecker operator";
+      return false;
+  }
+  *why = "unknown operator";
+  return false;
+}
+
+// A term whose outputs overlap an output written since the last barrier
+// (under another row partition) needs a barrier first.
+void mark_syncs(std::vector<Term>& ts) {
+  std::vector<std::pair<int64_t, int64_t>> win;
+  for (Term& t : ts) {
+    const int64_t a = t.yo, b = t.yo + t.rows;
+    bool hit = false;
+    for (auto& w : win) hit |= a < w.second && w.first < b;
+    t.sync = hit ? 1 : 0;
+    if (hit) win.clear();
+    win.push_back({a, b});
+  }
+}
+
+double term_bytes(const Term& t) {
+  switch (t.kind) {
+    case T_FILL: return 4.0 * t.rows;
+    case T_DIAG: return (t.a ? 12.0 : 8.0) * t.rows;
+    case T_CSR: {
+      return 0.0;  // filled in by plan_problem from the leaf's nnz
+    }
+    case T_DENSE_N: case T_DENSE_T: {
+      const double esz = t.prec == CF_FP32 ? 4 : (t.prec == CF_BF16 ? 2 : 1);
+      const double mrows = t.kind == T_DENSE_N ? t.rows : t.cols;
+      return mrows * t.lda * esz + (t.scale ? 4.0 * mrows : 0.0);
+    }
+    case T_CONV:
+      // input + output, and the multiply-adds at 16 flops per byte (one SM's
+      // FP32 rate over its share of the memory bandwidth)
+      return 4.0 * (t.rows + t.cols) + 2.0 * t.Lp * t.rows / 16.0;
+  }
+  return 0.0;
+}
+
+}  // namespace
+
+cf_err plan_problem(cf_problem* P) {
+  Plan& pl = P->plan;
+  pl = Plan();
+  std::string why;
+  if ((int64_t)P->q.size() > kMaxSeg) {
+    pl.why = "more than " + std::to_string(kMaxSeg) + " second-order cones";
+    return CF_OK;
+  }
+  if (!flatten(P->A, false, 1.f, 0, 0, false, pl.fwd, &why) ||
+      !flatten(P->A, true, 1.f, 0, 0, false, pl.adj, &why) ||
+      !flatten(P->A, true, -1.f, 0, 0, true, pl.adj_m, &why)) {
+    pl.fwd.clear();
+    pl.adj.clear();
+    pl.adj_m.clear();
+    pl.why = why;
+    return CF_OK;
+  }
+  mark_syncs(pl.fwd);
+  mark_syncs(pl.adj);
+  mark_syncs(pl.adj_m);
+  // sizes: bytes of a forward pass (CSR from the leaf's nnz), CSR rows,
+  // adjoint dense widths, shared memory
+  double bytes = 0.0, nnz = 0.0, rows = 0.0;
+  int64_t smem = 0;
+  for (const Term& t : pl.fwd) {
+    if (t.kind == T_CSR) {
+      std::vector<int32_t> ends(2);
+      // nnz of the leaf: rowptr[rows] (host copy of one entry)
+      cudaMemcpy(ends.data(), t.rowptr + t.rows, sizeof(int32_t), cudaMemcpyDeviceToHost);
+      const double esz = t.prec == CF_BF16 ? 2.0 : 4.0;
+      bytes += ends[0] * (4.0 + esz) + 4.0 * (t.rows + 1);
+      nnz += ends[0];
+      rows += t.rows;
+    } else {
+      bytes += term_bytes(t);
+    }
+  }
+  for (const std::vector<Term>* lst : {&pl.fwd, &pl.adj, &pl.adj_m})
+    for (const Term& t : *lst) {
+      if (t.kind == T_DENSE_N) smem = std::max<int64_t>(smem, (t.cols + 15) & ~(int64_t)15);
+      if (t.kind == T_CONV) smem = std::max<int64_t>(smem, 2 * t.Lp + kConvTile);
+      if (t.kind == T_DENSE_T) pl.dense_t_cols = std::max(pl.dense_t_cols, t.rows);
+    }
+  pl.pass_bytes = bytes + 4.0 * (P->n + P->m);
+  pl.avg_row_nnz = rows > 0 ? nnz / rows : 0.0;
+  pl.smem_floats = smem;
+  // device copy of the three lists
+  const size_t nt = pl.fwd.size() + pl.adj.size() + pl.adj_m.size();
+  std::vector<Term> all;
+  all.reserve(nt);
+  all.insert(all.end(), pl.fwd.begin(), pl.fwd.end());
+  all.insert(all.end(), pl.adj.begin(), pl.adj.end());
+  all.insert(all.end(), pl.adj_m.begin(), pl.adj_m.end());
+  cudaError_t e = cudaMalloc((void**)&P->team_terms, std::max<size_t>(nt, 1) * sizeof(Term));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    P->team_terms = nullptr;
+    return fail(CF_E_OOM, "cone_problem_create: allocation failed");
+  }
+  if (nt) CF_CUDA(cudaMemcpy(P->team_terms, all.data(), nt * sizeof(Term), cudaMemcpyHostToDevice));
+  pl.ok = true;
+  return CF_OK;
+}
+
+size_t scratch_floats(const cf_problem* P) {
+  return P->plan.ok ? (size_t)kDenseTGroups * (size_t)P->plan.dense_t_cols : 0;
+}
+
+void release(cf_problem* P) {
+  if (P->team_terms) cudaFree(P->team_terms);
+  if (P->team_buf) cudaFree(P->team_buf);
+  if (P->team_buf_host) cudaFreeHost(P->team_buf_host);
+  P->team_terms = nullptr;
+  P->team_buf = nullptr;
+  P->team_buf_host = nullptr;
+}
+
+// ------------------------------------------------------------ host: launches
+namespace {
+
+int lanes_for(const Plan& pl, const cf_schedule& s) {
+  int L = 1;
+  while (L < 32 && (double)L * s.csr_nnz_per_lane < pl.avg_row_nnz) L *= 2;
+  return L;
+}
+
+bool is_big(const cf_problem* P, const cf_schedule& s) {
+  return s.cluster > 1 && P->plan.pass_bytes >= s.team_bytes;
+}
+
+// Identifies the reduction partitions a problem runs with (>= 2; 1 is the
+// graph engine).
+int sig_for(const cf_problem* P, const cf_schedule& s) {
+  const int C = is_big(P, s) ? s.cluster : 1;
+  return 2 + (C * 4096 + s.threads) * 64 + lanes_for(P->plan, s);
+}
+
+void fill_prob(cf_problem* P, const cf_schedule& s, bool do_setup, bool tune, Prob* o) {
+  std::memset(o, 0, sizeof(Prob));
+  o->st = P->ctl_host->st;
+  o->ctl = P->ctl;
+  const Plan& pl = P->plan;
+  o->fwd = P->team_terms;
+  o->adj = P->team_terms + pl.fwd.size();
+  o->adj_m = P->team_terms + pl.fwd.size() + pl.adj.size();
+  o->nfwd = (int32_t)pl.fwd.size();
+  o->nadj = (int32_t)pl.adj.size();
+  o->nadj_m = (int32_t)pl.adj_m.size();
+  o->nseg = (int32_t)P->q.size();
+  o->lanes = lanes_for(pl, s);
+  o->do_setup = do_setup ? 1 : 0;
+  o->tune = tune ? 1 : 0;
+  o->want_out = (!tune && (P->x_out || P->y_out || P->s_out)) ? 1 : 0;
+  o->want_uv = (!tune && P->uv_out) ? 1 : 0;
+  o->n = P->n;
+  o->m = P->m;
+  o->z = P->z;
+  o->l = P->l;
+  int64_t off = P->z + P->l;
+  for (size_t j = 0; j < P->q.size(); ++j) {
+    o->seg_head[j] = off;
+    off += P->q[j];
+    o->seg_end[j] = off;
+  }
+  o->nb = P->nb;
+  o->nc = P->nc;
+  o->bf = P->bf;
+  o->cf = P->cf;
+  o->ux = P->ux; o->uy = P->uy; o->vs = P->vs; o->zx = P->zx; o->rhs = P->rhs; o->r = P->r;
+  o->p = P->p; o->q = P->qv; o->gx = P->gx; o->gy = P->gy; o->wy = P->wy; o->t = P->t;
+  o->zy = P->zy; o->cm = P->cm; o->cn = P->cn; o->gz = P->gz; o->az = P->az;
+  o->scratch = P->team_scratch;
+  o->warm = P->warm_dev;
+  o->out = P->out_dev;
+  o->uv = P->uv_dev;
+}
+
+struct Launch {
+  int C = 1, T = 512;
+  int64_t grid = 1;
+  size_t smem = 0;
+};
+
+template <int MaxT>
+cf_err launch_k(const Launch& L, const Prob* probs, const int32_t* order, int32_t nbig, int32_t nsmall,
+                unsigned int* counters, cudaStream_t s) {
+  auto kern = k_team<MaxT>;
+  if (L.smem > 48 * 1024) CF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)L.grid);
+  cfg.blockDim = dim3((unsigned)L.T);
+  cfg.dynamicSmemBytes = L.smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  if (L.C > 1) {
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)L.C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+  }
+  CF_CUDA(cudaLaunchKernelEx(&cfg, kern, probs, order, nbig, nsmall, counters, (int32_t)L.C));
+  return CF_OK;
+}
+
+template <int MaxT>
+cf_err max_grid(const Launch& L, int sm_count, int64_t* out) {
+  auto kern = k_team<MaxT>;
+  if (L.smem > 48 * 1024) CF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem));
+  if (L.C == 1) {
+    int nb = 0;
+    CF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, L.T, L.smem));
+    *out = (int64_t)std::max(nb, 1) * sm_count;
+    return CF_OK;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(L.C * sm_count));
+  cfg.blockDim = dim3((unsigned)L.T);
+  cfg.dynamicSmemBytes = L.smem;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)L.C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int nc = 0;
+  CF_CUDA(cudaOccupancyMaxActiveClusters(&nc, kern, &cfg));
+  *out = (int64_t)std::max(nc, 1) * L.C;
+  return CF_OK;
+}
+
+cf_err dispatch(const Launch& L, bool query, int sm_count, int64_t* grid, const Prob* probs,
+                const int32_t* order, int32_t nbig, int32_t nsmall, unsigned int* counters, cudaStream_t s) {
+  switch (L.T) {
+    case 256:
+      return query ? max_grid<256>(L, sm_count, grid) : launch_k<256>(L, probs, order, nbig, nsmall, counters, s);
+    case 512:
+      return query ? max_grid<512>(L, sm_count, grid) : launch_k<512>(L, probs, order, nbig, nsmall, counters, s);
+    case 1024:
+      return query ? max_grid<1024>(L, sm_count, grid) : launch_k<1024>(L, probs, order, nbig, nsmall, counters, s);
+  }
+  return fail(CF_E_INVALID, "team engine: threads per CTA must be 256, 512 or 1024");
+}
+
+// Launch table layout: counters (2), order (count), then the entries.
+size_t table_bytes(size_t count) {
+  return 256 + align_up(count * sizeof(int32_t), 256) + count * sizeof(Prob);
+}
+
+// Builds the table for `probs` under schedule s into host memory `h` (of
+// table_bytes(count)), orders big problems then small ones, longest first.
+void build_table(const std::vector<cf_problem*>& probs, const cf_schedule& s, bool tune, char* h,
+                 int32_t* nbig_out, int32_t* nsmall_out, size_t* smem_out, std::vector<int>* setups) {
+  const size_t count = probs.size();
+  std::memset(h, 0, 256);
+  int32_t* order = (int32_t*)(h + 256);
+  Prob* ents = (Prob*)(h + 256 + align_up(count * sizeof(int32_t), 256));
+  std::vector<int32_t> big, small;
+  size_t smem = 0;
+  setups->assign(count, 0);
+  for (size_t i = 0; i < count; ++i) {
+    cf_problem* P = probs[i];
+    const int sig = sig_for(P, s);
+    const bool do_setup = !tune && !(P->setup_done && P->setup_sig == sig);
+    (*setups)[i] = do_setup ? 1 : 0;
+    fill_prob(P, s, do_setup, tune, &ents[i]);
+    (is_big(P, s) ? big : small).push_back((int32_t)i);
+    smem = std::max(smem, (size_t)P->plan.smem_floats * sizeof(float));
+  }
+  auto longer = [&](int32_t a, int32_t b) {
+    const double wa = probs[a]->plan.pass_bytes, wb = probs[b]->plan.pass_bytes;
+    return wa != wb ? wa > wb : a < b;
+  };
+  std::sort(big.begin(), big.end(), longer);
+  std::sort(small.begin(), small.end(), longer);
+  size_t k = 0;
+  for (int32_t i : big) order[k++] = i;
+  for (int32_t i : small) order[k++] = i;
+  *nbig_out = (int32_t)big.size();
+  *nsmall_out = (int32_t)small.size();
+  *smem_out = smem;
+}
+
+// Enqueues the launch of a table already on the device at `dev` (same
+// layout) on stream s.
+cf_err enqueue(cf_ctx* ctx, const cf_schedule& s, char* dev, size_t count, int32_t nbig, int32_t nsmall,
+               size_t smem, cudaStream_t st) {
+  Launch L;
+  L.T = s.threads;
+  L.C = nbig > 0 ? s.cluster : 1;
+  L.smem = smem;
+  int64_t cap = 1;
+  CF_TRY(dispatch(L, true, ctx->sm_count, &cap, nullptr, nullptr, 0, 0, nullptr, nullptr));
+  const int64_t need = (int64_t)nbig * L.C + nsmall;  // CTAs that can be busy at once
+  int64_t g = std::min<int64_t>(cap, std::max<int64_t>(need, 1));
+  g = std::max<int64_t>((g + L.C - 1) / L.C * L.C, L.C);
+  if (g > cap) g = std::max<int64_t>(cap / L.C * L.C, L.C);
+  L.grid = g;
+  unsigned int* counters = (unsigned int*)dev;
+  const int32_t* order = (const int32_t*)(dev + 256);
+  const Prob* ents = (const Prob*)(dev + 256 + align_up(count * sizeof(int32_t), 256));
+  return dispatch(L, false, ctx->sm_count, nullptr, ents, order, nbig, nsmall, counters, st);
+}
+
+cf_schedule sched_of(cf_ctx* ctx) {
+  std::lock_guard<std::mutex> lk(ctx->sched_mu);
+  return ctx->sched;
+}
+
+}  // namespace
+
+cf_err solo_launch(cf_problem* P, const cf_settings* st, const double* warm_uv, bool join_ctx) {
+  const cf_schedule s = sched_of(P->ctx);
+  const size_t bytes = table_bytes(1);
+  if (!P->team_buf) {
+    cudaError_t e = cudaMalloc(&P->team_buf, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      P->team_buf = nullptr;
+      return fail(CF_E_OOM, "solve: team launch table allocation failed");
+    }
+    CF_CUDA(cudaMallocHost(&P->team_buf_host, bytes));
+  }
+  const int64_t N = P->n + P->m + 1;
+  CF_CUDA(cudaEventRecord(P->ev_in, P->ctx->stream));
+  CF_CUDA(cudaStreamWaitEvent(P->stream, P->ev_in, 0));
+  if (warm_uv) CF_TRY(copy_any(P->warm_dev, warm_uv, 2 * N * sizeof(double), P->stream));
+  int32_t nbig = 0, nsmall = 0;
+  size_t smem = 0;
+  std::vector<int> setups;
+  // the pinned staging buffer is free: the previous solve of P finished
+  build_table({P}, s, false, (char*)P->team_buf_host, &nbig, &nsmall, &smem, &setups);
+  CF_CUDA(cudaMemcpyAsync(P->team_buf, P->team_buf_host, bytes, cudaMemcpyHostToDevice, P->stream));
+  P->t_launch = now_ns();
+  CF_TRY(enqueue(P->ctx, s, (char*)P->team_buf, 1, nbig, nsmall, smem, P->stream));
+  CF_CUDA(cudaMemcpyAsync(P->ctl_host, P->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, P->stream));
+  CF_CUDA(cudaEventRecord(P->ev_out, P->stream));
+  if (join_ctx) CF_CUDA(cudaStreamWaitEvent(P->ctx->stream, P->ev_out, 0));
+  P->ran_setup = setups[0] != 0;
+  P->setup_done = true;
+  P->setup_sig = sig_for(P, s);
+  P->last_engine = CF_ENGINE_TEAM;
+  P->team_launches = 1;
+  (void)st;
+  return CF_OK;
+}
+
+namespace {
+
+// One launch of `probs` (one context) on stream s; table memory from the
+// stream-ordered allocator, freed after the launch.
+cf_err launch_group(const std::vector<cf_problem*>& probs, const cf_schedule& s, bool tune, cudaStream_t st,
+                    std::vector<int>* setups) {
+  cf_ctx* ctx = probs[0]->ctx;
+  const size_t bytes = table_bytes(probs.size());
+  std::vector<char> host(bytes);
+  int32_t nbig = 0, nsmall = 0;
+  size_t smem = 0;
+  build_table(probs, s, tune, host.data(), &nbig, &nsmall, &smem, setups);
+  char* dev = nullptr;
+  CF_CUDA(cudaMallocAsync((void**)&dev, bytes, st));
+  CF_CUDA(cudaMemcpyAsync(dev, host.data(), bytes, cudaMemcpyHostToDevice, st));
+  cf_err r = enqueue(ctx, s, dev, probs.size(), nbig, nsmall, smem, st);
+  cudaFreeAsync(dev, st);
+  return r;
+}
+
+}  // namespace
+
+cf_err batch_launch(const std::vector<cf_problem*>& probs, const cf_settings* st) {
+  if (probs.empty()) return CF_OK;
+  (void)st;
+  cf_ctx* ctx = probs[0]->ctx;
+  const cf_schedule s = sched_of(ctx);
+  cudaStream_t bs = nullptr;
+  cudaEvent_t ev = nullptr;
+  CF_CUDA(cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking));
+  cf_err r = [&]() -> cf_err {
+    CF_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    CF_CUDA(cudaEventRecord(ev, ctx->stream));
+    CF_CUDA(cudaStreamWaitEvent(bs, ev, 0));
+    const int64_t t0 = now_ns();
+    std::vector<int> setups;
+    CF_TRY(launch_group(probs, s, false, bs, &setups));
+    CF_CUDA(cudaEventRecord(ev, bs));
+    for (size_t i = 0; i < probs.size(); ++i) {
+      cf_problem* P = probs[i];
+      P->t_launch = t0;
+      CF_CUDA(cudaStreamWaitEvent(P->stream, ev, 0));
+      CF_CUDA(cudaMemcpyAsync(P->ctl_host, P->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, P->stream));
+      CF_CUDA(cudaEventRecord(P->ev_out, P->stream));
+      P->ran_setup = setups[i] != 0;
+      P->setup_done = true;
+      P->setup_sig = sig_for(P, s);
+      P->last_engine = CF_ENGINE_TEAM;
+      P->team_launches = i == 0 ? 1 : 0;
+    }
+    return CF_OK;
+  }();
+  if (ev) cudaEventDestroy(ev);
+  cudaStreamDestroy(bs);  // released once its work is done
+  return r;
+}
+
+}  // namespace team
+
+// ------------------------------------------------------------ schedules
+cf_schedule default_schedule() {
+  cf_schedule s{};
+  s.cluster = 4;
+  s.threads = 512;
+  s.csr_nnz_per_lane = 4;
+  s.team_bytes = 4e6;
+  s.auto_max_bytes = 48e6;
+  return s;
+}
+
+bool schedule_valid(const cf_schedule& s, std::string* why) {
+  if (s.cluster != 1 && s.cluster != 2 && s.cluster != 4 && s.cluster != 8) {
+    *why = "cluster must be 1, 2, 4 or 8";
+    return false;
+  }
+  if (s.threads != 256 && s.threads != 512 && s.threads != 1024) {
+    *why = "threads must be 256, 512 or 1024";
+    return false;
+  }
+  if (s.csr_nnz_per_lane < 1 || s.csr_nnz_per_lane > 64) {
+    *why = "csr_nnz_per_lane must be in [1, 64]";
+    return false;
+  }
+  if (!(s.team_bytes >= 0) || !(s.auto_max_bytes >= 0)) {
+    *why = "team_bytes and auto_max_bytes must be >= 0";
+    return false;
+  }
+  return true;
+}
+
+cf_err pick_engine(cf_problem* P, const cf_settings* st, int* engine) {
+  if (st->host_loop || st->engine == CF_ENGINE_GRAPH) {
+    *engine = CF_ENGINE_GRAPH;
+    return CF_OK;
+  }
+  if (st->engine == CF_ENGINE_TEAM) {
+    if (!P->plan.ok) return fail(CF_E_INVALID, "solve: the team engine does not support this problem: " + P->plan.why);
+    *engine = CF_ENGINE_TEAM;
+    return CF_OK;
+  }
+  double lim;
+  {
+    std::lock_guard<std::mutex> lk(P->ctx->sched_mu);
+    lim = P->ctx->sched.auto_max_bytes;
+  }
+  *engine = (P->plan.ok && P->plan.pass_bytes <= lim) ? CF_ENGINE_TEAM : CF_ENGINE_GRAPH;
+  return CF_OK;
+}
+
+}  // namespace cf
+
+using namespace cf;
+
+// ------------------------------------------------------------------ C ABI
+extern "C" cf_err cf_problem_team_info(const cf_problem* p, int32_t* supported, double* pass_bytes, char* why,
+                                       size_t why_len) {
+  if (!p) return fail(CF_E_INVALID, "cf_problem_team_info: NULL problem");
+  if (supported) *supported = p->plan.ok ? 1 : 0;
+  if (pass_bytes) *pass_bytes = p->plan.ok ? p->plan.pass_bytes : 0.0;
+  if (why && why_len > 0) {
+    const size_t k = std::min(why_len - 1, p->plan.why.size());
+    std::memcpy(why, p->plan.why.data(), k);
+    why[k] = 0;
+  }
+  return CF_OK;
+}
+
+extern "C" cf_err solve_batch_tune(cf_problem* const* probs, int32_t count, int32_t iters, cf_tune_info* info) {
+  if (count < 0 || (count > 0 && !probs) || iters < 1 || iters > 100000)
+    return fail(CF_E_INVALID, "solve_batch_tune: bad arguments");
+  if (info) std::memset(info, 0, sizeof(*info));
+  if (count == 0) return CF_OK;
+  for (int32_t i = 0; i < count; ++i) {
+    if (!probs[i]) return fail(CF_E_INVALID, "solve_batch_tune: NULL problem");
+    if (probs[i]->ctx != probs[0]->ctx) return fail(CF_E_INVALID, "solve_batch_tune: problems of different contexts");
+    for (int32_t j = 0; j < i; ++j)
+      if (probs[j] == probs[i]) return fail(CF_E_INVALID, "solve_batch_tune: a problem appears twice");
+  }
+  cf_ctx* ctx = probs[0]->ctx;
+  const int64_t t0 = now_ns();
+  std::vector<std::unique_lock<std::mutex>> locks;
+  for (int32_t i = 0; i < count; ++i) locks.emplace_back(probs[i]->mtx);
+  DevGuard guard(ctx->device);
+  cf_schedule held;
+  {
+    std::lock_guard<std::mutex> lk(ctx->sched_mu);
+    held = ctx->sched;
+  }
+  cf_settings st;
+  cf_settings_default(&st);
+  st.max_iters = iters;
+  st.check_interval = 1 << 30;
+  st.cg_fixed_iters = 2;
+  std::vector<cf_problem*> tp;
+  for (int32_t i = 0; i < count; ++i) {
+    cf_problem* P = probs[i];
+    if (!P->plan.ok || P->plan.pass_bytes > held.auto_max_bytes) continue;
+    CF_TRY(ensure_state(P));
+    write_settings(P, &st, false);
+    P->x_out = P->y_out = P->s_out = P->uv_out = nullptr;
+    tp.push_back(P);
+  }
+  if (tp.empty()) return CF_OK;
+  cudaStream_t s = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CF_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  int ncand = 0;
+  auto timed = [&](const cf_schedule& sc, double* ms) -> cf_err {
+    std::vector<int> setups;
+    CF_CUDA(cudaEventRecord(e0, s));
+    CF_TRY(team::launch_group(tp, sc, true, s, &setups));
+    CF_CUDA(cudaEventRecord(e1, s));
+    CF_CUDA(cudaEventSynchronize(e1));
+    float f = 0.f;
+    CF_CUDA(cudaEventElapsedTime(&f, e0, e1));
+    *ms = f;
+    ++ncand;
+    return CF_OK;
+  };
+  cf_schedule best = held;
+  double best_ms = 0.0, held_ms = 0.0;
+  cf_err r = [&]() -> cf_err {
+    CF_CUDA(cudaEventCreate(&e0));
+    CF_CUDA(cudaEventCreate(&e1));
+    CF_CUDA(cudaEventRecord(e0, ctx->stream));
+    CF_CUDA(cudaStreamWaitEvent(s, e0, 0));
+    double ms = 0.0;
+    CF_TRY(timed(held, &ms));  // warm-up (module load, caches)
+    CF_TRY(timed(held, &held_ms));
+    best_ms = held_ms;
+    // stage 1: one-CTA teams; threads per CTA and CSR lanes per row
+    cf_schedule b1 = held;
+    b1.cluster = 1;
+    double b1_ms = 1e300;
+    for (int T : {256, 512, 1024})
+      for (int npl : {2, 4, 8}) {
+        cf_schedule c = held;
+        c.cluster = 1;
+        c.threads = T;
+        c.csr_nnz_per_lane = npl;
+        CF_TRY(timed(c, &ms));
+        if (ms < b1_ms) {
+          b1_ms = ms;
+          b1 = c;
+        }
+      }
+    if (b1_ms < best_ms) {
+      best_ms = b1_ms;
+      best = b1;
+    }
+    // stage 2: cluster teams for the largest problems
+    std::vector<double> w;
+    for (cf_problem* P : tp) w.push_back(P->plan.pass_bytes);
+    std::sort(w.begin(), w.end(), std::greater<double>());
+    for (int C : {2, 4, 8})
+      for (double f : {0.02, 0.06, 0.15}) {
+        const size_t k = std::min(w.size() - 1, (size_t)std::floor(f * (double)w.size()));
+        cf_schedule c = b1;
+        c.cluster = C;
+        c.team_bytes = w[k];
+        CF_TRY(timed(c, &ms));
+        if (ms < best_ms) {
+          best_ms = ms;
+          best = c;
+        }
+      }
+    return CF_OK;
+  }();
+  cudaStreamSynchronize(s);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaStreamDestroy(s);
+  // the timing runs zeroed g: every problem redoes its setup
+  for (cf_problem* P : tp) P->setup_done = false;
+  if (r != CF_OK) return r;
+  best.auto_max_bytes = held.auto_max_bytes;
+  {
+    std::lock_guard<std::mutex> lk(ctx->sched_mu);
+    ctx->sched = best;
+  }
+  if (info) {
+    info->candidates = ncand;
+    info->problems = (int32_t)tp.size();
+    info->seconds = (now_ns() - t0) * 1e-9;
+    info->default_ms = held_ms;
+    info->best_ms = best_ms;
+    info->best = best;
+  }
+  return CF_OK;
+}

@@ -45,11 +45,39 @@ def test_struct_layouts_match_c(tmp_path):
     assert [int(v) for v in out] == got
 
 
+def test_team_struct_layouts_match_c(tmp_path):
+    from paper_1609_03488_b300 import binding as b
+    prog = tmp_path / "sz2.c"
+    prog.write_text('#include "cvxb300.h"\n#include <stdio.h>\n#include <stddef.h>\n'
+                    'int main(void){printf("%zu %zu %zu %zu %zu %d %d %d\\n", sizeof(cf_schedule),'
+                    ' sizeof(cf_tune_info), offsetof(cf_tune_info, best), offsetof(cf_settings, engine),'
+                    ' offsetof(cf_schedule, team_bytes), CF_ENGINE_AUTO, CF_ENGINE_GRAPH, CF_ENGINE_TEAM);'
+                    'return 0;}\n')
+    exe = tmp_path / "sz2"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
+    got = [C.sizeof(b.cf_schedule), C.sizeof(b.cf_tune_info), b.cf_tune_info.best.offset,
+           b.cf_settings.engine.offset, b.cf_schedule.team_bytes.offset,
+           b.CF_ENGINE_AUTO, b.CF_ENGINE_GRAPH, b.CF_ENGINE_TEAM]
+    assert [int(v) for v in out] == got
+
+
+def test_team_entry_points_reject_bad_arguments_without_a_device():
+    from paper_1609_03488_b300 import binding as b
+    s = b.cf_schedule()
+    assert b.lib.cf_ctx_get_schedule(None, C.byref(s)) == b.CF_E_INVALID
+    assert b.lib.cf_ctx_set_schedule(None, C.byref(s)) == b.CF_E_INVALID
+    assert b.lib.solve_batch_tune(None, -1, 10, None) == b.CF_E_INVALID
+    assert b.lib.solve_batch_tune(None, 0, 0, None) == b.CF_E_INVALID
+    assert b.lib.solve_batch_tune(None, 0, 10, None) == b.CF_OK    # empty batch: nothing to time
+
+
 def test_settings_defaults():
     from paper_1609_03488_b300 import binding
     s = binding.cf_settings_default()
     assert (s.eps, s.eps_infeas, s.alpha, s.max_iters, s.check_interval) == (1e-4, 1e-4, 1.5, 100000, 10)
     assert (s.cg_max_iters, s.cg_fixed_iters, s.cg_tol_rel, s.cg_tol_exp) == (50, 0, 1.0, 1.5)
+    assert s.engine == binding.CF_ENGINE_AUTO and s.host_loop == 0
 
 
 def test_null_arguments_are_rejected_without_a_device():

@@ -9,6 +9,10 @@ through the C ABI.
   of an FP64 optimum from an independent solver or from the oracle;
 * certificates of infeasible / unbounded problems satisfy their definitions;
 * batched and served solves return bit-identical results to solo solves.
+
+Every check runs on both solver programs: the graph engine (one CUDA graph
+per solve, whole-GPU kernels) and the team engine (one persistent kernel per
+solve or batch).
 """
 import numpy as np
 import pytest
@@ -20,6 +24,7 @@ from tests.helpers import fp64_residuals, objective_rel_err, rel
 
 pytestmark = pytest.mark.gpu
 EPS = 1e-4
+ENGINES = ["graph", "team"]
 
 
 @pytest.fixture(scope="module")
@@ -35,9 +40,9 @@ def ctx(B):
     return B.Context(0)
 
 
-def _solve(B, ctx, prob, **kw):
+def _solve(B, ctx, prob, engine="auto", **kw):
     P = B.cone_problem_create(ctx, prob)
-    st = B.settings(**kw)
+    st = B.settings(engine=engine, **kw)
     info, x, y, s = B.solve(P, st)
     return info, x, y, s, P
 
@@ -58,8 +63,9 @@ def _check_solution(prob, info, x, y, s, p_star, eps=EPS):
 
 
 # ---------------------------------------------------------------- trajectory
+@pytest.mark.parametrize("engine", ENGINES)
 @pytest.mark.parametrize("family", ["deconv", "lasso"])
-def test_first_20_iterates_match_oracle(B, ctx, family):
+def test_first_20_iterates_match_oracle(B, ctx, family, engine):
     if family == "deconv":
         prob = synth.deconv(n_x=1000, L=100, seed=synth.BASE_SEED + 1)     # the small workload
     else:
@@ -69,7 +75,7 @@ def test_first_20_iterates_match_oracle(B, ctx, family):
     P = B.cone_problem_create(ctx, prob)
     N = prob["A"]["n"] + prob["A"]["m"] + 1
     for k in (1, 2, 3, 5, 10, 15, 20):
-        st = B.settings(max_iters=k, check_interval=10 ** 6, cg_fixed_iters=3)
+        st = B.settings(max_iters=k, check_interval=10 ** 6, cg_fixed_iters=3, engine=engine)
         uv = np.empty(2 * N)
         info = B.cf_info()
         B.check(B.lib.solve(P.h, B.C.byref(st), None, None, None, None, B._ptr(uv), B.C.byref(info)), "solve")
@@ -80,43 +86,47 @@ def test_first_20_iterates_match_oracle(B, ctx, family):
 
 
 # ---------------------------------------------------------------- solutions
+@pytest.mark.parametrize("engine", ENGINES)
 @pytest.mark.parametrize("n_x,L,eps", [(300, 30, SOLVE_EPS), (1000, 100, 2e-5)])
-def test_deconv_solution(B, ctx, n_x, L, eps):
+def test_deconv_solution(B, ctx, n_x, L, eps, engine):
     """Against the NNLS optimum (an independent FP64 solver).  The small
     deconvolution workload (n = 1000, L = 100) needs residuals of 2e-5 before
     its objective is within 1e-4 (the dual residual converges slowly)."""
     prob = synth.deconv(n_x=n_x, L=L, seed=synth.BASE_SEED + 1)
     K = linop.densify(prob["A"]["parts"][2]["parts"][0]["parts"][0])
     _, p_star = so.nnls(K, prob["meta"]["b_obs"], maxiter=50 * n_x)
-    info, x, y, s, _ = _solve(B, ctx, prob, eps=eps, max_iters=300000)
+    info, x, y, s, _ = _solve(B, ctx, prob, engine, eps=eps, max_iters=300000)
     _check_solution(prob, info, x, y, s, p_star)
 
 
-def test_small_deconvolution_same_settings_as_oracle(B, ctx):
+@pytest.mark.parametrize("engine", ENGINES)
+def test_small_deconvolution_same_settings_as_oracle(B, ctx, engine):
     """The small deconvolution workload at eps = 1e-4 with the default CG
     rule, GPU (float32) and oracle (float64, same CG rule): same stopping
     iteration, objectives within 1e-5, both within the 1e-4 residuals."""
     prob = synth.deconv(n_x=1000, L=100, seed=synth.BASE_SEED + 1)
     ref = scs.problem_solve(prob, eps=EPS, max_iters=100000, linsys="cg")
     assert ref["status"] == scs.SOLVED
-    info, x, y, s, _ = _solve(B, ctx, prob, eps=EPS)
+    info, x, y, s, _ = _solve(B, ctx, prob, engine, eps=EPS)
     assert info["status_name"] == "solved"
     assert abs(info["iters"] - ref["iters"]) <= 2 * 10, (info["iters"], ref["iters"])
     assert objective_rel_err(prob["c"] @ x, ref["pobj"]) <= 1e-5
     assert max(fp64_residuals(prob, x, y, s)) <= EPS
 
 
+@pytest.mark.parametrize("engine", ENGINES)
 @pytest.mark.parametrize("storage", ["fp32", "bf16", "fp8"])
-def test_lasso_solution(B, ctx, storage):
+def test_lasso_solution(B, ctx, storage, engine):
     prob = synth.lasso(m_d=400, p=200, seed=synth.BASE_SEED + 3, storage=storage)
     ref = scs.problem_solve(prob, eps=1e-9, max_iters=200000)   # on the quantised instance
     assert ref["status"] == scs.SOLVED
-    info, x, y, s, _ = _solve(B, ctx, prob, eps=SOLVE_EPS)
+    info, x, y, s, _ = _solve(B, ctx, prob, engine, eps=SOLVE_EPS)
     _check_solution(prob, info, x, y, s, ref["pobj"])
 
 
+@pytest.mark.parametrize("engine", ENGINES)
 @pytest.mark.parametrize("storage", ["fp32", "bf16"])
-def test_sparse_lp_solution(B, ctx, storage):
+def test_sparse_lp_solution(B, ctx, storage, engine):
     prob = synth.lp(m_d=300, n_x=150, density=0.05, seed=synth.BASE_SEED + 4, storage=storage)
     ref = scs.problem_solve(prob, eps=1e-9, max_iters=400000)
     assert ref["status"] == scs.SOLVED
@@ -124,21 +134,23 @@ def test_sparse_lp_solution(B, ctx, storage):
         D = linop.densify(prob["A"]["parts"][0])
         hi = so.linprog(prob["c"], A_ub=D, b_ub=prob["b"][:300], bounds=(0, None), method="highs")
         assert objective_rel_err(ref["pobj"], hi.fun) <= 1e-7
-    info, x, y, s, _ = _solve(B, ctx, prob, eps=SOLVE_EPS)
+    info, x, y, s, _ = _solve(B, ctx, prob, engine, eps=SOLVE_EPS)
     _check_solution(prob, info, x, y, s, ref["pobj"])
 
 
+@pytest.mark.parametrize("engine", ENGINES)
 @pytest.mark.parametrize("seed", range(3))
-def test_mixed_cones_solution(B, ctx, seed):
+def test_mixed_cones_solution(B, ctx, seed, engine):
     rng = np.random.default_rng(400 + seed)
     prob = synth.mixed_cone_problem(rng, n=8, soc_sizes=(3, 1, 5), z=2, l=4)
     ref = scs.problem_solve(prob, eps=1e-10, max_iters=400000)
     assert ref["status"] == scs.SOLVED
-    info, x, y, s, _ = _solve(B, ctx, prob, eps=SOLVE_EPS)
+    info, x, y, s, _ = _solve(B, ctx, prob, engine, eps=SOLVE_EPS)
     _check_solution(prob, info, x, y, s, ref["pobj"])
 
 
-def test_large_soc_spanning_many_chunks(B, ctx):
+@pytest.mark.parametrize("engine", ENGINES)
+def test_large_soc_spanning_many_chunks(B, ctx, engine):
     """A deconvolution whose single SOC block (9100 rows) spans several
     projection chunks, so its norm is reduced across CTAs."""
     prob = synth.deconv(n_x=8000, L=1100, seed=7)
@@ -146,7 +158,7 @@ def test_large_soc_spanning_many_chunks(B, ctx):
                             cg_fixed_steps=2, trajectory=60)
     P = B.cone_problem_create(ctx, prob)
     N = prob["A"]["n"] + prob["A"]["m"] + 1
-    st = B.settings(max_iters=60, check_interval=10 ** 6, cg_fixed_iters=2)
+    st = B.settings(max_iters=60, check_interval=10 ** 6, cg_fixed_iters=2, engine=engine)
     uv = np.empty(2 * N)
     info = B.cf_info()
     B.check(B.lib.solve(P.h, B.C.byref(st), None, None, None, None, B._ptr(uv), B.C.byref(info)), "solve")
@@ -155,12 +167,13 @@ def test_large_soc_spanning_many_chunks(B, ctx):
 
 
 # ---------------------------------------------------------------- certificates
+@pytest.mark.parametrize("engine", ENGINES)
 @pytest.mark.parametrize("seed", range(3))
-def test_infeasible_certificate(B, ctx, seed):
+def test_infeasible_certificate(B, ctx, seed, engine):
     rng = np.random.default_rng(200 + seed)
     D, b_d, c = synth.random_tiny_lp(rng, 3, 3, "infeasible")
     prob = synth.dense_lp(D, b_d, c)
-    info, x, y, s, _ = _solve(B, ctx, prob, eps=1e-5, eps_infeas=1e-5)
+    info, x, y, s, _ = _solve(B, ctx, prob, engine, eps=1e-5, eps_infeas=1e-5)
     assert info["status_name"] == "infeasible", info
     A = linop.densify(prob["A"])
     assert abs(prob["b"] @ y + 1.0) < 1e-6
@@ -168,12 +181,13 @@ def test_infeasible_certificate(B, ctx, seed):
     assert np.linalg.norm(A.T @ y) <= 1e-4
 
 
+@pytest.mark.parametrize("engine", ENGINES)
 @pytest.mark.parametrize("seed", range(3))
-def test_unbounded_certificate(B, ctx, seed):
+def test_unbounded_certificate(B, ctx, seed, engine):
     rng = np.random.default_rng(300 + seed)
     D, b_d, c = synth.random_tiny_lp(rng, 3, 3, "unbounded")
     prob = synth.dense_lp(D, b_d, c)
-    info, x, y, s, _ = _solve(B, ctx, prob, eps=1e-5, eps_infeas=1e-5)
+    info, x, y, s, _ = _solve(B, ctx, prob, engine, eps=1e-5, eps_infeas=1e-5)
     assert info["status_name"] == "unbounded", info
     A = linop.densify(prob["A"])
     assert abs(prob["c"] @ x + 1.0) < 1e-6
@@ -182,17 +196,18 @@ def test_unbounded_certificate(B, ctx, seed):
 
 
 # ---------------------------------------------------------------- edge cases
-def test_max_iters_and_warm_start_roundtrip(B, ctx):
+@pytest.mark.parametrize("engine", ENGINES)
+def test_max_iters_and_warm_start_roundtrip(B, ctx, engine):
     prob = synth.deconv(n_x=200, L=20, seed=3)
     P = B.cone_problem_create(ctx, prob)
     N = prob["A"]["n"] + prob["A"]["m"] + 1
-    st = B.settings(max_iters=1)
+    st = B.settings(max_iters=1, engine=engine)
     info, *_ = B.solve(P, st)
     assert info["iters"] == 1 and info["status_name"] == "max_iters" and info["checks"] == 1
     # 7 iterations, then 5 more from the returned (u, v), equal 12 straight
     # ones when each CG solve is exact (the CG warm start is not carried over)
     def run(k, warm=None):
-        st = B.settings(max_iters=k, check_interval=10 ** 6, cg_fixed_iters=40)
+        st = B.settings(max_iters=k, check_interval=10 ** 6, cg_fixed_iters=40, engine=engine)
         uv = np.empty(2 * N)
         info = B.cf_info()
         B.check(B.lib.solve(P.h, B.C.byref(st), None, None, None, B._ptr(warm), B._ptr(uv),
@@ -213,8 +228,8 @@ def test_host_loop_equals_graph(B, ctx, family):
             "lasso": lambda: synth.lasso(m_d=300, p=150, seed=8, storage="bf16"),
             "lp": lambda: synth.lp(m_d=300, n_x=150, density=0.05, seed=8)}[family]()
     P = B.cone_problem_create(ctx, prob)
-    B.solve(P, B.settings(max_iters=1))          # setup runs here, so neither call below counts it
-    a = B.solve(P, B.settings(max_iters=240, host_loop=0))
+    B.solve(P, B.settings(max_iters=1, engine="graph"))  # setup runs here, so neither call below counts it
+    a = B.solve(P, B.settings(max_iters=240, host_loop=0, engine="graph"))
     b = B.solve(P, B.settings(max_iters=240, host_loop=1))
     for k in ("iters", "cg_iters_total", "checks", "status", "kernel_launches"):
         assert a[0][k] == b[0][k], k
@@ -222,11 +237,12 @@ def test_host_loop_equals_graph(B, ctx, family):
         np.testing.assert_array_equal(u, v)
 
 
-def test_repeat_solves_are_bitwise_identical(B, ctx):
+@pytest.mark.parametrize("engine", ENGINES)
+def test_repeat_solves_are_bitwise_identical(B, ctx, engine):
     prob = synth.lasso(m_d=200, p=100, seed=11)
     P = B.cone_problem_create(ctx, prob)
-    a = B.solve(P)
-    b = B.solve(P)
+    a = B.solve(P, B.settings(engine=engine))
+    b = B.solve(P, B.settings(engine=engine))
     assert a[0]["iters"] == b[0]["iters"]
     np.testing.assert_array_equal(a[1], b[1])
     np.testing.assert_array_equal(a[2], b[2])
@@ -241,7 +257,8 @@ def test_invalid_inputs(B, ctx):
     with pytest.raises(B.CfError):
         B.Problem(ctx, op, prob["b"], prob["c"], {"z": 0, "l": 50, "q": [0, 55]})
     P = B.Problem(ctx, op, prob["b"], prob["c"], prob["cone"])
-    for bad in (dict(alpha=2.5), dict(eps=0.0), dict(max_iters=0), dict(check_interval=0)):
+    for bad in (dict(alpha=2.5), dict(eps=0.0), dict(max_iters=0), dict(check_interval=0), dict(engine=7),
+                dict(engine=2, host_loop=1)):
         with pytest.raises(B.CfError) as e:
             B.solve(P, B.settings(**bad))
         assert e.value.code == B.CF_E_INVALID
@@ -251,12 +268,13 @@ def test_invalid_inputs(B, ctx):
         B.cf_op_csr(ctx, 2, 2, [0, 1, 2], [0, 5], [1.0, 1.0])
 
 
-def test_nan_data_reports_numerical(B, ctx):
+@pytest.mark.parametrize("engine", ENGINES)
+def test_nan_data_reports_numerical(B, ctx, engine):
     prob = synth.deconv(n_x=50, L=5, seed=3)
     k = prob["A"]["parts"][2]["parts"][0]["parts"][0]["kernel"].copy()
     k[2] = np.nan
     prob["A"]["parts"][2]["parts"][0]["parts"][0]["kernel"] = k
-    info, *_ = _solve(B, ctx, prob, max_iters=50)
+    info, *_ = _solve(B, ctx, prob, engine, max_iters=50)
     assert info["status_name"] == "numerical", info
 
 
@@ -298,11 +316,13 @@ def _mix():
             synth.lp(m_d=500, n_x=250, density=0.02, seed=5, storage="bf16")]
 
 
-def test_solve_batch_equals_solo(B, ctx):
+@pytest.mark.parametrize("engine", ["auto", "graph"])
+def test_solve_batch_equals_solo(B, ctx, engine):
     probs = _mix()
     Ps = [B.cone_problem_create(ctx, p) for p in probs]
-    solo = [B.solve(P) for P in Ps]
-    infos, xs, ys, ss = B.solve_batch(Ps)
+    st = B.settings(engine=engine)
+    solo = [B.solve(P, st) for P in Ps]
+    infos, xs, ys, ss = B.solve_batch(Ps, st)
     for (i0, x0, y0, s0), i1, x1, y1, s1 in zip(solo, infos, xs, ys, ss):
         assert i0["iters"] == i1["iters"] and i0["status"] == i1["status"]
         np.testing.assert_array_equal(x0, x1)
@@ -310,14 +330,16 @@ def test_solve_batch_equals_solo(B, ctx):
         np.testing.assert_array_equal(s0, s1)
 
 
+@pytest.mark.parametrize("engine", ["auto", "graph"])
 @pytest.mark.parametrize("slots,budget", [(3, 100 << 20), (8, 100 << 20), (4, 1 << 20)])
-def test_serving_equals_solo(B, ctx, slots, budget):
+def test_serving_equals_solo(B, ctx, slots, budget, engine):
     probs = _mix()
     Ps = [B.cone_problem_create(ctx, p) for p in probs]
-    solo = [B.solve(P) for P in Ps]
+    st = B.settings(engine=engine)
+    solo = [B.solve(P, st) for P in Ps]
     srv = B.Server(ctx, budget, slots)
     order = [0, 1, 2, 3, 4, 5, 4, 2, 0, 1]
-    tickets = [(i, srv.submit(Ps[i])) for i in order]
+    tickets = [(i, srv.submit(Ps[i], st)) for i in order]
     for i, t in tickets:
         info, x, y, s = srv.wait(t, Ps[i])
         assert info["iters"] == solo[i][0]["iters"]
