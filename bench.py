@@ -70,6 +70,9 @@ def parse():
     ap.add_argument("--slots", type=int, default=32, help="serve: concurrent solves")
     ap.add_argument("--budget-gb", type=float, default=60.0, help="serve: device memory budget")
     ap.add_argument("--lp-max-iters", type=int, default=50000)
+    ap.add_argument("--engine", default="auto", choices=["auto", "graph", "team"],
+                    help="solver program (auto: team engine for supported problems with small operator passes)")
+    ap.add_argument("--tune-iters", type=int, default=20, help="lp-batch: ADMM iterations per autotuner candidate")
     ap.add_argument("--host-loop", action="store_true",
                     help="launch the same kernels from the host instead of one CUDA graph per solve "
                          "(for profilers that cannot see kernels inside graph conditional nodes)")
@@ -199,13 +202,25 @@ def run_lp_batch(args, B, ctx, torch):
     probs16 = [synth.lp(m_d=m, n_x=n, density=d, seed=sd, storage="bf16") for m, n, d, sd in sizes]
     t_gen = time.perf_counter() - t0
     nnz = sum(len(p["A"]["parts"][0]["col"]) for p in probs16)
-    st = B.settings(eps=1e-4, max_iters=args.lp_max_iters)
+    st = B.settings(eps=1e-4, max_iters=args.lp_max_iters, engine=args.engine)
     Ps = [B.cone_problem_create(ctx, p) for p in probs16]
+    tune = None
+    if args.engine != "graph" and args.tune_iters > 0:
+        tune = B.solve_batch_tune(Ps, iters=args.tune_iters)     # schedule search (not timed below)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     infos, xs, ys, ss = B.solve_batch(Ps, st)
     t_batch = time.perf_counter() - t0
     lat = [(i["setup_ns"] + i["solve_ns"]) / 1e6 for i in infos]
+    # algorithmic operator bytes of the batch: per problem, its forward-pass
+    # bytes times the passes it ran (rhs adjoint each iteration, forward +
+    # adjoint per CG step, both at each residual check and each refresh)
+    pass_bytes = [B.team_info(P)[1] for P in Ps]
+    alg_bytes = sum(pb * (i["iters"] + 2 * i["cg_iters_total"] + 2 * i["checks"] + 2 * (i["iters"] // 50))
+                    for pb, i in zip(pass_bytes, infos))
+    hbm = {"bound": "hbm", "achieved": alg_bytes / t_batch / 1e9, "peak": hbm_peak(), "unit": "GB/s",
+           "frac": alg_bytes / t_batch / 1e9 / hbm_peak(), "algorithmic_bytes": alg_bytes,
+           "note": "whole batch, wall time; bytes = forward-pass bytes x operator passes of each problem"}
     status = {}
     for i in infos:
         status[i["status_name"]] = status.get(i["status_name"], 0) + 1
@@ -213,7 +228,19 @@ def run_lp_batch(args, B, ctx, torch):
     res16 = max(lp_problem_residuals(probs16[k], xs[k], ys[k], ss[k]) for k in check_idx)
     for P in Ps:
         P.close()
-    # FP32 single-solve form on an evenly spaced sample
+    # the same batch with FP32 operands (same schedule)
+    probs32 = [synth.lp(m_d=m, n_x=n, density=d, seed=sd, storage="fp32") for m, n, d, sd in sizes]
+    P32 = [B.cone_problem_create(ctx, p) for p in probs32]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    infos32, *_ = B.solve_batch(P32, st)
+    t_batch32 = time.perf_counter() - t0
+    for P in P32:
+        P.close()
+    del probs32
+    # plain FP32 single-solve form (one LP at a time, whole-GPU graph engine)
+    # on an evenly spaced sample
+    st_single = B.settings(eps=1e-4, max_iters=args.lp_max_iters, engine="graph")
     idx = list(range(0, len(sizes), max(1, len(sizes) // args.single_sample)))[:args.single_sample]
     t_single, single_status, res32 = 0.0, {}, 0.0
     for k in idx:
@@ -222,7 +249,7 @@ def run_lp_batch(args, B, ctx, torch):
         P = B.cone_problem_create(ctx, pr)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        info, x, y, sv = B.solve(P, st)
+        info, x, y, sv = B.solve(P, st_single)
         t_single += time.perf_counter() - t0
         single_status[info["status_name"]] = single_status.get(info["status_name"], 0) + 1
         res32 = max(res32, lp_problem_residuals(pr, x, y, sv))
@@ -231,13 +258,27 @@ def run_lp_batch(args, B, ctx, torch):
     single_rate = len(idx) / t_single
     return {"metric": "batched solves/s", "value": len(Ps) / t_batch, "unit": "solves/s",
             "workload": f"{len(Ps)} sparse LPs, m~U{{200..20000}}, n=m/2, density~U[0.5%,2%], total nnz {nnz}",
+            "engine": args.engine, "autotune": tune, "roofline": hbm,
             "batched_bf16": {"solves_per_s": len(Ps) / t_batch, "wall_s": t_batch, "p50_ms": pct(lat, 50),
                              "p99_ms": pct(lat, 99), "status": status,
                              "iters_p50": pct([i["iters"] for i in infos], 50),
                              "iters_max": max(i["iters"] for i in infos),
+                             "admm_iters_total": sum(i["iters"] for i in infos),
+                             "device_s": {"sum": 1e-9 * sum(i["device_ns"] for i in infos),
+                                          "max": 1e-9 * max(i["device_ns"] for i in infos),
+                                          "p50": 1e-9 * pct([i["device_ns"] for i in infos], 50),
+                                          "longest": [{"m": sizes[k][0], "density": round(sizes[k][2], 4),
+                                                       "iters": infos[k]["iters"],
+                                                       "s": 1e-9 * infos[k]["device_ns"]}
+                                                      for k in sorted(range(len(infos)),
+                                                                      key=lambda k: -infos[k]["device_ns"])[:5]]},
                              "gpu_launches": sum(i["kernel_launches"] for i in infos),
                              "fp64_max_residual_sampled": res16},
-            "single_fp32": {"solves_per_s": single_rate, "sample": len(idx), "wall_s": t_single,
+            "batched_fp32": {"solves_per_s": len(sizes) / t_batch32, "wall_s": t_batch32,
+                             "status": {k: sum(1 for i in infos32 if i["status_name"] == k)
+                                        for k in sorted({i["status_name"] for i in infos32})},
+                             "gpu_launches": sum(i["kernel_launches"] for i in infos32)},
+            "single_fp32": {"solves_per_s": single_rate, "sample": len(idx), "wall_s": t_single, "engine": "graph",
                             "status": single_status, "fp64_max_residual_sampled": res32},
             "batched_over_single": (len(Ps) / t_batch) / single_rate,
             "csr_roofline": {st_: csr_roofline(B, ctx, torch, storage=st_) for st_ in ("fp32", "bf16")},
@@ -400,7 +441,7 @@ def serve_trace(args, rng):
 def run_serve(args, B, ctx, torch):
     rng = np.random.default_rng(synth.BASE_SEED + 77)
     reqs = serve_trace(args, rng)
-    st = B.settings(eps=1e-4, max_iters=args.lp_max_iters)
+    st = B.settings(eps=1e-4, max_iters=args.lp_max_iters, engine=args.engine)
     Ps = [B.cone_problem_create(ctx, p) for _, p in reqs]
     srv = B.Server(ctx, int(args.budget_gb * (1 << 30)), args.slots)
     torch.cuda.synchronize()
@@ -430,6 +471,7 @@ def run_serve(args, B, ctx, torch):
                          "n in [1e3,1e5], BF16 lasso m in [1e3,5e3], sparse LP m in [1e3,2e4] (1%)"),
             "offered_rate": args.rate, "slots": args.slots, "budget_gb": args.budget_gb,
             "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99), "wall_s": t_all, "status": status,
+            "engine": args.engine, "gpu_launches": sum(r[0]["kernel_launches"] for r in results),
             "alone_equals_mix_bitwise": same}
 
 
@@ -485,7 +527,8 @@ def main():
     yo = torch.empty(m, dtype=torch.float64, device=dev)
     so = torch.empty(m, dtype=torch.float64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    st = B.settings(max_iters=args.iters_per_step, eps=1e-4, host_loop=1 if args.host_loop else 0)
+    st = B.settings(max_iters=args.iters_per_step, eps=1e-4, host_loop=1 if args.host_loop else 0,
+                    engine="graph" if args.host_loop else args.engine)
 
     def step():
         return B.solve(P, st, x=xo, y=yo, s=so)[0]
@@ -560,6 +603,29 @@ def main():
                 "per_launch_ms": {"forward": 1e3 * t_fwd, "adjoint": 1e3 * t_adj},
                 "flops_per_launch": {"forward": flops_fwd, "adjoint": flops_adj}}
 
+    team = all(i["kernel_launches"] == 1 for i in infos)
+    if team:
+        # the whole solve is one launch of the team kernel, which runs this
+        # problem on one CTA (one SM): its convolution flops per launch
+        # (forward + adjoint passes: rhs, CG steps, checks, refreshes) over
+        # the launch time, against one SM's FP32 rate
+        fl = 0.0
+        for i in infos:
+            passes_adj = i["iters"] + i["cg_iters_total"] + i["checks"] + i["iters"] // 50
+            passes_fwd = i["cg_iters_total"] + i["checks"] + i["iters"] // 50
+            fl += passes_fwd * flops_fwd + passes_adj * flops_adj
+        t_launch = ms / 1e3
+        sm_peak = FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+        roofline = {"bound": "alu", "kernel": "k_team (one-CTA team)", "achieved": fl / t_launch / 1e12,
+                    "peak": sm_peak, "unit": "TFLOP/s", "frac": fl / t_launch / 1e12 / sm_peak, "traffic": None,
+                    "peak_source": f"derived: 1 SM (the problem's team) x {FP32_LANES_PER_SM} FP32 lanes x 2 flop "
+                                   f"x {sm_max:.0f} MHz",
+                    "note": "latency-bound: every vector (12 KB) stays on chip and the iteration is a chain of "
+                            "CTA barriers; the other SMs are free for other problems",
+                    "launch_ms": 1e3 * t_launch / len(infos),
+                    "flops_per_launch": fl / len(infos),
+                    "conv_kernel_alone": roofline}
+
     # ---- end to end through the C ABI with host buffers
     e2e = None
     if not args.no_e2e:
@@ -590,7 +656,7 @@ def main():
     # ---- one-off time to 1e-4
     ttc = None
     if args.ttc_max_iters > 0:
-        st2 = B.settings(max_iters=args.ttc_max_iters, eps=1e-4)
+        st2 = B.settings(max_iters=args.ttc_max_iters, eps=1e-4, engine=st.engine)
         e0.record(stream)
         info = B.solve(P, st2, x=xo, y=yo, s=so)[0]
         e1.record(stream)
@@ -612,6 +678,7 @@ def main():
                                    "eps 1e-4 checked every 10 iterations",
                            "l2": "flushed between steps (256 MB write)",
                            "precision": "f32 vectors and operator, f64 reductions/norms/tau/kappa",
+                           "engine": ("team (one persistent launch per solve)" if team else "graph (one CUDA graph per solve)"),
                            "parallelism": f"replicas x{world}"},
                 "iters_per_step": it_total / max(args.steps * world, 1),
                 "cg_per_iter": sum(i["cg_iters_total"] for i in infos) / max(iters, 1),

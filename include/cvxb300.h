@@ -128,7 +128,8 @@ typedef struct {
 typedef enum {
   CF_ENGINE_AUTO = 0,  /* team engine when the problem is supported and one
                           operator pass is at most the schedule's
-                          auto_max_bytes; graph engine otherwise */
+                          auto_max_bytes (batch_max_bytes inside
+                          solve_batch); graph engine otherwise */
   CF_ENGINE_GRAPH = 1, /* always the graph engine */
   CF_ENGINE_TEAM = 2   /* always the team engine (CF_E_INVALID if the
                           problem is not supported) */
@@ -140,13 +141,18 @@ typedef enum {
 typedef struct {
   int32_t cluster;         /* CTAs per cluster team: 1, 2, 4 or 8 (4) */
   int32_t threads;         /* threads per CTA: 256, 512 or 1024 (512) */
-  int32_t csr_nnz_per_lane;/* CSR rows get 2^k lanes (1..32), the power of two
-                              nearest avg nnz per row / this (4) */
+  int32_t csr_nnz_per_lane;/* CSR rows get the fewest lanes (a power of two,
+                              1..32) that hold the average row at this many
+                              nonzeros per lane (8) */
   int32_t reserved;
   double team_bytes;       /* problems whose operator pass reads at least this
                               many bytes run on a whole cluster team; smaller
-                              ones on one CTA (4e6) */
-  double auto_max_bytes;   /* CF_ENGINE_AUTO limit (48e6) */
+                              ones on one CTA (512e3) */
+  double auto_max_bytes;   /* CF_ENGINE_AUTO limit for single and served solves
+                              (4e6: above it one problem fills the GPU's
+                              kernels and the graph engine is faster) */
+  double batch_max_bytes;  /* CF_ENGINE_AUTO limit inside solve_batch (48e6: the
+                              batch's other problems keep the SMs busy) */
 } cf_schedule;
 
 typedef struct {
@@ -163,6 +169,8 @@ typedef struct {
                               the setup's GPU time when it ran) */
   int64_t kernel_launches; /* kernels this call ran on the GPU */
   int64_t queue_ns;        /* serving: time from serve_submit to launch */
+  int64_t device_ns;       /* team engine: device time of this problem's
+                              solve inside its launch (0 on the graph engine) */
 } cf_info;
 
 /* Fill *s with the defaults listed above. */

@@ -51,7 +51,8 @@ ENGINE = {"auto": CF_ENGINE_AUTO, "graph": CF_ENGINE_GRAPH, "team": CF_ENGINE_TE
 
 class cf_schedule(C.Structure):
     _fields_ = [("cluster", C.c_int32), ("threads", C.c_int32), ("csr_nnz_per_lane", C.c_int32),
-                ("reserved", C.c_int32), ("team_bytes", C.c_double), ("auto_max_bytes", C.c_double)]
+                ("reserved", C.c_int32), ("team_bytes", C.c_double), ("auto_max_bytes", C.c_double),
+                ("batch_max_bytes", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -73,7 +74,7 @@ class cf_info(C.Structure):
                 ("pri_res", C.c_double), ("dual_res", C.c_double), ("gap", C.c_double),
                 ("pobj", C.c_double), ("dobj", C.c_double), ("tau", C.c_double),
                 ("kappa", C.c_double), ("setup_ns", C.c_int64), ("solve_ns", C.c_int64),
-                ("kernel_launches", C.c_int64), ("queue_ns", C.c_int64)]
+                ("kernel_launches", C.c_int64), ("queue_ns", C.c_int64), ("device_ns", C.c_int64)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}

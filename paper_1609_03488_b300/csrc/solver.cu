@@ -1212,6 +1212,7 @@ cf_err solve_finish(cf_problem* P, cf_info* info) {
     info->solve_ns = t1 - P->t_launch;
     if (P->last_engine == CF_ENGINE_TEAM) {
       info->kernel_launches = P->team_launches;  // the whole solve is one persistent launch
+      info->device_ns = c.t_end - c.t_start;
     } else {
       int64_t kl = P->kc.top + (int64_t)c.k * P->kc.body + c.cg_total * P->kc.cg +
                    (int64_t)c.checks * P->kc.check + (int64_t)c.refreshes * P->kc.refresh;
@@ -1484,7 +1485,7 @@ cf_err solve_batch(cf_problem* const* probs, int32_t count, const cf_settings* s
     cf_problem* P = probs[i];
     int engine = CF_ENGINE_GRAPH;
     cudaSetDevice(P->device);
-    cf_err r = pick_engine(P, &sv, &engine);
+    cf_err r = pick_engine(P, &sv, &engine, /*in_batch=*/true);
     if (r == CF_OK && engine == CF_ENGINE_TEAM) {
       r = ensure_state(P);
       if (r == CF_OK) {

@@ -29,6 +29,7 @@ struct Ctl {
   // loop decisions, also set as graph conditions inside a graph
   int cg_go, do_check, do_refresh, outer_go;
   unsigned int red_count;
+  long long t_start, t_end;  // team engine: device clock (ns) at the solve's start and end
 };
 
 struct KernelCounts {
@@ -98,7 +99,7 @@ bool settings_valid(const cf_settings* st, std::string* why);
 void write_settings(cf_problem* p, const cf_settings* st, bool warm);
 // Engine a solve of p with st runs on (CF_ENGINE_GRAPH or CF_ENGINE_TEAM), or
 // CF_E_INVALID when st asks for the team engine and p is not supported.
-cf_err pick_engine(cf_problem* p, const cf_settings* st, int* engine);
+cf_err pick_engine(cf_problem* p, const cf_settings* st, int* engine, bool in_batch = false);
 namespace team {
 // Flattens p's operator (at problem creation) and uploads the term lists.
 cf_err plan_problem(cf_problem* p);

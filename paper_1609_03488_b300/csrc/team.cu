@@ -16,12 +16,15 @@
 // order, the same map for every vector, so a thread rereads only what it
 // wrote.  Operator terms partition their outputs otherwise (rows to lane
 // groups, tiles to CTAs); a team barrier separates them from the vector
-// phases.  Vectors written in the solve are read with L2-only loads
-// (ld.global.cg): the CTA that wrote them may sit on another SM.
+// phases.
 //
-// Reductions are deterministic: compensated float32 per thread, float64
-// across the CTA, then every CTA of the team adds the CTAs' partials in rank
-// order, so all CTAs hold the same total and take the same loop decisions.
+// Reductions are deterministic: compensated float32 per thread, double-float
+// across a warp, float64 across the warps (one warp) and across the CTAs of
+// the team in rank order, so all CTAs hold the same totals and take the same
+// loop decisions.  The scalar recurrences (CG step sizes, tau, kappa,
+// stopping tests) run once per CTA on thread 0; float64 is never spread over
+// every thread, since one SM's float64 rate is a small fraction of its
+// float32 rate.
 // Every loop is bounded by counters (max_iters, the CG caps, the queues); the
 // kernel has no spin-waits.
 #include <cooperative_groups.h>
@@ -65,11 +68,26 @@ struct Team {
   int TT;    // threads in the team
 };
 
+// Scalar state of a solve.  Thread 0 of every CTA of the team updates it from
+// the team's sums (all CTAs hold the same sums, so they hold the same state);
+// the other threads read it after the barrier that ends each sum.
+struct __align__(16) Scal {
+  double tau, kappa, hg, rr, tol2, pri, dual, gap, cx, by, sx, sy, ss;
+  long long cg_total;
+  int k, checks, refreshes, status, stop, chk, ref, go;
+  int cg_it, cg_guard, cg_cont, cg_cap, cg_cap2, cg_fixed, setup_iters;
+  float alpha_f, beta_f, ut_f, tau_f;
+  int seg_mode[kMaxSeg];       // 0 keep, 1 zero, 2 scale onto the boundary
+  float seg_head[kMaxSeg];     // projected head value (mode 2)
+  float seg_scale[kMaxSeg];    // tail scale (mode 2)
+};
+
 struct __align__(16) Shared {
   Prob P;              // the problem being solved
-  double bs[8][32];    // block-sum scratch, one column per warp
+  Scal sc;             // its scalar state
   double part[2][8];   // this CTA's partials, double-buffered across sums
-  double res[8];       // team totals
+  float bh[8][32];     // block-sum scratch (double-float), one column per warp
+  float bl[8][32];
   int item;            // work-queue slot taken by the team's rank 0
 };
 
@@ -80,10 +98,10 @@ __device__ __forceinline__ void tsync(const Team& tm) {
     __syncthreads();
 }
 
-__device__ __forceinline__ float4 cg4(const float* p, int64_t v) {
-  return __ldcg(reinterpret_cast<const float4*>(p) + v);
-}
-__device__ __forceinline__ float cg1(const float* p, int64_t i) { return __ldcg(p + i); }
+// Vectors written during the solve are read with ordinary (L1-cached)
+// loads: a barrier of the team (CTA barrier, or the cluster barrier's
+// release/acquire) orders every write before it with every read after it.
+__device__ __forceinline__ float4 ld4v(const float* p, int64_t v) { return reinterpret_cast<const float4*>(p)[v]; }
 
 #define TV4(v, n) for (int64_t v = tm.tt; v < ((n) >> 2); v += tm.TT)
 #define TTAIL(i, n) for (int64_t i = ((n) & ~(int64_t)3) + tm.tt; i < (n); i += tm.TT)
@@ -100,42 +118,72 @@ __device__ __forceinline__ void each(const Team& tm, int64_t n, F&& f) {
   TTAIL(i, n) f(i);
 }
 
-// Team-wide deterministic sum of NV doubles; every thread receives the totals.
-template <int NV>
-__device__ void team_sum(const Team& tm, Shared& sh, int& ph, double (&v)[NV]) {
+// (hi, lo) + (hi2, lo2) in double-float: TwoSum of the heads, then the
+// error and the tails, renormalised.
+__device__ __forceinline__ void df_add(float& hi, float& lo, float hi2, float lo2) {
+  const float s = __fadd_rn(hi, hi2);
+  const float bb = __fsub_rn(s, hi);
+  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(hi2, bb));
+  const float t = __fadd_rn(__fadd_rn(lo, lo2), e);
+  hi = __fadd_rn(s, t);
+  lo = __fsub_rn(t, __fsub_rn(hi, s));
+}
+
+// Team-wide deterministic sum of NV compensated per-thread sums: double-float
+// across each warp (float shuffles), float64 across the warps of a CTA (warp
+// 0 only) and across the CTAs of the team (every CTA adds the partials in
+// rank order).  Then thread 0 of each CTA runs fin(totals), which updates
+// the scalar state, and a barrier makes it visible to the CTA.
+template <int NV, class F>
+__device__ void team_sum(const Team& tm, Shared& sh, int& ph, Acc2 (&a)[NV], F&& fin) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
   for (int j = 0; j < NV; ++j) {
-    double t = v[j];
+    float hi = a[j].hi, lo = a[j].lo;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if (lane == 0) sh.bs[j][wid] = t;
+    for (int o = 16; o > 0; o >>= 1) {
+      const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+      const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+      df_add(hi, lo, h2, l2);
+    }
+    if (lane == 0) {
+      sh.bh[j][wid] = hi;
+      sh.bl[j][wid] = lo;
+    }
   }
   __syncthreads();
   if (wid == 0) {
+    double tv[NV];
 #pragma unroll
     for (int j = 0; j < NV; ++j) {
-      double t = lane < nw ? sh.bs[j][lane] : 0.0;
+      double t = lane < nw ? (double)sh.bh[j][lane] + (double)sh.bl[j][lane] : 0.0;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-      if (lane == 0) sh.part[ph][j] = t;
+      tv[j] = t;  // lane 0's value is the CTA's sum
+    }
+    if (tm.C > 1) {
+      if (lane == 0) {
+#pragma unroll
+        for (int j = 0; j < NV; ++j) sh.part[ph][j] = tv[j];
+      }
+    } else if (lane == 0) {
+      fin(tv);
     }
   }
   if (tm.C > 1) {
     cgr::cluster_group cl = cgr::this_cluster();
     cl.sync();
-    if (threadIdx.x < NV) {
-      double s = 0.0;
-      for (int r = 0; r < tm.C; ++r) s += *cl.map_shared_rank(&sh.part[ph][threadIdx.x], r);
-      sh.res[threadIdx.x] = s;
+    if (wid == 0) {
+      double tot = 0.0;
+      if (lane < NV)
+        for (int r = 0; r < tm.C; ++r) tot += *cl.map_shared_rank(&sh.part[ph][lane], r);
+      double tv[NV];
+#pragma unroll
+      for (int j = 0; j < NV; ++j) tv[j] = __shfl_sync(0xffffffffu, tot, j);
+      if (lane == 0) fin(tv);
     }
-  } else {
-    __syncthreads();
-    if (threadIdx.x < NV) sh.res[threadIdx.x] = sh.part[ph][threadIdx.x];
   }
   __syncthreads();
-#pragma unroll
-  for (int j = 0; j < NV; ++j) v[j] = sh.res[j];
   ph ^= 1;
 }
 
@@ -143,9 +191,9 @@ __device__ void team_sum(const Team& tm, Shared& sh, int& ph, double (&v)[NV]) {
 __device__ void term_diag(const Team& tm, const Term& t, const float* x, float* y) {
   const float* d = (const float*)t.a;
   for (int64_t i = tm.tt; i < t.rows; i += tm.TT) {
-    const float xv = cg1(x, t.xo + i);
+    const float xv = x[t.xo + i];
     float* yp = y + t.yo + i;
-    *yp = fmaf(t.alpha, d ? __ldg(d + i) * xv : xv, t.acc ? __ldcg(yp) : 0.f);
+    *yp = fmaf(t.alpha, d ? __ldg(d + i) * xv : xv, t.acc ? *yp : 0.f);
   }
 }
 
@@ -154,43 +202,53 @@ __device__ __forceinline__ float tval(const void* __restrict__ val, int32_t k) {
   return BF16 ? __bfloat162float(__ldg(((const __nv_bfloat16*)val) + k)) : __ldg(((const float*)val) + k);
 }
 
-// Rows to groups of L lanes (L a power of two); each group walks its row with
-// four gathers in flight and adds across its lanes by shuffles.
-template <bool BF16>
+// Rows to groups of L lanes (L a power of two); each lane issues the index
+// and value loads of U entries before it uses any, then gathers x
+// (L1-resident) and adds across its group by shuffles.  The row pointers of a
+// warp's next rows are loaded while it works on the current ones.
+template <bool BF16, int U>
 __device__ void term_csr(const Team& tm, const Term& t, const float* x, float* y, int L) {
   const int lane = threadIdx.x & 31;
   const int rpw = 32 / L;
   const int sub = lane / L, l = lane & (L - 1);
   const int64_t warp = tm.tt >> 5, nwarps = tm.TT >> 5;
+  const int64_t step = nwarps * rpw;
   const int32_t* __restrict__ rp = t.rowptr;
   const int32_t* __restrict__ col = t.col;
   const void* __restrict__ val = t.a;
   const float* xb = x + t.xo;
-  for (int64_t rb = warp * rpw; rb < t.rows; rb += nwarps * rpw) {
-    const int64_t r = rb + sub;
-    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-    if (r < t.rows) {
-      const int32_t b = __ldg(rp + r), e = __ldg(rp + r + 1);
-      int32_t k = b + l;
-      for (; k + 3 * L < e; k += 4 * L) {
-        const int32_t c0 = __ldg(col + k), c1 = __ldg(col + k + L), c2 = __ldg(col + k + 2 * L),
-                      c3 = __ldg(col + k + 3 * L);
-        const float v0 = tval<BF16>(val, k), v1 = tval<BF16>(val, k + L);
-        const float v2 = tval<BF16>(val, k + 2 * L), v3 = tval<BF16>(val, k + 3 * L);
-        s0 = fmaf(v0, cg1(xb, c0), s0);
-        s1 = fmaf(v1, cg1(xb, c1), s1);
-        s2 = fmaf(v2, cg1(xb, c2), s2);
-        s3 = fmaf(v3, cg1(xb, c3), s3);
+  int64_t r = warp * rpw + sub;
+  int32_t b = r < t.rows ? __ldg(rp + r) : 0, e = r < t.rows ? __ldg(rp + r + 1) : 0;
+  for (int64_t rb = warp * rpw; rb < t.rows; rb += step) {
+    const int64_t rn = r + step;
+    const int32_t nb = rn < t.rows ? __ldg(rp + rn) : 0, ne = rn < t.rows ? __ldg(rp + rn + 1) : 0;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int32_t k = b + l; k < e; k += U * L) {
+      int32_t c[U];
+      float v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int32_t kk = k + u * L;
+        const bool ok = kk < e;
+        c[u] = ok ? __ldg(col + kk) : -1;
+        v[u] = ok ? tval<BF16>(val, kk) : 0.f;
       }
-      for (; k < e; k += L) s0 = fmaf(tval<BF16>(val, k), cg1(xb, __ldg(col + k)), s0);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const float xv = c[u] >= 0 ? xb[c[u]] : 0.f;
+        acc[u & 3] = fmaf(v[u], xv, acc[u & 3]);
+      }
     }
-    float s = (s0 + s1) + (s2 + s3);
+    float s = (acc[0] + acc[1]) + (acc[2] + acc[3]);
     for (int o = L >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (l == 0 && r < t.rows) {
       const float out = t.alpha * s;
       float* yp = y + t.yo + r;
-      *yp = t.acc ? __ldcg(yp) + out : out;
+      *yp = t.acc ? *yp + out : out;
     }
+    r = rn;
+    b = nb;
+    e = ne;
   }
 }
 
@@ -204,7 +262,7 @@ __device__ void term_dense_n(const Team& tm, const Term& t, const float* x, floa
   const int64_t n = t.cols, m = t.rows, lda = t.lda;
   const int64_t npad = (n + 15) & ~(int64_t)15;
   __syncthreads();  // earlier users of the shared buffer are done
-  for (int64_t i = threadIdx.x; i < npad; i += blockDim.x) dsm[i] = i < n ? cg1(x, t.xo + i) : 0.f;
+  for (int64_t i = threadIdx.x; i < npad; i += blockDim.x) dsm[i] = i < n ? x[t.xo + i] : 0.f;
   __syncthreads();
   const TS* A = (const TS*)t.a;
   const int lane = threadIdx.x & 31;
@@ -250,7 +308,7 @@ __device__ void term_dense_n(const Team& tm, const Term& t, const float* x, floa
       const int64_t r = r0 + lane;
       float out = t.alpha * (t.scale ? __ldg(t.scale + r) * s : s);
       float* yp = y + t.yo + r;
-      *yp = t.acc ? __ldcg(yp) + out : out;
+      *yp = t.acc ? *yp + out : out;
     }
   }
 }
@@ -285,7 +343,7 @@ __device__ void term_dense_t(const Team& tm, const Term& t, const float* x, floa
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           u[j] = __ldg(reinterpret_cast<const uint4*>(A + (i + j) * lda + col0));
-          xi[j] = cg1(x, t.xo + i + j);
+          xi[j] = x[t.xo + i + j];
           if (t.scale) xi[j] *= __ldg(t.scale + i + j);
         }
 #pragma unroll
@@ -298,7 +356,7 @@ __device__ void term_dense_t(const Team& tm, const Term& t, const float* x, floa
       }
       for (; i < r1; ++i) {
         const uint4 u = __ldg(reinterpret_cast<const uint4*>(A + i * lda + col0));
-        float xi = cg1(x, t.xo + i);
+        float xi = x[t.xo + i];
         if (t.scale) xi *= __ldg(t.scale + i);
         float f[V];
         Vec<TS>::unpack(u, f);
@@ -312,7 +370,7 @@ __device__ void term_dense_t(const Team& tm, const Term& t, const float* x, floa
           if (R == 1) {
             float* yp = y + t.yo + j;
             const float out = t.alpha * acc[q];
-            *yp = t.acc ? __ldcg(yp) + out : out;
+            *yp = t.acc ? *yp + out : out;
           } else {
             scratch[g * nout + j] = acc[q];
           }
@@ -324,21 +382,25 @@ __device__ void term_dense_t(const Team& tm, const Term& t, const float* x, floa
     tsync(tm);
     for (int64_t j = tm.tt; j < nout; j += tm.TT) {
       float s = 0.f;
-      for (int64_t g = 0; g < R; ++g) s += cg1(scratch, g * nout + j);
+      for (int64_t g = 0; g < R; ++g) s += scratch[g * nout + j];
       float* yp = y + t.yo + j;
       const float out = t.alpha * s;
-      *yp = t.acc ? __ldcg(yp) + out : out;
+      *yp = t.acc ? *yp + out : out;
     }
   }
 }
 
 // out[i] = sum_{j < Lp} wrev[j] x[i + shift - (Lp - 1) + j] (x = 0 outside
 // [0, cols)): output tiles go to the team's CTAs in turn; each tile's input
-// window and the taps sit in shared memory.
+// window and the taps sit in shared memory, and a thread computes kConvR
+// consecutive outputs from a register window of 2 kConvR inputs, so that
+// every 8 taps cost 6 shared-memory loads for 64 multiply-adds.
+constexpr int kConvR = 8;
+
 __device__ void term_conv(const Team& tm, const Term& t, const float* x, float* y, float* dsm) {
   const int64_t n_out = t.rows, n_in = t.cols, Lp = t.Lp;
   float* w_s = dsm;
-  float* in_s = dsm + Lp;
+  float* in_s = dsm + Lp;  // 64-byte aligned: Lp is a multiple of 16
   __syncthreads();  // earlier users of the shared buffer are done
   for (int64_t j = threadIdx.x; j < Lp; j += blockDim.x) w_s[j] = __ldg((const float*)t.a + j);
   const int64_t ntile = (n_out + kConvTile - 1) / kConvTile;
@@ -347,30 +409,56 @@ __device__ void term_conv(const Team& tm, const Term& t, const float* x, float* 
     const int64_t cnt = (n_out - o0) < kConvTile ? (n_out - o0) : (int64_t)kConvTile;
     const int64_t base = o0 + t.shift - (Lp - 1);
     __syncthreads();
-    for (int64_t j = threadIdx.x; j < cnt + Lp - 1; j += blockDim.x) {
+    // window [0, cnt + Lp + kConvR): the last register window of the last
+    // thread reaches index (cnt - 1) + Lp + kConvR - 2 at most
+    for (int64_t j = threadIdx.x; j < cnt + Lp + kConvR; j += blockDim.x) {
       const int64_t g = base + j;
-      in_s[j] = (g >= 0 && g < n_in) ? cg1(x, t.xo + g) : 0.f;
+      in_s[j] = (g >= 0 && g < n_in) ? x[t.xo + g] : 0.f;
     }
     __syncthreads();
-    for (int64_t o = threadIdx.x; o < cnt; o += blockDim.x) {
-      float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-      const float* win = in_s + o;
-      for (int64_t j = 0; j < Lp; j += 4) {  // Lp is a multiple of 16
-        s0 = fmaf(w_s[j], win[j], s0);
-        s1 = fmaf(w_s[j + 1], win[j + 1], s1);
-        s2 = fmaf(w_s[j + 2], win[j + 2], s2);
-        s3 = fmaf(w_s[j + 3], win[j + 3], s3);
+    const float4* w4 = reinterpret_cast<const float4*>(w_s);
+    for (int64_t ob = (int64_t)threadIdx.x * kConvR; ob < cnt; ob += (int64_t)blockDim.x * kConvR) {
+      float acc[kConvR];
+#pragma unroll
+      for (int r = 0; r < kConvR; ++r) acc[r] = 0.f;
+      const float4* x4 = reinterpret_cast<const float4*>(in_s + ob);
+      for (int64_t j = 0; j < Lp; j += 8) {
+        float xw[16], w[8];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float4 v = x4[(j >> 2) + q];
+          xw[4 * q] = v.x; xw[4 * q + 1] = v.y; xw[4 * q + 2] = v.z; xw[4 * q + 3] = v.w;
+        }
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const float4 v = w4[(j >> 2) + q];
+          w[4 * q] = v.x; w[4 * q + 1] = v.y; w[4 * q + 2] = v.z; w[4 * q + 3] = v.w;
+        }
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj)
+#pragma unroll
+          for (int r = 0; r < kConvR; ++r) acc[r] = fmaf(w[jj], xw[r + jj], acc[r]);
       }
-      const float out = t.alpha * ((s0 + s1) + (s2 + s3));
-      float* yp = y + t.yo + o0 + o;
-      *yp = t.acc ? __ldcg(yp) + out : out;
+#pragma unroll
+      for (int r = 0; r < kConvR; ++r) {
+        if (ob + r < cnt) {
+          const float out = t.alpha * acc[r];
+          float* yp = y + t.yo + o0 + ob + r;
+          *yp = t.acc ? *yp + out : out;
+        }
+      }
     }
   }
 }
 
-// y = the flattened operator applied to x (terms in order).
-__device__ void apply(const Team& tm, const Term* terms, int nt, const float* x, float* y,
-                      float* scratch, float* dsm, int lanes) {
+// y = the flattened operator applied to x (terms in order).  Compiled once
+// per CTA size (not inlined at each call) so that the term loops get
+// registers of their own; CTAs of 1024 threads (64 registers a thread) keep
+// 8 CSR entries a lane in flight, smaller CTAs 16.
+template <int MaxT>
+__device__ __noinline__ void apply(const Team& tm, const Term* terms, int nt, const float* x, float* y,
+                                   float* scratch, float* dsm, int lanes) {
+  constexpr int U = MaxT >= 1024 ? 8 : 16;
   for (int k = 0; k < nt; ++k) {
     const Term& t = terms[k];
     if (t.sync) tsync(tm);
@@ -383,9 +471,9 @@ __device__ void apply(const Team& tm, const Term* terms, int nt, const float* x,
         break;
       case T_CSR:
         if (t.prec == CF_BF16)
-          term_csr<true>(tm, t, x, y, lanes);
+          term_csr<true, U>(tm, t, x, y, lanes);
         else
-          term_csr<false>(tm, t, x, y, lanes);
+          term_csr<false, U>(tm, t, x, y, lanes);
         break;
       case T_DENSE_N:
         if (t.prec == CF_BF16)
@@ -411,139 +499,153 @@ __device__ void apply(const Team& tm, const Term* terms, int nt, const float* x,
 }
 
 // ------------------------------------------------------------ CG (Section 4.2)
-// CG on (lam I + A^T A) z = rhs from the z held (gz = G z carried, fresh
-// start not needed: setup starts at z = 0, iterations warm-start with the
-// carried G z).  mode CG_ITER also carries az = A z.  Returns the steps run.
-__device__ int cg_run(const Team& tm, Shared& sh, int& ph, float* dsm, int mode, float* z, int k_outer) {
+// CG on (I + A^T A) z = rhs from the z held, with gz = G z carried (setup
+// starts at z = 0; iterations warm-start with the carried G z).  mode
+// CG_ITER also carries az = A z.  k_outer: the ADMM iteration (tolerance).
+template <int MaxT>
+__device__ __noinline__ void cg_run(const Team& tm, Shared& sh, int& ph, float* dsm, int mode, float* z,
+                                    int k_outer) {
   const Prob& P = sh.P;
-  const Settings& st = P.st;
   const int64_t n = P.n, m = P.m;
-  const float lamf = 1.f;
   float *r = P.r, *p = P.p, *q = P.q, *gz = P.gz, *az = P.az, *t = P.t;
   const float* rhs = P.rhs;
-  Acc2 a0, a1;
-  TV4(v, n) {
-    const float4 g = cg4(gz, v), rh = cg4(rhs, v);
-    float4 rv;
+  {
+    Acc2 a[2];
+    TV4(v, n) {
+      const float4 g = ld4v(gz, v), rh = ld4v(rhs, v);
+      float4 rv;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      el(rv, k) = elc(rh, k) - elc(g, k);
-      a0.add_prod(elc(rv, k), elc(rv, k));
-      a1.add_prod(elc(rh, k), elc(rh, k));
+      for (int k = 0; k < 4; ++k) {
+        el(rv, k) = elc(rh, k) - elc(g, k);
+        a[0].add_prod(elc(rv, k), elc(rv, k));
+        a[1].add_prod(elc(rh, k), elc(rh, k));
+      }
+      st4(r, v, rv);
+      st4(p, v, rv);
     }
-    st4(r, v, rv);
-    st4(p, v, rv);
+    TTAIL(i, n) {
+      const float rh = rhs[i];
+      const float ri = rh - gz[i];
+      r[i] = ri;
+      p[i] = ri;
+      a[0].add_prod(ri, ri);
+      a[1].add_prod(rh, rh);
+    }
+    team_sum<2>(tm, sh, ph, a, [&](const double* tv) {
+      Scal& c = sh.sc;
+      const Settings& st = sh.P.st;
+      const double nrhs = sqrt(tv[1]);
+      double tol;
+      if (mode == CG_SETUP) {
+        tol = st.setup_tol * nrhs;
+        c.cg_cap = st.setup_cg_max;
+        c.cg_fixed = 0;
+      } else {
+        tol = st.cg_tol_rel * nrhs * (double)powf((float)k_outer + 1.0f, -(float)st.cg_tol_exp);
+        tol = fmax(tol, st.cg_tol_min);
+        c.cg_cap = st.cg_max;
+        c.cg_fixed = st.cg_fixed;
+      }
+      c.rr = tv[0];
+      c.tol2 = tol * tol;
+      c.cg_it = 0;
+      c.cg_guard = 0;
+      c.cg_cap2 = mode == CG_SETUP ? st.setup_cg_max : (st.cg_fixed > 0 ? st.cg_fixed : st.cg_max);
+      c.cg_cont = c.cg_fixed > 0 ? 1 : ((c.rr > c.tol2 && c.cg_cap > 0) ? 1 : 0);
+    });
   }
-  TTAIL(i, n) {
-    const float rh = cg1(rhs, i);
-    const float ri = rh - cg1(gz, i);
-    r[i] = ri;
-    p[i] = ri;
-    a0.add_prod(ri, ri);
-    a1.add_prod(rh, rh);
-  }
-  double v2[2] = {a0.value(), a1.value()};
-  team_sum<2>(tm, sh, ph, v2);
-  double rr = v2[0];
-  const double nrhs = sqrt(v2[1]);
-  double tol;
-  int cap, fixed;
-  if (mode == CG_SETUP) {
-    tol = st.setup_tol * nrhs;
-    cap = st.setup_cg_max;
-    fixed = 0;
-  } else {
-    tol = st.cg_tol_rel * nrhs * (double)powf((float)k_outer + 1.0f, -(float)st.cg_tol_exp);
-    tol = fmax(tol, st.cg_tol_min);
-    cap = st.cg_max;
-    fixed = st.cg_fixed;
-  }
-  const double tol2 = tol * tol;
-  const int cap2 = mode == CG_SETUP ? st.setup_cg_max : (fixed > 0 ? fixed : st.cg_max);
-  bool cont = fixed > 0 ? true : (rr > tol2 && cap > 0);
-  int it = 0, guard = 0;
+  bool cont = sh.sc.cg_cont != 0;
   while (cont) {
     // p (vector partition, followed by a sum or a barrier) -> t = A p -> q = A^T t
-    apply(tm, P.fwd, P.nfwd, p, t, P.scratch, dsm, P.lanes);
+    apply<MaxT>(tm, P.fwd, P.nfwd, p, t, P.scratch, dsm, P.lanes);
     tsync(tm);
-    apply(tm, P.adj, P.nadj, t, q, P.scratch, dsm, P.lanes);
+    apply<MaxT>(tm, P.adj, P.nadj, t, q, P.scratch, dsm, P.lanes);
     tsync(tm);
-    Acc2 b0;
-    TV4(v, n) {
-      const float4 pp = cg4(p, v);
-      float4 qq = cg4(q, v);
+    {
+      Acc2 b[1];
+      TV4(v, n) {
+        const float4 pp = ld4v(p, v);
+        float4 qq = ld4v(q, v);
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        el(qq, k) = el(qq, k) + lamf * elc(pp, k);
-        b0.add_prod(elc(pp, k), elc(qq, k));
+        for (int k = 0; k < 4; ++k) {
+          el(qq, k) = el(qq, k) + elc(pp, k);  // q += lam p, lam = 1
+          b[0].add_prod(elc(pp, k), elc(qq, k));
+        }
+        st4(q, v, qq);
       }
-      st4(q, v, qq);
+      TTAIL(i, n) {
+        const float pi = p[i];
+        const float qi = q[i] + pi;
+        q[i] = qi;
+        b[0].add_prod(pi, qi);
+      }
+      team_sum<1>(tm, sh, ph, b, [&](const double* tv) {
+        const double pq = tv[0];
+        sh.sc.alpha_f = (float)(pq > 0.0 ? sh.sc.rr / pq : 0.0);
+      });
     }
-    TTAIL(i, n) {
-      const float pi = cg1(p, i);
-      const float qi = cg1(q, i) + lamf * pi;
-      q[i] = qi;
-      b0.add_prod(pi, qi);
-    }
-    double v1[1] = {b0.value()};
-    team_sum<1>(tm, sh, ph, v1);
-    const double pq = v1[0];
-    const double alpha = pq > 0.0 ? rr / pq : 0.0;
-    const float a = (float)alpha;
-    Acc2 c0;
-    TV4(v, n) {
-      const float4 qq = cg4(q, v), pp = cg4(p, v);
-      float4 zz = cg4(z, v), gg = cg4(gz, v), rv = cg4(r, v);
+    const float a = sh.sc.alpha_f;
+    {
+      Acc2 c0[1];
+      TV4(v, n) {
+        const float4 qq = ld4v(q, v), pp = ld4v(p, v);
+        float4 zz = ld4v(z, v), gg = ld4v(gz, v), rv = ld4v(r, v);
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        el(zz, k) = fmaf(a, elc(pp, k), el(zz, k));
-        el(gg, k) = fmaf(a, elc(qq, k), el(gg, k));
-        el(rv, k) = fmaf(-a, elc(qq, k), el(rv, k));
-        c0.add_prod(elc(rv, k), elc(rv, k));
+        for (int k = 0; k < 4; ++k) {
+          el(zz, k) = fmaf(a, elc(pp, k), el(zz, k));
+          el(gg, k) = fmaf(a, elc(qq, k), el(gg, k));
+          el(rv, k) = fmaf(-a, elc(qq, k), el(rv, k));
+          c0[0].add_prod(elc(rv, k), elc(rv, k));
+        }
+        st4(z, v, zz);
+        st4(gz, v, gg);
+        st4(r, v, rv);
       }
-      st4(z, v, zz);
-      st4(gz, v, gg);
-      st4(r, v, rv);
-    }
-    TTAIL(i, n) {
-      const float qi = cg1(q, i);
-      z[i] = fmaf(a, cg1(p, i), cg1(z, i));
-      gz[i] = fmaf(a, qi, cg1(gz, i));
-      const float ri = fmaf(-a, qi, cg1(r, i));
-      r[i] = ri;
-      c0.add_prod(ri, ri);
-    }
-    if (mode == CG_ITER) {
-      TV4(v, m) {
-        const float4 tv = cg4(t, v);
-        float4 aa = cg4(az, v);
+      TTAIL(i, n) {
+        const float qi = q[i];
+        z[i] = fmaf(a, p[i], z[i]);
+        gz[i] = fmaf(a, qi, gz[i]);
+        const float ri = fmaf(-a, qi, r[i]);
+        r[i] = ri;
+        c0[0].add_prod(ri, ri);
+      }
+      if (mode == CG_ITER) {
+        TV4(v, m) {
+          const float4 tv = ld4v(t, v);
+          float4 aa = ld4v(az, v);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) el(aa, k) = fmaf(a, elc(tv, k), el(aa, k));
-        st4(az, v, aa);
+          for (int k = 0; k < 4; ++k) el(aa, k) = fmaf(a, elc(tv, k), el(aa, k));
+          st4(az, v, aa);
+        }
+        TTAIL(i, m) az[i] = fmaf(a, t[i], az[i]);
       }
-      TTAIL(i, m) az[i] = fmaf(a, cg1(t, i), cg1(az, i));
+      team_sum<1>(tm, sh, ph, c0, [&](const double* tv) {
+        Scal& c = sh.sc;
+        const double rr_new = tv[0];
+        c.beta_f = (float)(c.rr > 0.0 ? rr_new / c.rr : 0.0);
+        c.rr = rr_new;
+        ++c.cg_it;
+        if (mode == CG_SETUP)
+          ++c.setup_iters;
+        else
+          ++c.cg_total;
+        const bool more = c.cg_fixed > 0 ? (c.cg_it < c.cg_fixed) : (rr_new > c.tol2 && c.cg_it < c.cg_cap);
+        ++c.cg_guard;
+        c.cg_cont = (more && c.cg_guard < c.cg_cap2) ? 1 : 0;
+      });
     }
-    double v3[1] = {c0.value()};
-    team_sum<1>(tm, sh, ph, v3);
-    const double rr_new = v3[0];
-    const double beta = rr > 0.0 ? rr_new / rr : 0.0;
-    rr = rr_new;
-    ++it;
-    const bool more = fixed > 0 ? (it < fixed) : (rr_new > tol2 && it < cap);
-    const float b = (float)beta;
+    const float b = sh.sc.beta_f;
+    cont = sh.sc.cg_cont != 0;
     TV4(v, n) {
-      const float4 rv = cg4(r, v);
-      float4 pp = cg4(p, v);
+      const float4 rv = ld4v(r, v);
+      float4 pp = ld4v(p, v);
 #pragma unroll
       for (int k = 0; k < 4; ++k) el(pp, k) = fmaf(b, el(pp, k), elc(rv, k));
       st4(p, v, pp);
     }
-    TTAIL(i, n) p[i] = fmaf(b, cg1(p, i), cg1(r, i));
-    ++guard;
-    cont = more && guard < cap2;
+    TTAIL(i, n) p[i] = fmaf(b, p[i], r[i]);
     if (cont) tsync(tm);  // the next forward term reads p under its own partition
   }
-  return it;
 }
 
 // ------------------------------------------------------------ one solve
@@ -553,14 +655,34 @@ __device__ __forceinline__ int seg_of(const Prob& P, int64_t i) {
   return s;
 }
 
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+template <int MaxT>
 __device__ void solve_one(const Team& tm, Shared& sh, float* dsm) {
+  const unsigned long long t_start = gtimer();
   const Prob& P = sh.P;
   const Settings& st = P.st;
   const int64_t n = P.n, m = P.m, N = n + m + 1;
-  const double lam = 1.0;
   int ph = 0;
-  double hg = 0.0;
-  int setup_iters = 0;
+  const bool warm = st.warm != 0 && !P.tune;
+  if (threadIdx.x == 0) {
+    Scal& c = sh.sc;
+    c.cg_total = 0;
+    c.k = c.checks = c.refreshes = 0;
+    c.status = CF_MAX_ITERS;
+    c.stop = 0;
+    c.pri = c.dual = c.gap = INFINITY;
+    c.cx = c.by = 0.0;
+    c.setup_iters = 0;
+    c.hg = P.tune ? 0.0 : (P.do_setup ? 0.0 : P.ctl->hg);
+    c.tau = warm ? P.warm[n + m] : 1.0;
+    c.kappa = warm ? P.warm[N + n + m] : 1.0;
+  }
+  __syncthreads();
 
   // ---- setup: g = M^{-1} h, h^T g
   if (P.tune) {
@@ -573,29 +695,24 @@ __device__ void solve_one(const Team& tm, Shared& sh, float* dsm) {
       P.rhs[i] = __ldg(P.cf + i);
     });
     tsync(tm);
-    apply(tm, P.adj_m, P.nadj_m, P.bf, P.rhs, P.scratch, dsm, P.lanes);  // rhs = c - A^T b
+    apply<MaxT>(tm, P.adj_m, P.nadj_m, P.bf, P.rhs, P.scratch, dsm, P.lanes);  // rhs = c - A^T b
     tsync(tm);
-    setup_iters = cg_run(tm, sh, ph, dsm, CG_SETUP, P.gx, 0);
+    cg_run<MaxT>(tm, sh, ph, dsm, CG_SETUP, P.gx, 0);
     tsync(tm);
-    apply(tm, P.fwd, P.nfwd, P.gx, P.gy, P.scratch, dsm, P.lanes);  // A g_x
+    apply<MaxT>(tm, P.fwd, P.nfwd, P.gx, P.gy, P.scratch, dsm, P.lanes);  // A g_x
     tsync(tm);
-    Acc2 a;
+    Acc2 a[1];
     each(tm, m, [&](int64_t i) {
       const float bi = __ldg(P.bf + i);
-      const float gi = cg1(P.gy, i) + bi;
+      const float gi = P.gy[i] + bi;
       P.gy[i] = gi;
-      a.add_prod(bi, gi);
+      a[0].add_prod(bi, gi);
     });
-    each(tm, n, [&](int64_t i) { a.add_prod(__ldg(P.cf + i), cg1(P.gx, i)); });
-    double v[1] = {a.value()};
-    team_sum<1>(tm, sh, ph, v);
-    hg = v[0];
-  } else {
-    hg = __ldcg(&P.ctl->hg);
+    each(tm, n, [&](int64_t i) { a[0].add_prod(__ldg(P.cf + i), P.gx[i]); });
+    team_sum<1>(tm, sh, ph, a, [&](const double* tv) { sh.sc.hg = tv[0]; });
   }
 
   // ---- initial point u = v = (0, 0, 1) or the warm start
-  const bool warm = st.warm != 0 && !P.tune;
   each(tm, n, [&](int64_t i) {
     P.ux[i] = warm ? (float)P.warm[i] : 0.f;
     P.zx[i] = 0.f;
@@ -606,11 +723,6 @@ __device__ void solve_one(const Team& tm, Shared& sh, float* dsm) {
     P.vs[i] = warm ? (float)P.warm[N + n + i] : 0.f;
     P.az[i] = 0.f;
   });
-  double tau = warm ? P.warm[n + m] : 1.0;
-  double kappa = warm ? P.warm[N + n + m] : 1.0;
-  int k = 0, checks = 0, refreshes = 0, status = CF_MAX_ITERS;
-  long long cg_total = 0;
-  double pri = INFINITY, dual = INFINITY, gap = INFINITY, cx = 0.0, by = 0.0;
   const double al = st.alpha;
   const float af = (float)al, a1 = (float)(1.0 - al);
   const int64_t z = P.z, nl = P.z + P.l;
@@ -618,90 +730,106 @@ __device__ void solve_one(const Team& tm, Shared& sh, float* dsm) {
   for (int guard = 0; guard < st.max_iters; ++guard) {
     // ---- w = u + v; rhs = w_x - A^T w_y
     TV4(v, m) {
-      const float4 a = cg4(P.uy, v), b = cg4(P.vs, v);
+      const float4 a = ld4v(P.uy, v), b = ld4v(P.vs, v);
       st4(P.wy, v, make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w));
     }
-    TTAIL(i, m) P.wy[i] = cg1(P.uy, i) + cg1(P.vs, i);
-    TV4(v, n) st4(P.rhs, v, cg4(P.ux, v));
-    TTAIL(i, n) P.rhs[i] = cg1(P.ux, i);
-    const double w_tau = tau + kappa;
+    TTAIL(i, m) P.wy[i] = P.uy[i] + P.vs[i];
+    TV4(v, n) st4(P.rhs, v, ld4v(P.ux, v));
+    TTAIL(i, n) P.rhs[i] = P.ux[i];
     tsync(tm);
-    apply(tm, P.adj_m, P.nadj_m, P.wy, P.rhs, P.scratch, dsm, P.lanes);
+    apply<MaxT>(tm, P.adj_m, P.nadj_m, P.wy, P.rhs, P.scratch, dsm, P.lanes);
     tsync(tm);
     // ---- z_x by CG, warm-started at the previous z_x
-    cg_total += cg_run(tm, sh, ph, dsm, CG_ITER, P.zx, k);
-    // ---- z_y = w_y + A z_x (carried); u~_tau
-    double ut;
+    cg_run<MaxT>(tm, sh, ph, dsm, CG_ITER, P.zx, sh.sc.k);
+    // ---- z_y = w_y + A z_x (carried); u~_tau; then tau, kappa, the
+    // iteration counter and this iteration's decisions
     {
-      Acc2 a;
+      Acc2 a[1];
       TV4(v, m) {
-        const float4 aa = cg4(P.az, v), ww = cg4(P.wy, v), bb = __ldg(reinterpret_cast<const float4*>(P.bf) + v);
+        const float4 aa = ld4v(P.az, v), ww = ld4v(P.wy, v), bb = __ldg(reinterpret_cast<const float4*>(P.bf) + v);
         float4 zz;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           el(zz, j) = elc(aa, j) + elc(ww, j);
-          a.add_prod(elc(bb, j), elc(zz, j));
+          a[0].add_prod(elc(bb, j), elc(zz, j));
         }
         st4(P.zy, v, zz);
       }
       TTAIL(i, m) {
-        const float zi = cg1(P.az, i) + cg1(P.wy, i);
+        const float zi = P.az[i] + P.wy[i];
         P.zy[i] = zi;
-        a.add_prod(__ldg(P.bf + i), zi);
+        a[0].add_prod(__ldg(P.bf + i), zi);
       }
       TV4(v, n) {
-        const float4 cc = __ldg(reinterpret_cast<const float4*>(P.cf) + v), xx = cg4(P.zx, v);
+        const float4 cc = __ldg(reinterpret_cast<const float4*>(P.cf) + v), xx = ld4v(P.zx, v);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) a.add_prod(elc(cc, j), elc(xx, j));
+        for (int j = 0; j < 4; ++j) a[0].add_prod(elc(cc, j), elc(xx, j));
       }
-      TTAIL(i, n) a.add_prod(__ldg(P.cf + i), cg1(P.zx, i));
-      double v[1] = {a.value()};
-      team_sum<1>(tm, sh, ph, v);
-      ut = (w_tau + v[0]) / (1.0 + hg);
+      TTAIL(i, n) a[0].add_prod(__ldg(P.cf + i), P.zx[i]);
+      team_sum<1>(tm, sh, ph, a, [&](const double* tv) {
+        Scal& c = sh.sc;
+        const Settings& s = sh.P.st;
+        const double ut = (c.tau + c.kappa + tv[0]) / (1.0 + c.hg);  // w_tau = tau + kappa
+        c.ut_f = (float)ut;
+        const double uhat = s.alpha * ut + (1.0 - s.alpha) * c.tau;
+        const double pt = uhat - c.kappa;
+        const double tn = pt > 0.0 ? pt : 0.0;
+        c.tau = tn;
+        c.kappa = tn - pt;
+        c.tau_f = (float)tn;
+        const int k = ++c.k;
+        c.chk = ((k % s.check_interval == 0) || (k >= s.max_iters)) ? 1 : 0;
+        c.ref = ((k % 50 == 0) && (k < s.max_iters)) ? 1 : 0;
+        if (!isfinite(c.tau) || !isfinite(c.kappa)) {
+          c.status = CF_NUMERICAL;
+          c.stop = 1;
+        }
+        c.go = (!c.stop && k < s.max_iters) ? 1 : 0;
+      });
     }
-    const float utf = (float)ut;
+    const float utf = sh.sc.ut_f;
     // ---- second-order cones: head value and tail norm of each block
-    double sv[2 * kMaxSeg];
     if (P.nseg > 0) {
-      Acc2 acc[kMaxSeg];
-      double p0[kMaxSeg];
-#pragma unroll
-      for (int s = 0; s < kMaxSeg; ++s) p0[s] = 0.0;
+      Acc2 acc[2 * kMaxSeg];
       each(tm, m, [&](int64_t i) {
         if (i < nl) return;
-        const float pi = y_pre(af, a1, utf, cg1(P.zy, i), cg1(P.gy, i), cg1(P.uy, i), cg1(P.vs, i));
+        const float pi = y_pre(af, a1, utf, P.zy[i], P.gy[i], P.uy[i], P.vs[i]);
         const int s = seg_of(P, i);
 #pragma unroll
         for (int j = 0; j < kMaxSeg; ++j) {
           if (j == s) {
             if (i == P.seg_head[j])
-              p0[j] = (double)pi;
+              acc[2 * j].add(pi);
             else
-              acc[j].add_prod(pi, pi);
+              acc[2 * j + 1].add_prod(pi, pi);
           }
         }
       });
-#pragma unroll
-      for (int s = 0; s < kMaxSeg; ++s) {
-        sv[2 * s] = p0[s];
-        sv[2 * s + 1] = acc[s].value();
-      }
-      team_sum<2 * kMaxSeg>(tm, sh, ph, sv);
+      team_sum<2 * kMaxSeg>(tm, sh, ph, acc, [&](const double* tv) {
+        Scal& c = sh.sc;
+        for (int s = 0; s < sh.P.nseg; ++s) {
+          const double p0 = tv[2 * s], nrm = sqrt(tv[2 * s + 1]);
+          const double ah = 0.5 * (p0 + nrm);
+          c.seg_mode[s] = nrm <= p0 ? 0 : (nrm <= -p0 ? 1 : 2);
+          c.seg_head[s] = (float)ah;
+          c.seg_scale[s] = c.seg_mode[s] == 2 ? (float)(ah / nrm) : 0.f;
+        }
+      });
     }
     // ---- projection onto C and dual update (u+ = Pi(u_hat - v), v+ = v - u_hat + u+)
     TV4(v, n) {
-      const float4 zz = cg4(P.zx, v), gg = cg4(P.gx, v);
-      float4 uu = cg4(P.ux, v);
+      const float4 zz = ld4v(P.zx, v), gg = ld4v(P.gx, v);
+      float4 uu = ld4v(P.ux, v);
 #pragma unroll
       for (int j = 0; j < 4; ++j)
         el(uu, j) = __fadd_rn(__fmul_rn(af, __fsub_rn(elc(zz, j), __fmul_rn(utf, elc(gg, j)))),
                               __fmul_rn(a1, el(uu, j)));
       st4(P.ux, v, uu);
     }
-    TTAIL(i, n) P.ux[i] = __fadd_rn(__fmul_rn(af, __fsub_rn(cg1(P.zx, i), __fmul_rn(utf, cg1(P.gx, i)))),
-                                    __fmul_rn(a1, cg1(P.ux, i)));
+    TTAIL(i, n) P.ux[i] = __fadd_rn(__fmul_rn(af, __fsub_rn(P.zx[i], __fmul_rn(utf, P.gx[i]))),
+                                    __fmul_rn(a1, P.ux[i]));
     each(tm, m, [&](int64_t i) {
-      const float pi = y_pre(af, a1, utf, cg1(P.zy, i), cg1(P.gy, i), cg1(P.uy, i), cg1(P.vs, i));
+      const float pi = y_pre(af, a1, utf, P.zy[i], P.gy[i], P.uy[i], P.vs[i]);
       float ui;
       if (i < z) {
         ui = pi;
@@ -709,155 +837,146 @@ __device__ void solve_one(const Team& tm, Shared& sh, float* dsm) {
         ui = fmaxf(pi, 0.f);
       } else {
         const int s = seg_of(P, i);
-        const double nrm = sqrt(sv[2 * s + 1]), p0 = sv[2 * s];
-        if (nrm <= p0) {
-          ui = pi;
-        } else if (nrm <= -p0) {
-          ui = 0.f;
-        } else {
-          const double ah = 0.5 * (p0 + nrm);
-          ui = (i == P.seg_head[s]) ? (float)ah : __fmul_rn((float)(ah / nrm), pi);
-        }
+        const int md = sh.sc.seg_mode[s];
+        ui = md == 0 ? pi : (md == 1 ? 0.f : (i == P.seg_head[s] ? sh.sc.seg_head[s] : __fmul_rn(sh.sc.seg_scale[s], pi)));
       }
       P.uy[i] = ui;
       P.vs[i] = __fsub_rn(ui, pi);
     });
-    {
-      const double uhat = al * ut + (1.0 - al) * tau;
-      const double pt = uhat - kappa;
-      const double tn = pt > 0.0 ? pt : 0.0;
-      tau = tn;
-      kappa = tn - pt;
-    }
-    ++k;
-    const bool chk = (k % st.check_interval == 0) || (k >= st.max_iters);
-    const bool ref = (k % 50 == 0) && (k < st.max_iters);
-    bool stop = false;
-    if (!isfinite(tau) || !isfinite(kappa)) {
-      status = CF_NUMERICAL;
-      stop = true;
-    }
+    const bool chk = sh.sc.chk != 0, ref = sh.sc.ref != 0;
+    bool go = sh.sc.go != 0;
     // ---- residuals and certificates
-    if (chk && !stop) {
+    if (chk && !sh.sc.stop) {
       tsync(tm);
-      apply(tm, P.fwd, P.nfwd, P.ux, P.cm, P.scratch, dsm, P.lanes);
-      apply(tm, P.adj, P.nadj, P.uy, P.cn, P.scratch, dsm, P.lanes);
+      apply<MaxT>(tm, P.fwd, P.nfwd, P.ux, P.cm, P.scratch, dsm, P.lanes);
+      apply<MaxT>(tm, P.adj, P.nadj, P.uy, P.cn, P.scratch, dsm, P.lanes);
       tsync(tm);
-      const float tf = (float)tau;
-      Acc2 s0, s1, s2, s3, s4, s5;
+      const float tf = sh.sc.tau_f;
+      Acc2 s[6];
       each(tm, m, [&](int64_t i) {
         const float bi = __ldg(P.bf + i);
-        const float e = cg1(P.cm, i) + cg1(P.vs, i);
+        const float e = P.cm[i] + P.vs[i];
         const float d = fmaf(-bi, tf, e);
-        s0.add_prod(d, d);
-        s1.add_prod(e, e);
-        s2.add_prod(bi, cg1(P.uy, i));
+        s[0].add_prod(d, d);
+        s[1].add_prod(e, e);
+        s[2].add_prod(bi, P.uy[i]);
       });
       each(tm, n, [&](int64_t i) {
-        const float ci = __ldg(P.cf + i), cn = cg1(P.cn, i);
+        const float ci = __ldg(P.cf + i), cn = P.cn[i];
         const float d = fmaf(ci, tf, cn);
-        s3.add_prod(d, d);
-        s4.add_prod(cn, cn);
-        s5.add_prod(ci, cg1(P.ux, i));
+        s[3].add_prod(d, d);
+        s[4].add_prod(cn, cn);
+        s[5].add_prod(ci, P.ux[i]);
       });
-      double v[6] = {s0.value(), s1.value(), s2.value(), s3.value(), s4.value(), s5.value()};
-      team_sum<6>(tm, sh, ph, v);
-      ++checks;
-      cx = v[5];
-      by = v[2];
-      bool bad = false;
-      for (int j = 0; j < 6; ++j) bad |= !isfinite(v[j]);
-      if (bad) {
-        status = CF_NUMERICAL;
-        stop = true;
-      } else {
-        if (tau > 0.0) {
-          pri = sqrt(v[0]) / tau / (1.0 + P.nb);
-          dual = sqrt(v[3]) / tau / (1.0 + P.nc);
-          const double cxt = v[5] / tau, byt = v[2] / tau;
-          gap = fabs(cxt + byt) / (1.0 + fabs(cxt) + fabs(byt));
-          if (pri <= st.eps && dual <= st.eps && gap <= st.eps) {
-            status = CF_SOLVED;
-            stop = true;
+      team_sum<6>(tm, sh, ph, s, [&](const double* v) {
+        Scal& c = sh.sc;
+        const Settings& st2 = sh.P.st;
+        const double tau = c.tau;
+        ++c.checks;
+        c.cx = v[5];
+        c.by = v[2];
+        bool bad = false;
+        for (int j = 0; j < 6; ++j) bad |= !isfinite(v[j]);
+        if (bad) {
+          c.status = CF_NUMERICAL;
+          c.stop = 1;
+        } else {
+          if (tau > 0.0) {
+            c.pri = sqrt(v[0]) / tau / (1.0 + sh.P.nb);
+            c.dual = sqrt(v[3]) / tau / (1.0 + sh.P.nc);
+            const double cxt = v[5] / tau, byt = v[2] / tau;
+            c.gap = fabs(cxt + byt) / (1.0 + fabs(cxt) + fabs(byt));
+            if (c.pri <= st2.eps && c.dual <= st2.eps && c.gap <= st2.eps) {
+              c.status = CF_SOLVED;
+              c.stop = 1;
+            }
+          }
+          if (!c.stop) {
+            if (-v[2] > 0.0 && sqrt(v[4]) <= st2.eps_inf * (-v[2])) {
+              c.status = CF_INFEASIBLE;
+              c.stop = 1;
+            } else if (-v[5] > 0.0 && sqrt(v[1]) <= st2.eps_inf * (-v[5])) {
+              c.status = CF_UNBOUNDED;
+              c.stop = 1;
+            }
           }
         }
-        if (!stop) {
-          if (-v[2] > 0.0 && sqrt(v[4]) <= st.eps_inf * (-v[2])) {
-            status = CF_INFEASIBLE;
-            stop = true;
-          } else if (-v[5] > 0.0 && sqrt(v[1]) <= st.eps_inf * (-v[5])) {
-            status = CF_UNBOUNDED;
-            stop = true;
-          }
-        }
-      }
+        c.go = (!c.stop && c.k < st2.max_iters) ? 1 : 0;
+      });
+      go = sh.sc.go != 0;
     }
-    const bool go = !stop && k < st.max_iters;
     if (!go) break;
     // ---- exact A z_x and G z_x every 50 iterations
     if (ref) {
-      ++refreshes;
+      if (threadIdx.x == 0) ++sh.sc.refreshes;
       tsync(tm);
-      apply(tm, P.fwd, P.nfwd, P.zx, P.az, P.scratch, dsm, P.lanes);
+      apply<MaxT>(tm, P.fwd, P.nfwd, P.zx, P.az, P.scratch, dsm, P.lanes);
       tsync(tm);
-      apply(tm, P.adj, P.nadj, P.az, P.gz, P.scratch, dsm, P.lanes);
+      apply<MaxT>(tm, P.adj, P.nadj, P.az, P.gz, P.scratch, dsm, P.lanes);
       tsync(tm);
-      each(tm, n, [&](int64_t i) { P.gz[i] = fmaf((float)lam, cg1(P.zx, i), cg1(P.gz, i)); });
+      each(tm, n, [&](int64_t i) { P.gz[i] = P.zx[i] + P.gz[i]; });  // G z = lam z + A^T A z, lam = 1
     }
   }
 
   // ---- outputs
+  if (threadIdx.x == 0) {
+    Scal& c = sh.sc;
+    if (c.status == CF_INFEASIBLE) {
+      c.sx = NAN; c.ss = NAN; c.sy = 1.0 / (-c.by);
+    } else if (c.status == CF_UNBOUNDED) {
+      c.sx = 1.0 / (-c.cx); c.ss = c.sx; c.sy = NAN;
+    } else if (c.tau > 0.0) {
+      c.sx = c.sy = c.ss = 1.0 / c.tau;
+    } else {
+      c.sx = c.sy = c.ss = NAN;
+    }
+  }
+  __syncthreads();
   if (!P.tune) {
     if (P.want_out) {
-      double sx, sy, ss;
-      if (status == CF_INFEASIBLE) {
-        sx = NAN; ss = NAN; sy = 1.0 / (-by);
-      } else if (status == CF_UNBOUNDED) {
-        sx = 1.0 / (-cx); ss = sx; sy = NAN;
-      } else if (tau > 0.0) {
-        sx = sy = ss = 1.0 / tau;
-      } else {
-        sx = sy = ss = NAN;
-      }
-      each(tm, n, [&](int64_t i) { P.out[i] = (double)cg1(P.ux, i) * sx; });
+      const double sx = sh.sc.sx, sy = sh.sc.sy, ss = sh.sc.ss;
+      each(tm, n, [&](int64_t i) { P.out[i] = (double)P.ux[i] * sx; });
       each(tm, m, [&](int64_t i) {
-        P.out[n + i] = (double)cg1(P.uy, i) * sy;
-        P.out[n + m + i] = (double)cg1(P.vs, i) * ss;
+        P.out[n + i] = (double)P.uy[i] * sy;
+        P.out[n + m + i] = (double)P.vs[i] * ss;
       });
     }
     if (P.want_uv) {
       each(tm, n, [&](int64_t i) {
-        P.uv[i] = cg1(P.ux, i);
+        P.uv[i] = P.ux[i];
         P.uv[N + i] = 0.0;
       });
       each(tm, m, [&](int64_t i) {
-        P.uv[n + i] = cg1(P.uy, i);
-        P.uv[N + n + i] = cg1(P.vs, i);
+        P.uv[n + i] = P.uy[i];
+        P.uv[N + n + i] = P.vs[i];
       });
       if (tm.tt == 0) {
-        P.uv[n + m] = tau;
-        P.uv[N + n + m] = kappa;
+        P.uv[n + m] = sh.sc.tau;
+        P.uv[N + n + m] = sh.sc.kappa;
       }
     }
   }
   if (tm.tt == 0) {
+    const Scal& s = sh.sc;
     Ctl* c = P.ctl;
-    c->lam = lam;
-    c->hg = hg;
-    c->tau = tau;
-    c->kappa = kappa;
-    c->pri = pri;
-    c->dual = dual;
-    c->gap = gap;
-    c->cx = cx;
-    c->by = by;
-    c->cg_total = cg_total;
-    c->k = k;
-    c->checks = checks;
-    c->refreshes = refreshes;
-    c->status = status;
+    c->lam = 1.0;
+    c->hg = s.hg;
+    c->tau = s.tau;
+    c->kappa = s.kappa;
+    c->pri = s.pri;
+    c->dual = s.dual;
+    c->gap = s.gap;
+    c->cx = s.cx;
+    c->by = s.by;
+    c->cg_total = s.cg_total;
+    c->k = s.k;
+    c->checks = s.checks;
+    c->refreshes = s.refreshes;
+    c->status = s.status;
     c->stop = 1;
-    if (P.do_setup && !P.tune) c->setup_iters = setup_iters;
+    if (P.do_setup && !P.tune) c->setup_iters = s.setup_iters;
+    c->t_start = (long long)t_start;
+    c->t_end = (long long)gtimer();
   }
 }
 
@@ -890,7 +1009,7 @@ __global__ void __launch_bounds__(MaxT) k_team(const Prob* __restrict__ probs, c
       cl.sync();
       if (it >= nbig) break;
       load_prob(sh, probs + order[it]);
-      solve_one(tm, sh, dsm);
+      solve_one<MaxT>(tm, sh, dsm);
     }
   }
   tm.C = 1;
@@ -904,7 +1023,7 @@ __global__ void __launch_bounds__(MaxT) k_team(const Prob* __restrict__ probs, c
     __syncthreads();
     if (it >= nsmall) break;
     load_prob(sh, probs + order[nbig + it]);
-    solve_one(tm, sh, dsm);
+    solve_one<MaxT>(tm, sh, dsm);
   }
 }
 
@@ -1102,7 +1221,7 @@ cf_err plan_problem(cf_problem* P) {
   for (const std::vector<Term>* lst : {&pl.fwd, &pl.adj, &pl.adj_m})
     for (const Term& t : *lst) {
       if (t.kind == T_DENSE_N) smem = std::max<int64_t>(smem, (t.cols + 15) & ~(int64_t)15);
-      if (t.kind == T_CONV) smem = std::max<int64_t>(smem, 2 * t.Lp + kConvTile);
+      if (t.kind == T_CONV) smem = std::max<int64_t>(smem, 2 * t.Lp + kConvTile + 2 * kConvR);
       if (t.kind == T_DENSE_T) pl.dense_t_cols = std::max(pl.dense_t_cols, t.rows);
     }
   pl.pass_bytes = bytes + 4.0 * (P->n + P->m);
@@ -1435,9 +1554,10 @@ cf_schedule default_schedule() {
   cf_schedule s{};
   s.cluster = 4;
   s.threads = 512;
-  s.csr_nnz_per_lane = 4;
-  s.team_bytes = 4e6;
-  s.auto_max_bytes = 48e6;
+  s.csr_nnz_per_lane = 8;
+  s.team_bytes = 512e3;
+  s.auto_max_bytes = 4e6;
+  s.batch_max_bytes = 48e6;
   return s;
 }
 
@@ -1454,14 +1574,14 @@ bool schedule_valid(const cf_schedule& s, std::string* why) {
     *why = "csr_nnz_per_lane must be in [1, 64]";
     return false;
   }
-  if (!(s.team_bytes >= 0) || !(s.auto_max_bytes >= 0)) {
-    *why = "team_bytes and auto_max_bytes must be >= 0";
+  if (!(s.team_bytes >= 0) || !(s.auto_max_bytes >= 0) || !(s.batch_max_bytes >= 0)) {
+    *why = "team_bytes, auto_max_bytes and batch_max_bytes must be >= 0";
     return false;
   }
   return true;
 }
 
-cf_err pick_engine(cf_problem* P, const cf_settings* st, int* engine) {
+cf_err pick_engine(cf_problem* P, const cf_settings* st, int* engine, bool in_batch) {
   if (st->host_loop || st->engine == CF_ENGINE_GRAPH) {
     *engine = CF_ENGINE_GRAPH;
     return CF_OK;
@@ -1474,7 +1594,8 @@ cf_err pick_engine(cf_problem* P, const cf_settings* st, int* engine) {
   double lim;
   {
     std::lock_guard<std::mutex> lk(P->ctx->sched_mu);
-    lim = P->ctx->sched.auto_max_bytes;
+    lim = in_batch ? std::max(P->ctx->sched.auto_max_bytes, P->ctx->sched.batch_max_bytes)
+                   : P->ctx->sched.auto_max_bytes;
   }
   *engine = (P->plan.ok && P->plan.pass_bytes <= lim) ? CF_ENGINE_TEAM : CF_ENGINE_GRAPH;
   return CF_OK;
@@ -1527,7 +1648,7 @@ extern "C" cf_err solve_batch_tune(cf_problem* const* probs, int32_t count, int3
   std::vector<cf_problem*> tp;
   for (int32_t i = 0; i < count; ++i) {
     cf_problem* P = probs[i];
-    if (!P->plan.ok || P->plan.pass_bytes > held.auto_max_bytes) continue;
+    if (!P->plan.ok || P->plan.pass_bytes > std::max(held.auto_max_bytes, held.batch_max_bytes)) continue;
     CF_TRY(ensure_state(P));
     write_settings(P, &st, false);
     P->x_out = P->y_out = P->s_out = P->uv_out = nullptr;
@@ -1566,7 +1687,7 @@ extern "C" cf_err solve_batch_tune(cf_problem* const* probs, int32_t count, int3
     b1.cluster = 1;
     double b1_ms = 1e300;
     for (int T : {256, 512, 1024})
-      for (int npl : {2, 4, 8}) {
+      for (int npl : {4, 8, 16, 32}) {
         cf_schedule c = held;
         c.cluster = 1;
         c.threads = T;
@@ -1607,6 +1728,7 @@ extern "C" cf_err solve_batch_tune(cf_problem* const* probs, int32_t count, int3
   for (cf_problem* P : tp) P->setup_done = false;
   if (r != CF_OK) return r;
   best.auto_max_bytes = held.auto_max_bytes;
+  best.batch_max_bytes = held.batch_max_bytes;
   {
     std::lock_guard<std::mutex> lk(ctx->sched_mu);
     ctx->sched = best;
