@@ -143,14 +143,14 @@ typedef struct {
   int32_t threads;         /* threads per CTA: 256, 512 or 1024 (512) */
   int32_t csr_nnz_per_lane;/* CSR rows get the fewest lanes (a power of two,
                               1..32) that hold the average row at this many
-                              nonzeros per lane (8) */
+                              nonzeros per lane (16) */
   int32_t reserved;
   double team_bytes;       /* problems whose operator pass reads at least this
                               many bytes run on a whole cluster team; smaller
-                              ones on one CTA (512e3) */
+                              ones on one CTA (256e3) */
   double auto_max_bytes;   /* CF_ENGINE_AUTO limit for single and served solves
-                              (4e6: above it one problem fills the GPU's
-                              kernels and the graph engine is faster) */
+                              (1e6: above it the graph engine's whole-GPU
+                              passes outrun a cluster team) */
   double batch_max_bytes;  /* CF_ENGINE_AUTO limit inside solve_batch (48e6: the
                               batch's other problems keep the SMs busy) */
 } cf_schedule;

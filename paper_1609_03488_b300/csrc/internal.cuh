@@ -93,7 +93,8 @@ struct cf_op {
   void* a = nullptr;
   float* row_scale = nullptr;
   int64_t lda = 0;
-  // csr (and its transpose, built at creation for a deterministic adjoint)
+  // csr (and its transpose, built at creation for a deterministic adjoint);
+  // col / val arrays padded with zeros to whole 8-entry chunks plus one chunk
   int64_t nnz = 0;
   int32_t *rowptr = nullptr, *col = nullptr, *t_rowptr = nullptr, *t_col = nullptr;
   void *val = nullptr, *t_val = nullptr;

@@ -365,11 +365,18 @@ cf_err cf_op_csr(cf_ctx* ctx, int64_t m, int64_t n, int64_t nnz, const int32_t* 
   cf_op* op = new_op(ctx, OP_CSR, m, n);
   op->prec = storage;
   op->nnz = nnz;
+  // Index and value arrays hold whole 8-entry chunks plus one spare chunk of
+  // zeros, so that a kernel may load any aligned chunk that starts before
+  // nnz with 16-byte vector loads.
+  const int64_t npad = (int64_t)align_up((size_t)nnz, 8) + 8;
+  const size_t vsz = storage == CF_FP32 ? 4 : 2;
   auto run = [&]() -> cf_err {
     CF_TRY(dev_alloc(&op->rowptr, m + 1, &op->device_bytes));
-    CF_TRY(dev_alloc(&op->col, nnz, &op->device_bytes));
+    CF_TRY(dev_alloc(&op->col, npad, &op->device_bytes));
     CF_TRY(dev_alloc(&op->t_rowptr, n + 1, &op->device_bytes));
-    CF_TRY(dev_alloc(&op->t_col, nnz, &op->device_bytes));
+    CF_TRY(dev_alloc(&op->t_col, npad, &op->device_bytes));
+    CF_CUDA(cudaMemset(op->col, 0, npad * 4));
+    CF_CUDA(cudaMemset(op->t_col, 0, npad * 4));
     CF_CUDA(cudaMemcpy(op->rowptr, rp.data(), (m + 1) * 4, cudaMemcpyHostToDevice));
     CF_CUDA(cudaMemcpy(op->t_rowptr, trp.data(), (n + 1) * 4, cudaMemcpyHostToDevice));
     if (nnz) {
@@ -377,15 +384,20 @@ cf_err cf_op_csr(cf_ctx* ctx, int64_t m, int64_t n, int64_t nnz, const int32_t* 
       CF_CUDA(cudaMemcpy(op->t_col, tcl.data(), nnz * 4, cudaMemcpyHostToDevice));
     }
     if (storage == CF_FP32) {
-      CF_TRY(dev_alloc((float**)&op->val, nnz, &op->device_bytes));
-      CF_TRY(dev_alloc((float**)&op->t_val, nnz, &op->device_bytes));
+      CF_TRY(dev_alloc((float**)&op->val, npad, &op->device_bytes));
+      CF_TRY(dev_alloc((float**)&op->t_val, npad, &op->device_bytes));
+    } else {
+      CF_TRY(dev_alloc((__nv_bfloat16**)&op->val, npad, &op->device_bytes));
+      CF_TRY(dev_alloc((__nv_bfloat16**)&op->t_val, npad, &op->device_bytes));
+    }
+    CF_CUDA(cudaMemset(op->val, 0, npad * vsz));
+    CF_CUDA(cudaMemset(op->t_val, 0, npad * vsz));
+    if (storage == CF_FP32) {
       if (nnz) {
         CF_CUDA(cudaMemcpy(op->val, vl.data(), nnz * 4, cudaMemcpyHostToDevice));
         CF_CUDA(cudaMemcpy(op->t_val, tvl.data(), nnz * 4, cudaMemcpyHostToDevice));
       }
     } else {
-      CF_TRY(dev_alloc((__nv_bfloat16**)&op->val, nnz, &op->device_bytes));
-      CF_TRY(dev_alloc((__nv_bfloat16**)&op->t_val, nnz, &op->device_bytes));
       std::vector<__nv_bfloat16> b1(nnz), b2(nnz);
       for (int64_t k = 0; k < nnz; ++k) {
         b1[k] = __float2bfloat16_rn(vl[k]);

@@ -85,7 +85,7 @@ struct __align__(16) Scal {
 struct __align__(16) Shared {
   Prob P;              // the problem being solved
   Scal sc;             // its scalar state
-  double part[2][8];   // this CTA's partials, double-buffered across sums
+  float part[2][16];   // this CTA's partials (hi, lo pairs), double-buffered across sums
   float bh[8][32];     // block-sum scratch (double-float), one column per warp
   float bl[8][32];
   int item;            // work-queue slot taken by the team's rank 0
@@ -129,10 +129,12 @@ __device__ __forceinline__ void df_add(float& hi, float& lo, float hi2, float lo
   lo = __fsub_rn(t, __fsub_rn(hi, s));
 }
 
-// Team-wide deterministic sum of NV compensated per-thread sums: double-float
-// across each warp (float shuffles), float64 across the warps of a CTA (warp
-// 0 only) and across the CTAs of the team (every CTA adds the partials in
-// rank order).  Then thread 0 of each CTA runs fin(totals), which updates
+// Team-wide deterministic sum of NV compensated per-thread sums, in
+// double-float throughout (float shuffles and float arithmetic; one SM's
+// float64 rate is a small fraction of its float32 rate): across each warp,
+// across the warps of a CTA (warp 0), then across the CTAs of the team (lane
+// j of warp 0 adds value j of every CTA's partial in rank order).  Thread 0
+// of each CTA then runs fin(totals) -- the totals as float64 -- which updates
 // the scalar state, and a barrier makes it visible to the CTA.
 template <int NV, class F>
 __device__ void team_sum(const Team& tm, Shared& sh, int& ph, Acc2 (&a)[NV], F&& fin) {
@@ -153,20 +155,31 @@ __device__ void team_sum(const Team& tm, Shared& sh, int& ph, Acc2 (&a)[NV], F&&
   }
   __syncthreads();
   if (wid == 0) {
-    double tv[NV];
+    float th[NV], tl[NV];
 #pragma unroll
     for (int j = 0; j < NV; ++j) {
-      double t = lane < nw ? (double)sh.bh[j][lane] + (double)sh.bl[j][lane] : 0.0;
+      float hi = lane < nw ? sh.bh[j][lane] : 0.f, lo = lane < nw ? sh.bl[j][lane] : 0.f;
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-      tv[j] = t;  // lane 0's value is the CTA's sum
+      for (int o = 16; o > 0; o >>= 1) {
+        const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+        const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+        df_add(hi, lo, h2, l2);
+      }
+      th[j] = hi;  // lane 0's values are the CTA's sums
+      tl[j] = lo;
     }
     if (tm.C > 1) {
       if (lane == 0) {
 #pragma unroll
-        for (int j = 0; j < NV; ++j) sh.part[ph][j] = tv[j];
+        for (int j = 0; j < NV; ++j) {
+          sh.part[ph][2 * j] = th[j];
+          sh.part[ph][2 * j + 1] = tl[j];
+        }
       }
     } else if (lane == 0) {
+      double tv[NV];
+#pragma unroll
+      for (int j = 0; j < NV; ++j) tv[j] = (double)th[j] + (double)tl[j];
       fin(tv);
     }
   }
@@ -174,12 +187,16 @@ __device__ void team_sum(const Team& tm, Shared& sh, int& ph, Acc2 (&a)[NV], F&&
     cgr::cluster_group cl = cgr::this_cluster();
     cl.sync();
     if (wid == 0) {
-      double tot = 0.0;
+      float hi = 0.f, lo = 0.f;
       if (lane < NV)
-        for (int r = 0; r < tm.C; ++r) tot += *cl.map_shared_rank(&sh.part[ph][lane], r);
+        for (int r = 0; r < tm.C; ++r) {
+          const float* pr = cl.map_shared_rank(&sh.part[ph][2 * lane], r);
+          df_add(hi, lo, pr[0], pr[1]);
+        }
       double tv[NV];
 #pragma unroll
-      for (int j = 0; j < NV; ++j) tv[j] = __shfl_sync(0xffffffffu, tot, j);
+      for (int j = 0; j < NV; ++j)
+        tv[j] = (double)__shfl_sync(0xffffffffu, hi, j) + (double)__shfl_sync(0xffffffffu, lo, j);
       if (lane == 0) fin(tv);
     }
   }
@@ -202,12 +219,37 @@ __device__ __forceinline__ float tval(const void* __restrict__ val, int32_t k) {
   return BF16 ? __bfloat162float(__ldg(((const __nv_bfloat16*)val) + k)) : __ldg(((const float*)val) + k);
 }
 
-// Rows to groups of L lanes (L a power of two); each lane issues the index
-// and value loads of U entries before it uses any, then gathers x
-// (L1-resident) and adds across its group by shuffles.  The row pointers of a
-// warp's next rows are loaded while it works on the current ones.
-template <bool BF16, int U>
-__device__ void term_csr(const Team& tm, const Term& t, const float* x, float* y, int L) {
+// Streaming loads of operator data that skip L1 (so that they do not evict
+// the gathered vector) and stay cacheable in L2.
+__device__ __forceinline__ int4 ld_stream_i4(const int32_t* p) {
+  int4 v;
+  asm("ld.global.nc.L1::no_allocate.v4.s32 {%0, %1, %2, %3}, [%4];"
+      : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ uint4 ld_stream_u4(const void* p) {
+  uint4 v;
+  asm("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
+      : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
+  return v;
+}
+
+// CSR rows to groups of L lanes (L a power of two).  A lane takes aligned
+// chunks of 8 entries of its row (the arrays are padded to whole chunks):
+// two 16-byte loads of column indices and one (BF16) or two (FP32) of values
+// per chunk, UC chunks issued before any is used, entries outside the row
+// masked.  The input vector is staged in the CTA's shared memory when it
+// fits, so the gathers never leave the SM.  The row pointers of a warp's
+// next rows are loaded while it works on the current ones.
+template <bool BF16, int UC>
+__device__ void term_csr(const Team& tm, const Term& t, const float* x, float* y, int L, float* dsm) {
+  const bool staged = t.cols <= kCsrStageFloats;
+  if (staged) {
+    __syncthreads();  // earlier users of the shared buffer are done
+    for (int64_t i = threadIdx.x; i < t.cols; i += blockDim.x) dsm[i] = x[t.xo + i];
+    __syncthreads();
+  }
+  const float* xs = staged ? dsm : x + t.xo;
   const int lane = threadIdx.x & 31;
   const int rpw = 32 / L;
   const int sub = lane / L, l = lane & (L - 1);
@@ -215,28 +257,45 @@ __device__ void term_csr(const Team& tm, const Term& t, const float* x, float* y
   const int64_t step = nwarps * rpw;
   const int32_t* __restrict__ rp = t.rowptr;
   const int32_t* __restrict__ col = t.col;
-  const void* __restrict__ val = t.a;
-  const float* xb = x + t.xo;
+  const char* __restrict__ val = (const char*)t.a;
+  constexpr int VB = BF16 ? 2 : 4;  // bytes per value
   int64_t r = warp * rpw + sub;
   int32_t b = r < t.rows ? __ldg(rp + r) : 0, e = r < t.rows ? __ldg(rp + r + 1) : 0;
   for (int64_t rb = warp * rpw; rb < t.rows; rb += step) {
     const int64_t rn = r + step;
     const int32_t nb = rn < t.rows ? __ldg(rp + rn) : 0, ne = rn < t.rows ? __ldg(rp + rn + 1) : 0;
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int32_t k = b + l; k < e; k += U * L) {
-      int32_t c[U];
-      float v[U];
+    for (int32_t k = (b & ~7) + 8 * l; k < e; k += 8 * L * UC) {
+      int4 ca[UC], cb[UC];
+      uint4 va[UC], vb[UC];
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int32_t kk = k + u * L;
-        const bool ok = kk < e;
-        c[u] = ok ? __ldg(col + kk) : -1;
-        v[u] = ok ? tval<BF16>(val, kk) : 0.f;
+      for (int j = 0; j < UC; ++j) {
+        const int32_t kk = k + 8 * L * j;
+        if (kk < e) {
+          ca[j] = ld_stream_i4(col + kk);
+          cb[j] = ld_stream_i4(col + kk + 4);
+          va[j] = ld_stream_u4(val + (size_t)kk * VB);
+          if (!BF16) vb[j] = ld_stream_u4(val + (size_t)kk * VB + 16);
+        }
       }
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const float xv = c[u] >= 0 ? xb[c[u]] : 0.f;
-        acc[u & 3] = fmaf(v[u], xv, acc[u & 3]);
+      for (int j = 0; j < UC; ++j) {
+        const int32_t kk = k + 8 * L * j;
+        if (kk < e) {
+          const int32_t c8[8] = {ca[j].x, ca[j].y, ca[j].z, ca[j].w, cb[j].x, cb[j].y, cb[j].z, cb[j].w};
+          float v8[8];
+          if (BF16) {
+            Vec<__nv_bfloat16>::unpack(va[j], v8);
+          } else {
+            Vec<float>::unpack(va[j], v8);
+            Vec<float>::unpack(vb[j], v8 + 4);
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int32_t idx = kk + u;
+            if (idx >= b && idx < e) acc[u & 3] = fmaf(v8[u], xs[c8[u]], acc[u & 3]);
+          }
+        }
       }
     }
     float s = (acc[0] + acc[1]) + (acc[2] + acc[3]);
@@ -454,11 +513,11 @@ __device__ void term_conv(const Team& tm, const Term& t, const float* x, float* 
 // y = the flattened operator applied to x (terms in order).  Compiled once
 // per CTA size (not inlined at each call) so that the term loops get
 // registers of their own; CTAs of 1024 threads (64 registers a thread) keep
-// 8 CSR entries a lane in flight, smaller CTAs 16.
+// one CSR chunk (8 entries) a lane in flight, smaller CTAs two.
 template <int MaxT>
 __device__ __noinline__ void apply(const Team& tm, const Term* terms, int nt, const float* x, float* y,
                                    float* scratch, float* dsm, int lanes) {
-  constexpr int U = MaxT >= 1024 ? 8 : 16;
+  constexpr int UC = MaxT >= 1024 ? 1 : 2;  // CSR chunks in flight per lane
   for (int k = 0; k < nt; ++k) {
     const Term& t = terms[k];
     if (t.sync) tsync(tm);
@@ -471,9 +530,9 @@ __device__ __noinline__ void apply(const Team& tm, const Term* terms, int nt, co
         break;
       case T_CSR:
         if (t.prec == CF_BF16)
-          term_csr<true, U>(tm, t, x, y, lanes);
+          term_csr<true, UC>(tm, t, x, y, lanes, dsm);
         else
-          term_csr<false, U>(tm, t, x, y, lanes);
+          term_csr<false, UC>(tm, t, x, y, lanes, dsm);
         break;
       case T_DENSE_N:
         if (t.prec == CF_BF16)
@@ -580,8 +639,9 @@ __device__ __noinline__ void cg_run(const Team& tm, Shared& sh, int& ph, float* 
         b[0].add_prod(pi, qi);
       }
       team_sum<1>(tm, sh, ph, b, [&](const double* tv) {
-        const double pq = tv[0];
-        sh.sc.alpha_f = (float)(pq > 0.0 ? sh.sc.rr / pq : 0.0);
+        // the step length is a float32 quantity; float64 stays in the CG test
+        const float pq = (float)tv[0];
+        sh.sc.alpha_f = pq > 0.f ? (float)sh.sc.rr / pq : 0.f;
       });
     }
     const float a = sh.sc.alpha_f;
@@ -622,7 +682,7 @@ __device__ __noinline__ void cg_run(const Team& tm, Shared& sh, int& ph, float* 
       team_sum<1>(tm, sh, ph, c0, [&](const double* tv) {
         Scal& c = sh.sc;
         const double rr_new = tv[0];
-        c.beta_f = (float)(c.rr > 0.0 ? rr_new / c.rr : 0.0);
+        c.beta_f = c.rr > 0.0 ? (float)rr_new / (float)c.rr : 0.f;
         c.rr = rr_new;
         ++c.cg_it;
         if (mode == CG_SETUP)
@@ -659,6 +719,41 @@ __device__ __forceinline__ unsigned long long gtimer() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
+}
+
+// Head value p0 and tail norm of each of the NS second-order cone blocks of
+// the point to project; the projection constants of each block (float32:
+// the projection is a float32 step) go to the scalar state.
+template <int NS>
+__device__ void soc_norms(const Team& tm, Shared& sh, int& ph, float af, float a1, float utf) {
+  const Prob& P = sh.P;
+  const int64_t nl = P.z + P.l;
+  Acc2 acc[2 * NS];
+  each(tm, P.m, [&](int64_t i) {
+    if (i < nl) return;
+    const float pi = y_pre(af, a1, utf, P.zy[i], P.gy[i], P.uy[i], P.vs[i]);
+    const int s = seg_of(P, i);
+#pragma unroll
+    for (int j = 0; j < NS; ++j) {
+      if (j == s) {
+        if (i == P.seg_head[j])
+          acc[2 * j].add(pi);
+        else
+          acc[2 * j + 1].add_prod(pi, pi);
+      }
+    }
+  });
+  team_sum<2 * NS>(tm, sh, ph, acc, [&](const double* tv) {
+    Scal& c = sh.sc;
+#pragma unroll
+    for (int j = 0; j < NS; ++j) {
+      const float p0 = (float)tv[2 * j], nrm = sqrtf((float)tv[2 * j + 1]);
+      const float ah = 0.5f * (p0 + nrm);
+      c.seg_mode[j] = nrm <= p0 ? 0 : (nrm <= -p0 ? 1 : 2);
+      c.seg_head[j] = ah;
+      c.seg_scale[j] = c.seg_mode[j] == 2 ? ah / nrm : 0.f;
+    }
+  });
 }
 
 template <int MaxT>
@@ -789,32 +884,12 @@ __device__ void solve_one(const Team& tm, Shared& sh, float* dsm) {
     }
     const float utf = sh.sc.ut_f;
     // ---- second-order cones: head value and tail norm of each block
-    if (P.nseg > 0) {
-      Acc2 acc[2 * kMaxSeg];
-      each(tm, m, [&](int64_t i) {
-        if (i < nl) return;
-        const float pi = y_pre(af, a1, utf, P.zy[i], P.gy[i], P.uy[i], P.vs[i]);
-        const int s = seg_of(P, i);
-#pragma unroll
-        for (int j = 0; j < kMaxSeg; ++j) {
-          if (j == s) {
-            if (i == P.seg_head[j])
-              acc[2 * j].add(pi);
-            else
-              acc[2 * j + 1].add_prod(pi, pi);
-          }
-        }
-      });
-      team_sum<2 * kMaxSeg>(tm, sh, ph, acc, [&](const double* tv) {
-        Scal& c = sh.sc;
-        for (int s = 0; s < sh.P.nseg; ++s) {
-          const double p0 = tv[2 * s], nrm = sqrt(tv[2 * s + 1]);
-          const double ah = 0.5 * (p0 + nrm);
-          c.seg_mode[s] = nrm <= p0 ? 0 : (nrm <= -p0 ? 1 : 2);
-          c.seg_head[s] = (float)ah;
-          c.seg_scale[s] = c.seg_mode[s] == 2 ? (float)(ah / nrm) : 0.f;
-        }
-      });
+    switch (P.nseg) {
+      case 1: soc_norms<1>(tm, sh, ph, af, a1, utf); break;
+      case 2: soc_norms<2>(tm, sh, ph, af, a1, utf); break;
+      case 3: soc_norms<3>(tm, sh, ph, af, a1, utf); break;
+      case 4: soc_norms<4>(tm, sh, ph, af, a1, utf); break;
+      default: break;
     }
     // ---- projection onto C and dual update (u+ = Pi(u_hat - v), v+ = v - u_hat + u+)
     TV4(v, n) {
@@ -1223,6 +1298,7 @@ cf_err plan_problem(cf_problem* P) {
       if (t.kind == T_DENSE_N) smem = std::max<int64_t>(smem, (t.cols + 15) & ~(int64_t)15);
       if (t.kind == T_CONV) smem = std::max<int64_t>(smem, 2 * t.Lp + kConvTile + 2 * kConvR);
       if (t.kind == T_DENSE_T) pl.dense_t_cols = std::max(pl.dense_t_cols, t.rows);
+      if (t.kind == T_CSR && t.cols <= kCsrStageFloats) smem = std::max<int64_t>(smem, t.cols);
     }
   pl.pass_bytes = bytes + 4.0 * (P->n + P->m);
   pl.avg_row_nnz = rows > 0 ? nnz / rows : 0.0;
@@ -1554,9 +1630,9 @@ cf_schedule default_schedule() {
   cf_schedule s{};
   s.cluster = 4;
   s.threads = 512;
-  s.csr_nnz_per_lane = 8;
-  s.team_bytes = 512e3;
-  s.auto_max_bytes = 4e6;
+  s.csr_nnz_per_lane = 16;
+  s.team_bytes = 256e3;
+  s.auto_max_bytes = 1e6;
   s.batch_max_bytes = 48e6;
   return s;
 }
@@ -1687,7 +1763,7 @@ extern "C" cf_err solve_batch_tune(cf_problem* const* probs, int32_t count, int3
     b1.cluster = 1;
     double b1_ms = 1e300;
     for (int T : {256, 512, 1024})
-      for (int npl : {4, 8, 16, 32}) {
+      for (int npl : {8, 16, 32, 64}) {
         cf_schedule c = held;
         c.cluster = 1;
         c.threads = T;

@@ -18,6 +18,7 @@ constexpr int kConvMaxLp = 2048;    // padded taps of a 1-D convolution leaf
 constexpr int kConvTile = 4096;     // convolution outputs per shared-memory tile
 constexpr int kDenseMaxCols = 16384;// forward dense input staged in shared memory
 constexpr int kDenseTGroups = 16;   // row groups of the adjoint dense product
+constexpr int kCsrStageFloats = 40960; // CSR input staged in shared memory up to this length
 
 enum TermKind : int32_t { T_FILL = 0, T_DIAG = 1, T_CSR = 2, T_DENSE_N = 3, T_DENSE_T = 4, T_CONV = 5 };
 

@@ -148,7 +148,7 @@ def test_auto_routing_and_unsupported_problems(B):
     B.set_schedule(ctx, auto_max_bytes=0.0)       # now everything is too large for AUTO
     info, *_ = B.solve(P)
     assert info["kernel_launches"] > 1
-    B.set_schedule(ctx, auto_max_bytes=4e6)
+    B.set_schedule(ctx, auto_max_bytes=1e6)
     # unsupported: an operator product, 5 second-order cones, a long
     # convolution, a wide dense leaf
     D = rng.standard_normal((30, 20)).astype(np.float32)
@@ -171,13 +171,13 @@ def test_auto_routing_and_unsupported_problems(B):
 
 def test_schedule_validation(B):
     ctx = _ctx(B)
-    assert B.get_schedule(ctx)["team_bytes"] == 512e3
+    assert B.get_schedule(ctx)["team_bytes"] == 256e3 and B.get_schedule(ctx)["auto_max_bytes"] == 1e6
     for bad in (dict(cluster=3), dict(threads=128), dict(csr_nnz_per_lane=0), dict(team_bytes=-1.0)):
         with pytest.raises(B.CfError) as e:
             B.set_schedule(ctx, **bad)
         assert e.value.code == B.CF_E_INVALID
     s = B.get_schedule(ctx)
-    assert (s["cluster"], s["threads"], s["csr_nnz_per_lane"]) == (4, 512, 8)
+    assert (s["cluster"], s["threads"], s["csr_nnz_per_lane"]) == (4, 512, 16)
 
 
 def test_engine_switch_redoes_setup(B):
