@@ -38,7 +38,7 @@ import numpy as np
 import scipy.linalg as sla
 
 from . import cg as cg_mod
-from . import cones, linop
+from . import cones, equil as equil_mod, linop
 
 SOLVED, INFEASIBLE, UNBOUNDED, MAX_ITERS, NUMERICAL = 0, 1, 2, 3, 4
 STATUS_NAMES = {SOLVED: "solved", INFEASIBLE: "infeasible", UNBOUNDED: "unbounded",
@@ -137,7 +137,7 @@ def setup(op, b, c, ls):
 
 def solve(A, b, c, cone, *, eps=1e-4, eps_infeas=None, alpha=1.5, max_iters=100000,
           check_interval=10, linsys="direct", cg_fixed_steps=None, cg_max_steps=50,
-          cg_tol_rel=1.0, cg_tol_exp=1.5, cg_tol_min=1e-12, trajectory=0):
+          cg_tol_rel=1.0, cg_tol_exp=1.5, cg_tol_min=1e-12, trajectory=0, equil=None):
     """Run SCS on ``min c^T x s.t. A x + s = b, s in K`` in float64.
 
     ``linsys="direct"`` solves the subspace step exactly (Cholesky of
@@ -153,15 +153,31 @@ def solve(A, b, c, cone, *, eps=1e-4, eps_infeas=None, alpha=1.5, max_iters=1000
         infeasible  if -b^T u_y > 0 and ||A^T u_y|| <= eps_infeas (-b^T u_y)
         unbounded   if -c^T u_x > 0 and ||A u_x + v_s|| <= eps_infeas (-c^T u_x)
 
+    ``equil`` (from ``equil.equilibrate``: ``D, E, sigma, rho``) runs the
+    iteration on the scaled data ``A^ = D A E``, ``b^ = sigma D b``,
+    ``c^ = rho E c``; every test above is then made on the original problem at
+    the point mapped back (``x = E x^ / sigma``, ``s = s^ / (sigma D)``,
+    ``y = D y^ / rho``; the certificate tests are invariant to the common
+    factors), and the point returned is the original one.  ``u``, ``v`` and the
+    trajectory stay in the scaled coordinates.
+
     Returns a dict with ``x, y, s, status, iters, pobj, dobj, pri, dual, gap,
     u, v, cg_steps``, the wall times ``t_setup`` / ``t_iter`` of the setup and
     of the iterations, and, if ``trajectory`` > 0, the first ``trajectory``
     iterates ``traj_u``/``traj_v``.
     """
-    op = A if isinstance(A, Operator) else Operator(A)
-    m, n = op.m, op.n
-    b = np.asarray(b, dtype=np.float64)
-    c = np.asarray(c, dtype=np.float64)
+    op0 = A if isinstance(A, Operator) else Operator(A)
+    m, n = op0.m, op0.n
+    b0 = np.asarray(b, dtype=np.float64)
+    c0 = np.asarray(c, dtype=np.float64)
+    if equil is None:
+        Dv, Ev, sigma, rho = np.ones(m), np.ones(n), 1.0, 1.0
+        op, b, c = op0, b0, c0
+    else:
+        Dv, Ev, sigma, rho = equil["D"], equil["E"], float(equil["sigma"]), float(equil["rho"])
+        op = equil_mod.ScaledOperator(op0, Dv, Ev)
+        b, c = sigma * Dv * b0, rho * Ev * c0
+    back = (op0, b0, c0, Dv, Ev, sigma, rho)
     if eps_infeas is None:
         eps_infeas = eps
     t0 = time.perf_counter()
@@ -210,26 +226,28 @@ def solve(A, b, c, cone, *, eps=1e-4, eps_infeas=None, alpha=1.5, max_iters=1000
             status = NUMERICAL
             break
         if it % check_interval == 0 or it == max_iters:
-            st, res = _check(op, b, c, u, v, n, m, eps, eps_infeas)
+            st, res = _check(back, u, v, n, m, eps, eps_infeas)
             if st is not None:
                 status = st
                 break
 
     t2 = time.perf_counter()
     tau = u[-1]
-    x = u[:n] / tau if tau > 0 else np.full(n, np.nan)
-    y = u[n:n + m] / tau if tau > 0 else np.full(m, np.nan)
-    s = v[n:n + m] / tau if tau > 0 else np.full(m, np.nan)
+    # the point in the original coordinates (identity maps without equil)
+    xo, yo, so = Ev * u[:n] / sigma, Dv * u[n:n + m] / rho, v[n:n + m] / (sigma * Dv)
+    x = xo / tau if tau > 0 else np.full(n, np.nan)
+    y = yo / tau if tau > 0 else np.full(m, np.nan)
+    s = so / tau if tau > 0 else np.full(m, np.nan)
     if status == INFEASIBLE:
-        d = -float(b @ u[n:n + m])
-        x, s, y = np.full(n, np.nan), np.full(m, np.nan), u[n:n + m] / d
+        d = -float(b0 @ yo)
+        x, s, y = np.full(n, np.nan), np.full(m, np.nan), yo / d
     elif status == UNBOUNDED:
-        d = -float(c @ u[:n])
-        x, s, y = u[:n] / d, v[n:n + m] / d, np.full(m, np.nan)
+        d = -float(c0 @ xo)
+        x, s, y = xo / d, so / d, np.full(m, np.nan)
     if status in (SOLVED, MAX_ITERS) and tau > 0:
-        res = residuals(op, b, c, x, y, s)
+        res = residuals(op0, b0, c0, x, y, s)
     out = {"x": x, "y": y, "s": s, "status": status, "iters": it,
-           "pobj": float(c @ x), "dobj": float(-(b @ y)),
+           "pobj": float(c0 @ x), "dobj": float(-(b0 @ y)),
            "pri": res[0], "dual": res[1], "gap": res[2],
            "u": u, "v": v, "cg_steps": cg_steps, "g_x": g_x, "g_y": g_y, "hg": hg,
            "t_setup": t1 - t0, "t_iter": t2 - t1}
@@ -239,9 +257,14 @@ def solve(A, b, c, cone, *, eps=1e-4, eps_infeas=None, alpha=1.5, max_iters=1000
     return out
 
 
-def _check(op, b, c, u, v, n, m, eps, eps_infeas):
+def _check(back, u, v, n, m, eps, eps_infeas):
+    """Termination and certificate tests on the original problem at the
+    point the iterate maps back to."""
+    op, b, c, Dv, Ev, sigma, rho = back
     tau = u[-1]
-    ux, uy, vs = u[:n], u[n:n + m], v[n:n + m]
+    ux = Ev * u[:n] / sigma
+    uy = Dv * u[n:n + m] / rho
+    vs = v[n:n + m] / (sigma * Dv)
     if tau > 0:
         res = residuals(op, b, c, ux / tau, uy / tau, vs / tau)
         if max(res) <= eps:
@@ -257,6 +280,15 @@ def _check(op, b, c, u, v, n, m, eps, eps_infeas):
     return None, res
 
 
-def problem_solve(prob, **kw):
-    """``solve`` on a generator problem dict (uses its operator tree)."""
-    return solve(prob["A"], prob["b"], prob["c"], prob["cone"], **kw)
+def problem_solve(prob, equilibrate=None, **kw):
+    """``solve`` on a generator problem dict (uses its operator tree).
+    ``equilibrate``: None, or a dict of ``equil.equilibrate`` keyword
+    arguments (``iters``, ``probes``, ``seed``) to scale the data first; the
+    scalings are returned under ``"equil"``."""
+    if equilibrate is None:
+        return solve(prob["A"], prob["b"], prob["c"], prob["cone"], **kw)
+    op = Operator(prob["A"])
+    eq = equil_mod.equilibrate(op, prob["cone"], prob["b"], prob["c"], **equilibrate)
+    out = solve(op, prob["b"], prob["c"], prob["cone"], equil=eq, **kw)
+    out["equil"] = eq
+    return out
