@@ -13,7 +13,9 @@ and ``E`` (columns) found with operator applications only.
   ``probes`` such products.
 * Ruiz-style step: ``D_i <- D_i / r_i^(1/4)``, ``E_j <- E_j / c_j^(1/4)`` (each
   row / column divided by the square root of its estimated norm), the
-  cumulative factors clipped to [1e-4, 1e4].  Rows of one second-order cone
+  cumulative factors clipped to [1e-4, 1e4]; a row or column whose
+  estimated squared norm is zero (an empty row of a sparse operator) keeps
+  its factor, as scaling it would only inflate ``b``.  Rows of one second-order cone
   share one factor (the block's mean squared norm): a positive multiple of
   the cone is the cone, a general diagonal scaling of it is not.
 * Then ``b^ = sigma D b`` and ``c^ = rho E c`` with
@@ -39,6 +41,7 @@ _M1 = np.uint64(0xBF58476D1CE4E5B9)
 _M2 = np.uint64(0x94D049BB133111EB)
 SCALE_MIN, SCALE_MAX = 1e-4, 1e4
 NORM_FLOOR = 1e-3
+ZERO_NORM2 = 1e-18
 
 
 def splitmix64_mix(z):
@@ -77,6 +80,12 @@ def soc_blocks(cone):
     return out
 
 
+def _step(r):
+    """Ruiz factor ``r^(-1/4)``; a row / column whose estimated squared norm
+    is zero (<= ZERO_NORM2) has nothing to equalise and keeps its scale."""
+    return np.where(r > ZERO_NORM2, 1.0 / np.sqrt(np.sqrt(np.maximum(r, ZERO_NORM2))), 1.0)
+
+
 def equilibrate(op, cone, b, c, iters=10, probes=8, seed=0x5EED):
     """Row / column scalings of the operator ``op`` (``mv``, ``rmv``, ``m``,
     ``n``) and the b / c factors; returns ``dict(D, E, sigma, rho)``."""
@@ -97,8 +106,8 @@ def equilibrate(op, cone, b, c, iters=10, probes=8, seed=0x5EED):
         cc /= probes
         for lo, hi in blocks:
             r[lo:hi] = r[lo:hi].mean()
-        D = np.clip(D / np.sqrt(np.sqrt(np.maximum(r, 1e-30))), SCALE_MIN, SCALE_MAX)
-        E = np.clip(E / np.sqrt(np.sqrt(np.maximum(cc, 1e-30))), SCALE_MIN, SCALE_MAX)
+        D = np.clip(D * _step(r), SCALE_MIN, SCALE_MAX)
+        E = np.clip(E * _step(cc), SCALE_MIN, SCALE_MAX)
     b = np.asarray(b, dtype=np.float64)
     c = np.asarray(c, dtype=np.float64)
     sigma = 1.0 / max(float(np.linalg.norm(D * b)), NORM_FLOOR)

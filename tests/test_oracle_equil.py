@@ -131,3 +131,18 @@ def test_planted_mistake_in_the_scaling_is_caught(monkeypatch):
     x_bad = eq["E"] * eqd["u"][:n] / tau          # sigma dropped
     pri_bad = scs.residuals(scs.Operator(prob["A"]), prob["b"], prob["c"], x_bad, eqd["y"], eqd["s"])[0]
     assert abs(eq["sigma"] - 1.0) > 1e-3 and pri_bad > 1e-3
+
+
+def test_empty_rows_keep_their_scale_and_the_lp_still_solves():
+    """A sparse LP with empty rows (120 x 60 at 3% density): the empty rows'
+    factor stays 1 (their estimated norm is exactly zero); scaling them up
+    instead would shrink sigma by orders of magnitude and stall the solve."""
+    prob = synth.lp(m_d=120, n_x=60, density=0.03, seed=170, storage="bf16")
+    rp = np.asarray(prob["A"]["parts"][0]["rowptr"])
+    empty = np.nonzero(np.diff(rp) == 0)[0]
+    assert empty.size > 0
+    op = scs.Operator(prob["A"])
+    eq = equil.equilibrate(op, prob["cone"], prob["b"], prob["c"], iters=10, probes=8)
+    np.testing.assert_array_equal(eq["D"][empty], 1.0)
+    out = scs.problem_solve(prob, eps=1e-4, max_iters=40000, linsys="cg", equilibrate=dict(iters=10, probes=8))
+    assert out["status"] == scs.SOLVED
