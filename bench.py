@@ -41,6 +41,7 @@ METRIC = "ADMM iters/s"
 # DRAM bytes (read + write) per k_conv1d launch on this workload from one ncu
 # capture (profiles/conv1d_large_deconvolution.md), valid only for the kernel
 # source it was taken on.
+EQUIL = dict(iters=10, probes=8, seed=0x5EED)
 CONV_NCU = {"traffic_bytes": 4029184 + 0, "src_sha256_16": "5eb743ed9e31474c"}
 FP32_LANES_PER_SM = 128
 L2_FLUSH_BYTES = 256 << 20
@@ -73,6 +74,10 @@ def parse():
     ap.add_argument("--engine", default="auto", choices=["auto", "graph", "team"],
                     help="solver program (auto: team engine for supported problems with small operator passes)")
     ap.add_argument("--tune-iters", type=int, default=20, help="lp-batch: ADMM iterations per autotuner candidate")
+    ap.add_argument("--equil", default="on", choices=["on", "off"],
+                    help="deconv / lp-batch: matrix-free equilibration of each problem (10 Ruiz steps x 8 probes)")
+    ap.add_argument("--cg-tol-rel", type=float, default=None,
+                    help="CG tolerance prefactor (default: 10 for the equilibrated large deconvolution, else the library's 1)")
     ap.add_argument("--host-loop", action="store_true",
                     help="launch the same kernels from the host instead of one CUDA graph per solve "
                          "(for profilers that cannot see kernels inside graph conditional nodes)")
@@ -144,11 +149,12 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ oracle
-def cpu_sample(prob, iters, label):
+def cpu_sample(prob, iters, label, equilibrate=None, cg_tol_rel=1.0):
     """The FP64 oracle (matrix-free, CG linear solves) on the same instance
     for a bounded number of ADMM iterations on the host cores."""
     from oracle import scs
-    r = scs.problem_solve(prob, eps=1e-4, max_iters=iters, linsys="cg")
+    r = scs.problem_solve(prob, eps=1e-4, max_iters=iters, linsys="cg", equilibrate=equilibrate,
+                          cg_tol_rel=cg_tol_rel)
     return {"value": r["iters"] / r["t_iter"], "unit": METRIC, "cores": 1, "kind": "oracle",
             "sample": (f"{r['iters']} ADMM iterations of the same {label} instance (FP64, matrix-free "
                        f"numpy.convolve operators, CG subspace solves; setup {r['t_setup']:.1f} s excluded, "
@@ -202,8 +208,15 @@ def run_lp_batch(args, B, ctx, torch):
     probs16 = [synth.lp(m_d=m, n_x=n, density=d, seed=sd, storage="bf16") for m, n, d, sd in sizes]
     t_gen = time.perf_counter() - t0
     nnz = sum(len(p["A"]["parts"][0]["col"]) for p in probs16)
-    st = B.settings(eps=1e-4, max_iters=args.lp_max_iters, engine=args.engine)
+    st = B.settings(eps=1e-4, max_iters=args.lp_max_iters, engine=args.engine,
+                    **({"cg_tol_rel": args.cg_tol_rel} if args.cg_tol_rel is not None else {}))
     Ps = [B.cone_problem_create(ctx, p) for p in probs16]
+    t_eq = 0.0
+    if args.equil == "on":
+        t0 = time.perf_counter()
+        for P in Ps:
+            B.equilibrate(P, **EQUIL)
+        t_eq = time.perf_counter() - t0
     tune = None
     if args.engine != "graph" and args.tune_iters > 0:
         tune = B.solve_batch_tune(Ps, iters=args.tune_iters)     # schedule search (not timed below)
@@ -231,6 +244,9 @@ def run_lp_batch(args, B, ctx, torch):
     # the same batch with FP32 operands (same schedule)
     probs32 = [synth.lp(m_d=m, n_x=n, density=d, seed=sd, storage="fp32") for m, n, d, sd in sizes]
     P32 = [B.cone_problem_create(ctx, p) for p in probs32]
+    if args.equil == "on":
+        for P in P32:
+            B.equilibrate(P, **EQUIL)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     infos32, *_ = B.solve_batch(P32, st)
@@ -259,6 +275,7 @@ def run_lp_batch(args, B, ctx, torch):
     return {"metric": "batched solves/s", "value": len(Ps) / t_batch, "unit": "solves/s",
             "workload": f"{len(Ps)} sparse LPs, m~U{{200..20000}}, n=m/2, density~U[0.5%,2%], total nnz {nnz}",
             "engine": args.engine, "autotune": tune, "roofline": hbm,
+            "equilibration": ({"per_problem": EQUIL, "seconds_total": t_eq} if args.equil == "on" else None),
             "batched_bf16": {"solves_per_s": len(Ps) / t_batch, "wall_s": t_batch, "p50_ms": pct(lat, 50),
                              "p99_ms": pct(lat, 99), "status": status,
                              "iters_p50": pct([i["iters"] for i in infos], 50),
@@ -443,6 +460,9 @@ def run_serve(args, B, ctx, torch):
     reqs = serve_trace(args, rng)
     st = B.settings(eps=1e-4, max_iters=args.lp_max_iters, engine=args.engine)
     Ps = [B.cone_problem_create(ctx, p) for _, p in reqs]
+    if args.equil == "on":
+        for P in Ps:
+            B.equilibrate(P, **EQUIL)
     srv = B.Server(ctx, int(args.budget_gb * (1 << 30)), args.slots)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -472,6 +492,7 @@ def run_serve(args, B, ctx, torch):
             "offered_rate": args.rate, "slots": args.slots, "budget_gb": args.budget_gb,
             "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99), "wall_s": t_all, "status": status,
             "engine": args.engine, "gpu_launches": sum(r[0]["kernel_launches"] for r in results),
+            "equilibration": EQUIL if args.equil == "on" else None,
             "alone_equals_mix_bitwise": same}
 
 
@@ -514,6 +535,11 @@ def main():
         return
 
     W = WORKLOAD_SMALL if small else WORKLOAD
+    eq = args.equil == "on"
+    # CG prefactor per workload (measured): 10 on the equilibrated n=1e6
+    # deconvolution (1280 iterations / 0.69 s to 1e-4 vs 1980 / 3.3 s at 1),
+    # 1 on the small one (750 iterations vs 2090 at 10)
+    cg_rel = args.cg_tol_rel if args.cg_tol_rel is not None else (10.0 if (eq and not small) else 1.0)
     prob = synth.deconv(**{**W, "seed": W["seed"] + rank})
     n, m = prob["A"]["n"], prob["A"]["m"]
     # a dedicated (non-default) stream: the library launches on it and the
@@ -522,13 +548,15 @@ def main():
     torch.cuda.set_stream(stream)
     ctx = B.Context(local, stream.cuda_stream)
     P = B.cone_problem_create(ctx, prob)
+    if eq:
+        B.equilibrate(P, **EQUIL)
     dev = torch.device("cuda", local)
     xo = torch.empty(n, dtype=torch.float64, device=dev)
     yo = torch.empty(m, dtype=torch.float64, device=dev)
     so = torch.empty(m, dtype=torch.float64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     st = B.settings(max_iters=args.iters_per_step, eps=1e-4, host_loop=1 if args.host_loop else 0,
-                    engine="graph" if args.host_loop else args.engine)
+                    engine="graph" if args.host_loop else args.engine, cg_tol_rel=cg_rel)
 
     def step():
         return B.solve(P, st, x=xo, y=yo, s=so)[0]
@@ -641,6 +669,8 @@ def main():
             t0 = time.perf_counter()
             ops = B.build_operator(ctx, prob["A"])
             Pk = B.Problem(ctx, ops, bh.numpy(), ch.numpy(), prob["cone"])
+            if eq:
+                B.equilibrate(Pk, **EQUIL)
             info = B.solve(Pk, st, x=xh.numpy(), y=yh.numpy(), s=sh.numpy())[0]
             torch.cuda.synchronize()
             e2e_t += time.perf_counter() - t0
@@ -650,13 +680,13 @@ def main():
         e2e = {"value": e2e_iters / e2e_t, "unit": "iters/s",
                "h2d_bytes_per_step": int(4 * L + 8 * m + 8 * n),
                "d2h_bytes_per_step": int(8 * (n + 2 * m)),
-               "includes": "operator + problem creation from pinned host buffers, setup (g = M^-1 h), "
-                           "solve, x/y/s copied to host"}
+               "includes": "operator + problem creation from pinned host buffers, "
+                           + ("equilibration, " if eq else "") + "setup (g = M^-1 h), solve, x/y/s copied to host"}
 
     # ---- one-off time to 1e-4
     ttc = None
     if args.ttc_max_iters > 0:
-        st2 = B.settings(max_iters=args.ttc_max_iters, eps=1e-4, engine=st.engine)
+        st2 = B.settings(max_iters=args.ttc_max_iters, eps=1e-4, engine=st.engine, cg_tol_rel=cg_rel)
         e0.record(stream)
         info = B.solve(P, st2, x=xo, y=yo, s=so)[0]
         e1.record(stream)
@@ -667,7 +697,9 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu:
-        cpu = cpu_sample(prob, max(args.cpu_iters, 20000) if small else args.cpu_iters, "n=1000" if small else "n=1e6")
+        cpu = cpu_sample(prob, max(args.cpu_iters, 20000) if small else args.cpu_iters,
+                         "n=1000" if small else "n=1e6 (unequilibrated: the oracle's probes would take minutes)",
+                         equilibrate=EQUIL if (eq and small) else None, cg_tol_rel=cg_rel)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
@@ -678,6 +710,9 @@ def main():
                                    "eps 1e-4 checked every 10 iterations",
                            "l2": "flushed between steps (256 MB write)",
                            "precision": "f32 vectors and operator, f64 reductions/norms/tau/kappa",
+                           "equilibration": (f"matrix-free, {EQUIL['iters']} Ruiz steps x {EQUIL['probes']} sign probes"
+                                             if eq else "none"),
+                           "cg_tol": f"max(1e-9, {cg_rel:g} ||rhs|| (k+1)^-1.5)",
                            "engine": ("team (one persistent launch per solve)" if team else "graph (one CUDA graph per solve)"),
                            "parallelism": f"replicas x{world}"},
                 "iters_per_step": it_total / max(args.steps * world, 1),

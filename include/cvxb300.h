@@ -303,6 +303,24 @@ cf_err solve(cf_problem* p, const cf_settings* settings, double* x, double* y, d
 cf_err solve_batch(cf_problem* const* probs, int32_t count, const cf_settings* settings,
                    double* const* xs, double* const* ys, double* const* ss, cf_info* infos);
 
+/* Matrix-free data equilibration (Section 3: forward and adjoint
+ * evaluations suffice to precondition a problem, after stochastic matrix-free
+ * equilibration).  Finds positive diagonal scalings D (rows; one factor per
+ * second-order cone block) and E (columns) with `iters` Ruiz steps, each
+ * estimating the squared row and column norms of D A E from `probes` random
+ * sign vectors (SplitMix64 of `seed`, counter-based); then scales b and c to
+ * unit norm (sigma, rho).  Later solves iterate on D A E, sigma D b, rho E c
+ * and stop on, and return, the original problem's residuals and point
+ * (warm-start / uv vectors are in the scaled coordinates).  The problem's
+ * setup is redone at its next solve.  iters in [0, 100], probes in
+ * [1, 1024]; CF_E_STATE if the problem is already equilibrated. */
+cf_err cone_problem_equilibrate(cf_problem* p, int32_t iters, int32_t probes, uint64_t seed);
+
+/* The equilibration of a problem: D (m floats), E (n floats) -- host or
+ * device buffers, may be NULL -- and sigma, rho (all 1 without
+ * equilibration). */
+cf_err cf_problem_scaling(const cf_problem* p, float* D, float* E, double* sigma, double* rho);
+
 /* The team engine's view of a problem: *supported = 1 when the team engine
  * can run it (else 0, and why -- when not NULL -- receives the reason,
  * NUL-terminated, at most why_len bytes); *pass_bytes = the bytes (and

@@ -112,6 +112,8 @@ _sig = {
     "cf_ctx_set_schedule": (C.c_int, [P, C.POINTER(cf_schedule)]),
     "cf_problem_team_info": (C.c_int, [P, C.POINTER(C.c_int32), C.POINTER(C.c_double), C.c_char_p,
                                        C.c_size_t]),
+    "cone_problem_equilibrate": (C.c_int, [P, C.c_int32, C.c_int32, C.c_uint64]),
+    "cf_problem_scaling": (C.c_int, [P, P, P, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "cg_solve": (C.c_int, [P, C.c_double, P, P, C.c_int32, C.c_double, C.POINTER(C.c_int32),
                            C.POINTER(C.c_double)]),
     "serve_create": (C.c_int, [P, C.c_size_t, C.c_int32, PP]),
@@ -410,6 +412,20 @@ def solve_batch(problems, st=None):
     infos = (cf_info * k)()
     check(lib.solve_batch(hs, k, C.byref(st) if st is not None else None, px, py, ps, infos), "solve_batch")
     return [i.as_dict() for i in infos], xs, ys, ss
+
+
+def equilibrate(problem, iters=10, probes=8, seed=0x5EED):
+    """cone_problem_equilibrate: scale the problem's data (see the header)."""
+    check(lib.cone_problem_equilibrate(problem.h, int(iters), int(probes), int(seed)), "cone_problem_equilibrate")
+
+
+def scaling(problem):
+    """(D, E, sigma, rho) of a problem's equilibration."""
+    D = np.empty(problem.m, dtype=np.float32)
+    E = np.empty(problem.n, dtype=np.float32)
+    sg, rh = C.c_double(), C.c_double()
+    check(lib.cf_problem_scaling(problem.h, _ptr(D), _ptr(E), C.byref(sg), C.byref(rh)), "cf_problem_scaling")
+    return D, E, sg.value, rh.value
 
 
 def team_info(problem):

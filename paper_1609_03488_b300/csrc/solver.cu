@@ -534,38 +534,50 @@ __global__ void k_apply(Ctl* c, int64_t n, int64_t m, int64_t z, int64_t l, int 
 }
 
 // ------------------------------------------------------------ termination
-// With cm = A u_x and cn = A^T u_y:
-//   S0 = ||cm + v_s - b tau||^2   S1 = ||cm + v_s||^2   S2 = b^T u_y
-//   S3 = ||cn + c tau||^2         S4 = ||cn||^2         S5 = c^T u_x
-// x = u_x / tau, y = u_y / tau, s = v_s / tau give
-//   pri = sqrt(S0)/tau/(1+||b||), dual = sqrt(S3)/tau/(1+||c||),
-//   gap = |S5 + S2|/tau / (1 + |S5|/tau + |S2|/tau).
+// With cm = A u_x and cn = A^T u_y (A the solver's, possibly equilibrated,
+// operator), weights w_i = 1/D_i on rows and 1/E_j on columns (1 without
+// equilibration):
+//   S0 = ||w (cm + v_s - b tau)||^2   S1 = ||w (cm + v_s)||^2   S2 = b^T u_y
+//   S3 = ||w (cn + c tau)||^2         S4 = ||w cn||^2         S5 = c^T u_x
+// The original problem's point is x = E u_x / (sigma tau), y = D u_y / (rho tau),
+// s = v_s / (sigma D tau), so
+//   pri = sqrt(S0)/(sigma tau)/(1+||b||), dual = sqrt(S3)/(rho tau)/(1+||c||),
+//   c^T x = S5/(rho sigma tau), b^T y = S2/(rho sigma tau),
+// and the certificates (invariant to the common factors) read
+//   infeasible: -S2 > 0 and sigma sqrt(S4) <= eps_infeas (-S2),
+//   unbounded:  -S5 > 0 and rho sqrt(S1) <= eps_infeas (-S5).
 __global__ void k_resid(Ctl* c, int64_t n, int64_t m, const float* __restrict__ cm,
                         const float* __restrict__ cn, const float* __restrict__ ux,
                         const float* __restrict__ uy, const float* __restrict__ vs,
-                        const float* __restrict__ bf, const float* __restrict__ cf, double* part,
+                        const float* __restrict__ bf, const float* __restrict__ cf,
+                        const float* __restrict__ dinv, const float* __restrict__ einv, double* part,
                         cudaGraphConditionalHandle h_outer, int in_graph) {
   const double tau = c->tau;
   const float tf = (float)tau;
   Acc2 s0, s1, s2, s3, s4, s5;
   GRID_STRIDE(i, m) {
+    const float w = dinv ? dinv[i] : 1.f;
     const float e = cm[i] + vs[i];
-    const float d = fmaf(-bf[i], tf, e);
+    const float d = w * fmaf(-bf[i], tf, e);
+    const float we = w * e;
     s0.add_prod(d, d);
-    s1.add_prod(e, e);
+    s1.add_prod(we, we);
     s2.add_prod(bf[i], uy[i]);
   }
   GRID_STRIDE(i, n) {
-    const float d = fmaf(cf[i], tf, cn[i]);
+    const float w = einv ? einv[i] : 1.f;
+    const float d = w * fmaf(cf[i], tf, cn[i]);
+    const float wc = w * cn[i];
     s3.add_prod(d, d);
-    s4.add_prod(cn[i], cn[i]);
+    s4.add_prod(wc, wc);
     s5.add_prod(cf[i], ux[i]);
   }
   double v[6] = {s0.value(), s1.value(), s2.value(), s3.value(), s4.value(), s5.value()};
   if (grid_sum<6>(v, part, &c->red_count) && threadIdx.x == 0) {
+    const double sig = c->sigma, rho = c->rho;
     c->checks += 1;
-    c->cx = v[5];
-    c->by = v[2];
+    c->cx = v[5] / (rho * sig);
+    c->by = v[2] / (rho * sig);
     bool bad = false;
     for (int j = 0; j < 6; ++j) bad |= !isfinite(v[j]);
     if (bad || !isfinite(tau) || !isfinite(c->kappa)) {
@@ -573,9 +585,9 @@ __global__ void k_resid(Ctl* c, int64_t n, int64_t m, const float* __restrict__ 
       c->stop = 1;
     } else {
       if (tau > 0.0) {
-        const double pri = sqrt(v[0]) / tau / (1.0 + c->nb);
-        const double dual = sqrt(v[3]) / tau / (1.0 + c->nc);
-        const double cx = v[5] / tau, by = v[2] / tau;
+        const double pri = sqrt(v[0]) / (sig * tau) / (1.0 + c->nb);
+        const double dual = sqrt(v[3]) / (rho * tau) / (1.0 + c->nc);
+        const double cx = c->cx / tau, by = c->by / tau;
         const double gap = fabs(cx + by) / (1.0 + fabs(cx) + fabs(by));
         c->pri = pri;
         c->dual = dual;
@@ -586,10 +598,10 @@ __global__ void k_resid(Ctl* c, int64_t n, int64_t m, const float* __restrict__ 
         }
       }
       if (!c->stop) {
-        if (-v[2] > 0.0 && sqrt(v[4]) <= c->st.eps_inf * (-v[2])) {
+        if (-v[2] > 0.0 && sig * sqrt(v[4]) <= c->st.eps_inf * (-v[2])) {
           c->status = CF_INFEASIBLE;
           c->stop = 1;
-        } else if (-v[5] > 0.0 && sqrt(v[1]) <= c->st.eps_inf * (-v[5])) {
+        } else if (-v[5] > 0.0 && rho * sqrt(v[1]) <= c->st.eps_inf * (-v[5])) {
           c->status = CF_UNBOUNDED;
           c->stop = 1;
         }
@@ -633,9 +645,14 @@ __global__ void k_setup_fin(Ctl* c, int64_t n, int64_t m, const float* __restric
 }
 
 // ------------------------------------------------------------ outputs
+// The original problem's point (see k_resid): x = E u_x / sigma, y = D u_y / rho,
+// s = v_s / (sigma D), divided by tau, or normalised as a certificate
+// (b^T y = -1, or c^T x = -1 with s scaled alike).  c->cx, c->by hold
+// c^T x, b^T y of the undivided point.
 __global__ void k_output(const Ctl* c, int64_t n, int64_t m, const float* __restrict__ ux,
                          const float* __restrict__ uy, const float* __restrict__ vs,
-                         double* __restrict__ out) {
+                         const float* __restrict__ d, const float* __restrict__ e,
+                         const float* __restrict__ dinv, double* __restrict__ out) {
   const int st = c->status;
   const double tau = c->tau;
   double sx, sy, ss;  // multipliers for x, y, s
@@ -648,10 +665,11 @@ __global__ void k_output(const Ctl* c, int64_t n, int64_t m, const float* __rest
   } else {
     sx = sy = ss = NAN;
   }
-  GRID_STRIDE(i, n) out[i] = (double)ux[i] * sx;
+  const double fx = sx / c->sigma, fy = sy / c->rho, fs = ss / c->sigma;
+  GRID_STRIDE(i, n) out[i] = (double)ux[i] * (e ? (double)e[i] : 1.0) * fx;
   GRID_STRIDE(i, m) {
-    out[n + i] = (double)uy[i] * sy;
-    out[n + m + i] = (double)vs[i] * ss;
+    out[n + i] = (double)uy[i] * (d ? (double)d[i] : 1.0) * fy;
+    out[n + m + i] = (double)vs[i] * (dinv ? (double)dinv[i] : 1.0) * fs;
   }
 }
 
@@ -824,7 +842,8 @@ void emit_check(cf_problem* P, const Conds& cd, cudaStream_t s) {
   op_apply(P->A, false, 1.f, P->ux, P->cm, false, P->ws, s);
   op_apply(P->A, true, 1.f, P->uy, P->cn, false, P->ws, s);
   k_resid<<<red_grid(std::max(n, m)), kThreads, 0, s>>>(P->ctl, n, m, P->cm, P->cn, P->ux, P->uy, P->vs,
-                                                        P->bf, P->cf, P->part, cd.outer, cd.in_graph);
+                                                        P->bf, P->cf, P->eq_dinv, P->eq_einv, P->part, cd.outer,
+                                                        cd.in_graph);
 }
 
 // exact A z_x and G z_x (every kRefreshInterval iterations)
@@ -1043,8 +1062,12 @@ cf_err ensure_state(cf_problem* P) {
   CF_CUDA(cudaStreamSynchronize(P->stream));
   P->ctl_host->nb = P->nb;
   P->ctl_host->nc = P->nc;
+  P->ctl_host->sigma = P->sigma;
+  P->ctl_host->rho = P->rho;
   CF_CUDA(cudaMemcpy(&P->ctl->nb, &P->nb, sizeof(double), cudaMemcpyHostToDevice));
   CF_CUDA(cudaMemcpy(&P->ctl->nc, &P->nc, sizeof(double), cudaMemcpyHostToDevice));
+  CF_CUDA(cudaMemcpy(&P->ctl->sigma, &P->sigma, sizeof(double), cudaMemcpyHostToDevice));
+  CF_CUDA(cudaMemcpy(&P->ctl->rho, &P->rho, sizeof(double), cudaMemcpyHostToDevice));
   P->setup_done = false;
   return CF_OK;
 }
@@ -1168,7 +1191,8 @@ cf_err solve_launch(cf_problem* P, const cf_settings* st_in, double* x, double* 
   P->uv_out = uv_out;
   if (x || y || s) {
     k_output<<<grid_for(std::max(P->n, P->m)), kThreads, 0, P->stream>>>(P->ctl, P->n, P->m, P->ux, P->uy,
-                                                                       P->vs, P->out_dev);
+                                                                       P->vs, P->eq_d, P->eq_e, P->eq_dinv,
+                                                                       P->out_dev);
     CF_CUDA(cudaGetLastError());
   }
   if (uv_out) {
@@ -1439,6 +1463,8 @@ void cf_problem_destroy(cf_problem* P) {
   if (P->stream) cudaStreamSynchronize(P->stream);
   release_state(P);
   team::release(P);
+  if (P->eq) cudaFree(P->eq);
+  if (P->A_orig) cf_op_destroy(P->A_orig);
   if (P->bf) cudaFree(P->bf);  // base of the persistent block
   if (P->ctl_host) cudaFreeHost(P->ctl_host);
   if (P->flags_host) cudaFreeHost(P->flags_host);

@@ -20,7 +20,8 @@ struct Settings {
 struct Ctl {
   Settings st;
   double lam;            // Gram shift: CG solves (lam I + A^T A) z = rhs
-  double hg, nb, nc;     // h^T g, ||b||, ||c||
+  double hg, nb, nc;     // h^T g, ||b||, ||c|| (original data)
+  double sigma, rho;     // equilibration: b^ = sigma D b, c^ = rho E c (1 without)
   double tau, kappa, w_tau, ut_tau;
   double rr, tol2, alpha_cg, beta_cg;
   double pri, dual, gap, cx, by;
@@ -84,6 +85,12 @@ struct cf_problem {
   int setup_sig = 0;              // program that computed g: 0 none, 1 graph, >= 2 team
   int last_engine = 0;            // CF_ENGINE_GRAPH or CF_ENGINE_TEAM
   int64_t team_launches = 0;      // kernels attributed to this problem's last solve
+  // equilibration (cone_problem_equilibrate): the solver's A is then
+  // diag(D) A_orig diag(E), bf / cf hold sigma D b / rho E c
+  float* eq = nullptr;            // one allocation: D, 1/D, E, 1/E
+  float *eq_d = nullptr, *eq_dinv = nullptr, *eq_e = nullptr, *eq_einv = nullptr;
+  double sigma = 1.0, rho = 1.0;
+  cf_op* A_orig = nullptr;
 };
 
 namespace cf {

@@ -58,6 +58,8 @@ struct __align__(16) Prob {
   float *ux, *uy, *vs, *zx, *rhs, *r, *p, *q, *gx, *gy, *wy, *t, *zy, *cm, *cn, *gz, *az, *scratch;
   const double* warm;
   double *out, *uv;
+  const float *eq_d, *eq_e, *eq_dinv, *eq_einv;  // equilibration (null: none)
+  double sigma, rho;
 };
 static_assert(sizeof(Prob) % 16 == 0, "Prob is copied as 16-byte words");
 
@@ -208,9 +210,10 @@ __device__ void team_sum(const Team& tm, Shared& sh, int& ph, Acc2 (&a)[NV], F&&
 __device__ void term_diag(const Team& tm, const Term& t, const float* x, float* y) {
   const float* d = (const float*)t.a;
   for (int64_t i = tm.tt; i < t.rows; i += tm.TT) {
-    const float xv = x[t.xo + i];
+    const float xv = t.sin ? t.sin[i] * x[t.xo + i] : x[t.xo + i];
+    const float a = t.sout ? t.alpha * t.sout[i] : t.alpha;
     float* yp = y + t.yo + i;
-    *yp = fmaf(t.alpha, d ? __ldg(d + i) * xv : xv, t.acc ? *yp : 0.f);
+    *yp = fmaf(a, d ? __ldg(d + i) * xv : xv, t.acc ? *yp : 0.f);
   }
 }
 
@@ -246,10 +249,12 @@ __device__ void term_csr(const Team& tm, const Term& t, const float* x, float* y
   const bool staged = t.cols <= kCsrStageFloats;
   if (staged) {
     __syncthreads();  // earlier users of the shared buffer are done
-    for (int64_t i = threadIdx.x; i < t.cols; i += blockDim.x) dsm[i] = x[t.xo + i];
+    for (int64_t i = threadIdx.x; i < t.cols; i += blockDim.x)
+      dsm[i] = t.sin ? t.sin[i] * x[t.xo + i] : x[t.xo + i];
     __syncthreads();
   }
   const float* xs = staged ? dsm : x + t.xo;
+  const float* sx = staged ? nullptr : t.sin;  // input scale still to apply
   const int lane = threadIdx.x & 31;
   const int rpw = 32 / L;
   const int sub = lane / L, l = lane & (L - 1);
@@ -293,7 +298,7 @@ __device__ void term_csr(const Team& tm, const Term& t, const float* x, float* y
 #pragma unroll
           for (int u = 0; u < 8; ++u) {
             const int32_t idx = kk + u;
-            if (idx >= b && idx < e) acc[u & 3] = fmaf(v8[u], xs[c8[u]], acc[u & 3]);
+            if (idx >= b && idx < e) acc[u & 3] = fmaf(v8[u], sx ? sx[c8[u]] * xs[c8[u]] : xs[c8[u]], acc[u & 3]);
           }
         }
       }
@@ -301,7 +306,7 @@ __device__ void term_csr(const Team& tm, const Term& t, const float* x, float* y
     float s = (acc[0] + acc[1]) + (acc[2] + acc[3]);
     for (int o = L >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (l == 0 && r < t.rows) {
-      const float out = t.alpha * s;
+      const float out = (t.sout ? t.alpha * t.sout[r] : t.alpha) * s;
       float* yp = y + t.yo + r;
       *yp = t.acc ? *yp + out : out;
     }
@@ -321,7 +326,8 @@ __device__ void term_dense_n(const Team& tm, const Term& t, const float* x, floa
   const int64_t n = t.cols, m = t.rows, lda = t.lda;
   const int64_t npad = (n + 15) & ~(int64_t)15;
   __syncthreads();  // earlier users of the shared buffer are done
-  for (int64_t i = threadIdx.x; i < npad; i += blockDim.x) dsm[i] = i < n ? x[t.xo + i] : 0.f;
+  for (int64_t i = threadIdx.x; i < npad; i += blockDim.x)
+    dsm[i] = i < n ? (t.sin ? t.sin[i] * x[t.xo + i] : x[t.xo + i]) : 0.f;
   __syncthreads();
   const TS* A = (const TS*)t.a;
   const int lane = threadIdx.x & 31;
@@ -365,7 +371,7 @@ __device__ void term_dense_n(const Team& tm, const Term& t, const float* x, floa
       for (int rr = 1; rr < RW; ++rr)
         if (lane == rr) s = acc[rr];
       const int64_t r = r0 + lane;
-      float out = t.alpha * (t.scale ? __ldg(t.scale + r) * s : s);
+      float out = (t.sout ? t.alpha * t.sout[r] : t.alpha) * (t.scale ? __ldg(t.scale + r) * s : s);
       float* yp = y + t.yo + r;
       *yp = t.acc ? *yp + out : out;
     }
@@ -404,6 +410,7 @@ __device__ void term_dense_t(const Team& tm, const Term& t, const float* x, floa
           u[j] = __ldg(reinterpret_cast<const uint4*>(A + (i + j) * lda + col0));
           xi[j] = x[t.xo + i + j];
           if (t.scale) xi[j] *= __ldg(t.scale + i + j);
+          if (t.sin) xi[j] *= t.sin[i + j];
         }
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
@@ -417,6 +424,7 @@ __device__ void term_dense_t(const Team& tm, const Term& t, const float* x, floa
         const uint4 u = __ldg(reinterpret_cast<const uint4*>(A + i * lda + col0));
         float xi = x[t.xo + i];
         if (t.scale) xi *= __ldg(t.scale + i);
+        if (t.sin) xi *= t.sin[i];
         float f[V];
         Vec<TS>::unpack(u, f);
 #pragma unroll
@@ -428,7 +436,7 @@ __device__ void term_dense_t(const Team& tm, const Term& t, const float* x, floa
         if (j < nout) {
           if (R == 1) {
             float* yp = y + t.yo + j;
-            const float out = t.alpha * acc[q];
+            const float out = (t.sout ? t.alpha * t.sout[j] : t.alpha) * acc[q];
             *yp = t.acc ? *yp + out : out;
           } else {
             scratch[g * nout + j] = acc[q];
@@ -443,7 +451,7 @@ __device__ void term_dense_t(const Team& tm, const Term& t, const float* x, floa
       float s = 0.f;
       for (int64_t g = 0; g < R; ++g) s += scratch[g * nout + j];
       float* yp = y + t.yo + j;
-      const float out = t.alpha * s;
+      const float out = (t.sout ? t.alpha * t.sout[j] : t.alpha) * s;
       *yp = t.acc ? *yp + out : out;
     }
   }
@@ -472,7 +480,7 @@ __device__ void term_conv(const Team& tm, const Term& t, const float* x, float* 
     // thread reaches index (cnt - 1) + Lp + kConvR - 2 at most
     for (int64_t j = threadIdx.x; j < cnt + Lp + kConvR; j += blockDim.x) {
       const int64_t g = base + j;
-      in_s[j] = (g >= 0 && g < n_in) ? x[t.xo + g] : 0.f;
+      in_s[j] = (g >= 0 && g < n_in) ? (t.sin ? t.sin[g] * x[t.xo + g] : x[t.xo + g]) : 0.f;
     }
     __syncthreads();
     const float4* w4 = reinterpret_cast<const float4*>(w_s);
@@ -501,7 +509,7 @@ __device__ void term_conv(const Team& tm, const Term& t, const float* x, float* 
 #pragma unroll
       for (int r = 0; r < kConvR; ++r) {
         if (ob + r < cnt) {
-          const float out = t.alpha * acc[r];
+          const float out = (t.sout ? t.alpha * t.sout[o0 + ob + r] : t.alpha) * acc[r];
           float* yp = y + t.yo + o0 + ob + r;
           *yp = t.acc ? *yp + out : out;
         }
@@ -926,30 +934,35 @@ __device__ void solve_one(const Team& tm, Shared& sh, float* dsm) {
       apply<MaxT>(tm, P.fwd, P.nfwd, P.ux, P.cm, P.scratch, dsm, P.lanes);
       apply<MaxT>(tm, P.adj, P.nadj, P.uy, P.cn, P.scratch, dsm, P.lanes);
       tsync(tm);
+      // sums of k_resid (solver.cu): weighted by 1/D, 1/E when equilibrated
       const float tf = sh.sc.tau_f;
       Acc2 s[6];
       each(tm, m, [&](int64_t i) {
         const float bi = __ldg(P.bf + i);
+        const float w = P.eq_dinv ? P.eq_dinv[i] : 1.f;
         const float e = P.cm[i] + P.vs[i];
-        const float d = fmaf(-bi, tf, e);
+        const float d = w * fmaf(-bi, tf, e);
+        const float we = w * e;
         s[0].add_prod(d, d);
-        s[1].add_prod(e, e);
+        s[1].add_prod(we, we);
         s[2].add_prod(bi, P.uy[i]);
       });
       each(tm, n, [&](int64_t i) {
         const float ci = __ldg(P.cf + i), cn = P.cn[i];
-        const float d = fmaf(ci, tf, cn);
+        const float w = P.eq_einv ? P.eq_einv[i] : 1.f;
+        const float d = w * fmaf(ci, tf, cn);
+        const float wc = w * cn;
         s[3].add_prod(d, d);
-        s[4].add_prod(cn, cn);
+        s[4].add_prod(wc, wc);
         s[5].add_prod(ci, P.ux[i]);
       });
       team_sum<6>(tm, sh, ph, s, [&](const double* v) {
         Scal& c = sh.sc;
         const Settings& st2 = sh.P.st;
-        const double tau = c.tau;
+        const double tau = c.tau, sig = sh.P.sigma, rho = sh.P.rho;
         ++c.checks;
-        c.cx = v[5];
-        c.by = v[2];
+        c.cx = v[5] / (rho * sig);
+        c.by = v[2] / (rho * sig);
         bool bad = false;
         for (int j = 0; j < 6; ++j) bad |= !isfinite(v[j]);
         if (bad) {
@@ -957,9 +970,9 @@ __device__ void solve_one(const Team& tm, Shared& sh, float* dsm) {
           c.stop = 1;
         } else {
           if (tau > 0.0) {
-            c.pri = sqrt(v[0]) / tau / (1.0 + sh.P.nb);
-            c.dual = sqrt(v[3]) / tau / (1.0 + sh.P.nc);
-            const double cxt = v[5] / tau, byt = v[2] / tau;
+            c.pri = sqrt(v[0]) / (sig * tau) / (1.0 + sh.P.nb);
+            c.dual = sqrt(v[3]) / (rho * tau) / (1.0 + sh.P.nc);
+            const double cxt = c.cx / tau, byt = c.by / tau;
             c.gap = fabs(cxt + byt) / (1.0 + fabs(cxt) + fabs(byt));
             if (c.pri <= st2.eps && c.dual <= st2.eps && c.gap <= st2.eps) {
               c.status = CF_SOLVED;
@@ -967,10 +980,10 @@ __device__ void solve_one(const Team& tm, Shared& sh, float* dsm) {
             }
           }
           if (!c.stop) {
-            if (-v[2] > 0.0 && sqrt(v[4]) <= st2.eps_inf * (-v[2])) {
+            if (-v[2] > 0.0 && sig * sqrt(v[4]) <= st2.eps_inf * (-v[2])) {
               c.status = CF_INFEASIBLE;
               c.stop = 1;
-            } else if (-v[5] > 0.0 && sqrt(v[1]) <= st2.eps_inf * (-v[5])) {
+            } else if (-v[5] > 0.0 && rho * sqrt(v[1]) <= st2.eps_inf * (-v[5])) {
               c.status = CF_UNBOUNDED;
               c.stop = 1;
             }
@@ -1009,11 +1022,12 @@ __device__ void solve_one(const Team& tm, Shared& sh, float* dsm) {
   __syncthreads();
   if (!P.tune) {
     if (P.want_out) {
-      const double sx = sh.sc.sx, sy = sh.sc.sy, ss = sh.sc.ss;
-      each(tm, n, [&](int64_t i) { P.out[i] = (double)P.ux[i] * sx; });
+      // the original problem's point (see k_output in solver.cu)
+      const double sx = sh.sc.sx / P.sigma, sy = sh.sc.sy / P.rho, ss = sh.sc.ss / P.sigma;
+      each(tm, n, [&](int64_t i) { P.out[i] = (double)P.ux[i] * (P.eq_e ? (double)P.eq_e[i] : 1.0) * sx; });
       each(tm, m, [&](int64_t i) {
-        P.out[n + i] = (double)P.uy[i] * sy;
-        P.out[n + m + i] = (double)P.vs[i] * ss;
+        P.out[n + i] = (double)P.uy[i] * (P.eq_d ? (double)P.eq_d[i] : 1.0) * sy;
+        P.out[n + m + i] = (double)P.vs[i] * (P.eq_dinv ? (double)P.eq_dinv[i] : 1.0) * ss;
       });
     }
     if (P.want_uv) {
@@ -1264,15 +1278,34 @@ cf_err plan_problem(cf_problem* P) {
     pl.why = "more than " + std::to_string(kMaxSeg) + " second-order cones";
     return CF_OK;
   }
-  if (!flatten(P->A, false, 1.f, 0, 0, false, pl.fwd, &why) ||
-      !flatten(P->A, true, 1.f, 0, 0, false, pl.adj, &why) ||
-      !flatten(P->A, true, -1.f, 0, 0, true, pl.adj_m, &why)) {
+  // an equilibrated operator diag(D) A diag(E): A's terms with the scalings
+  // folded in (inputs scaled by E forward / D adjoint, outputs by D / E)
+  const cf_op* core = P->A;
+  const float *dsc = nullptr, *esc = nullptr;
+  if (P->A->kind == OP_PRODUCT && P->A->parts.size() == 3 && P->A->parts[0]->kind == OP_DIAG &&
+      P->A->parts[2]->kind == OP_DIAG) {
+    core = P->A->parts[1];
+    dsc = P->A->parts[0]->d;
+    esc = P->A->parts[2]->d;
+  }
+  auto scale = [](std::vector<Term>& ts, const float* in, const float* out) {
+    for (Term& t : ts) {
+      t.sin = in ? in + t.xo : nullptr;
+      t.sout = out ? out + t.yo : nullptr;
+    }
+  };
+  if (!flatten(core, false, 1.f, 0, 0, false, pl.fwd, &why) ||
+      !flatten(core, true, 1.f, 0, 0, false, pl.adj, &why) ||
+      !flatten(core, true, -1.f, 0, 0, true, pl.adj_m, &why)) {
     pl.fwd.clear();
     pl.adj.clear();
     pl.adj_m.clear();
     pl.why = why;
     return CF_OK;
   }
+  scale(pl.fwd, esc, dsc);
+  scale(pl.adj, dsc, esc);
+  scale(pl.adj_m, dsc, esc);
   mark_syncs(pl.fwd);
   mark_syncs(pl.adj);
   mark_syncs(pl.adj_m);
@@ -1392,6 +1425,12 @@ void fill_prob(cf_problem* P, const cf_schedule& s, bool do_setup, bool tune, Pr
   o->warm = P->warm_dev;
   o->out = P->out_dev;
   o->uv = P->uv_dev;
+  o->eq_d = P->eq_d;
+  o->eq_e = P->eq_e;
+  o->eq_dinv = P->eq_dinv;
+  o->eq_einv = P->eq_einv;
+  o->sigma = P->sigma;
+  o->rho = P->rho;
 }
 
 struct Launch {

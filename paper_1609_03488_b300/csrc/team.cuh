@@ -22,7 +22,7 @@ constexpr int kCsrStageFloats = 40960; // CSR input staged in shared memory up t
 
 enum TermKind : int32_t { T_FILL = 0, T_DIAG = 1, T_CSR = 2, T_DENSE_N = 3, T_DENSE_T = 4, T_CONV = 5 };
 
-// One leaf application y[yo : yo + rows] (+)= alpha * leaf(x[xo : xo + cols]).
+// One leaf application y[yo : yo + rows] (+)= sout * alpha * leaf(sin * x[xo : xo + cols]).
 // `sync`: a team barrier runs first (an earlier term since the last barrier
 // wrote overlapping outputs under another partition of the rows).
 struct __align__(16) Term {
@@ -35,6 +35,11 @@ struct __align__(16) Term {
   const int32_t* rowptr;  // CSR (for the adjoint: the stored transpose)
   const int32_t* col;
   int64_t lda, Lp, shift; // dense leading dimension; conv padded taps and shift
+  // diagonal scalings around the leaf (equilibration), aligned with the
+  // term's slices: x[xo + j] is read as sin[j] x[xo + j], and the term's
+  // result for y[yo + i] is multiplied by sout[i]; null means 1
+  const float* sin;
+  const float* sout;
 };
 
 // A problem's flattened operator: forward (t = A p), adjoint (q = A^T t) and
