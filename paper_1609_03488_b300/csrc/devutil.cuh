@@ -87,4 +87,19 @@ template <> struct Vec<__nv_fp8_e4m3> {
   }
 };
 
+// Streaming loads of operator data that skip L1 (so that they do not evict
+// the gathered vector) and stay cacheable in L2.
+__device__ __forceinline__ int4 ld_stream_i4(const int32_t* p) {
+  int4 v;
+  asm("ld.global.nc.L1::no_allocate.v4.s32 {%0, %1, %2, %3}, [%4];"
+      : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ uint4 ld_stream_u4(const void* p) {
+  uint4 v;
+  asm("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
+      : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
+  return v;
+}
+
 }  // namespace cf

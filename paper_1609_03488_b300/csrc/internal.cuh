@@ -138,9 +138,10 @@ void op_apply(const cf_op* op, bool trans, float alpha, const float* x, float* y
               float* ws, cudaStream_t s);
 void op_retain(cf_op* op);
 
-// ---- elementwise segments: y = sum_k alpha_k d_k x_k (+ y if acc); no
-// terms and acc == 0 is a zero fill.  Several independent segments go out
-// in one launch.
+// ---- elementwise segments: y = sout * sum_k alpha_k d_k sin_k x_k (+ y if
+// acc); no terms and acc == 0 is a zero fill.  Several independent segments
+// go out in one launch.  (sin / sout: diagonal scalings around the operator,
+// nullptr = 1.)
 constexpr int kEwMaxTerms = 4;
 constexpr int kEwMaxSegs = 8;
 struct EwSeg {
@@ -149,6 +150,8 @@ struct EwSeg {
   int acc, nterm;
   const float* x[kEwMaxTerms];
   const float* d[kEwMaxTerms];  // nullptr: identity
+  const float* sin[kEwMaxTerms];
+  const float* sout;
   float alpha[kEwMaxTerms];
 };
 struct EwBatch {
@@ -161,18 +164,24 @@ void launch_ew(cudaStream_t s, const EwBatch& b);
 void launch_fill(cudaStream_t s, int64_t n, float v, float* y);
 void launch_diag(cudaStream_t s, int64_t n, const float* d, float alpha, const float* x, float* y,
                  bool acc);
+// Leaves taking sin / sout compute y (+)= sout * alpha * leaf(sin * x)
+// (elementwise scalings of the input and output, nullptr = 1).
 void launch_conv1d(cudaStream_t s, int64_t n_out, int64_t n_in, int64_t Lp, int64_t shift,
-                   const float* wrev, float alpha, const float* x, float* y, bool acc);
+                   const float* wrev, float alpha, const float* x, float* y, bool acc,
+                   const float* sin = nullptr, const float* sout = nullptr);
 void launch_conv2d(cudaStream_t s, int64_t Ho, int64_t Wo, int64_t Hi, int64_t Wi, int64_t kh,
                    int64_t kw, int64_t sh, int64_t sw, const float* kern, float alpha,
                    const float* x, float* y, bool acc);
 void launch_gemv_n(cudaStream_t s, cf_prec p, int64_t m, int64_t n, int64_t lda, const void* A,
-                   const float* rs, float alpha, const float* x, float* y, bool acc);
+                   const float* rs, float alpha, const float* x, float* y, bool acc,
+                   const float* sin = nullptr, const float* sout = nullptr);
 size_t gemv_t_ws_floats(int64_t m, int64_t n, int64_t lda);
 void launch_gemv_t(cudaStream_t s, cf_prec p, int64_t m, int64_t n, int64_t lda, const void* A,
-                   const float* rs, float alpha, const float* x, float* y, bool acc, float* ws);
-void launch_csr(cudaStream_t s, cf_prec p, int64_t m, const int32_t* rowptr, const int32_t* col,
-                const void* val, float alpha, const float* x, float* y, bool acc);
+                   const float* rs, float alpha, const float* x, float* y, bool acc, float* ws,
+                   const float* sin = nullptr, const float* sout = nullptr);
+void launch_csr(cudaStream_t s, cf_prec p, int64_t m, int64_t nnz, const int32_t* rowptr, const int32_t* col,
+                const void* val, float alpha, const float* x, float* y, bool acc,
+                const float* sin = nullptr, const float* sout = nullptr);
 void launch_gemm(cudaStream_t s, int64_t M, int64_t N, int64_t K, const float* A, int64_t lda,
                  bool ta, const float* B, int64_t ldb, bool tb, float alpha, float* C, bool acc);
 void launch_quantize(cudaStream_t s, cf_prec p, int64_t m, int64_t n, int64_t lda,

@@ -27,9 +27,10 @@ __global__ void k_ew(EwBatch b) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n;
        i += (int64_t)gridDim.x * blockDim.x) {
     float v = g.acc ? g.y[i] : 0.f;
+    const float so = g.sout ? g.sout[i] : 1.f;
     for (int k = 0; k < g.nterm; ++k) {
-      const float xv = g.x[k][i];
-      v = fmaf(g.alpha[k], g.d[k] ? g.d[k][i] * xv : xv, v);
+      const float xv = g.sin[k] ? g.sin[k][i] * g.x[k][i] : g.x[k][i];
+      v = fmaf(g.sout ? g.alpha[k] * so : g.alpha[k], g.d[k] ? g.d[k][i] * xv : xv, v);
     }
     g.y[i] = v;
   }
@@ -106,9 +107,12 @@ __device__ __forceinline__ void conv_load(float (&dst)[kConvR], const float* __r
   }
 }
 
+// SC: the input is read as sin * x and the outputs are multiplied by sout.
+template <bool SC>
 __global__ void __launch_bounds__(kConvThreads)
 k_conv1d(int64_t n_out, int64_t n_in, int64_t Lp, int64_t shift, const float* __restrict__ wrev,
-         float alpha, const float* __restrict__ x, float* __restrict__ y, bool acc) {
+         float alpha, const float* __restrict__ x, float* __restrict__ y, bool acc,
+         const float* __restrict__ sin, const float* __restrict__ sout) {
   extern __shared__ __align__(16) float sm[];
   const int tid = threadIdx.x;
   const int grp = tid / kConvOutThreads;       // which part of the taps
@@ -128,7 +132,7 @@ k_conv1d(int64_t n_out, int64_t n_in, int64_t Lp, int64_t shift, const float* __
     __syncthreads();
     for (int j = tid; j < kConvTile + lc + kConvR; j += kConvThreads) {
       int64_t g = base + j;
-      in_s[conv_pad(j)] = (g >= 0 && g < n_in) ? __ldg(x + g) : 0.f;
+      in_s[conv_pad(j)] = (g >= 0 && g < n_in) ? (SC ? __ldg(sin + g) * __ldg(x + g) : __ldg(x + g)) : 0.f;
     }
     const float* wsrc = wrev + (Lp - l0 - lc);
     for (int j = tid; j < lc; j += kConvThreads) w_s[j] = __ldg(wsrc + j);
@@ -175,19 +179,25 @@ k_conv1d(int64_t n_out, int64_t n_in, int64_t Lp, int64_t shift, const float* __
   for (int r = 0; r < kConvR; ++r) {
     int64_t i = i0 + t * kConvR + r;
     if (i < n_out) {
-      float v = alpha * accum[r];
+      float v = (SC ? alpha * __ldg(sout + i) : alpha) * accum[r];
       y[i] = acc ? y[i] + v : v;
     }
   }
 }
 
 void launch_conv1d(cudaStream_t s, int64_t n_out, int64_t n_in, int64_t Lp, int64_t shift,
-                   const float* wrev, float alpha, const float* x, float* y, bool acc) {
+                   const float* wrev, float alpha, const float* x, float* y, bool acc,
+                   const float* sin, const float* sout) {
   if (n_out <= 0) return;
   const int lc_max = (int)std::min<int64_t>(Lp, kConvChunk);
   const size_t smem = (size_t)(conv_pad(kConvTile + lc_max + kConvR) + 4 + lc_max) * sizeof(float);
   const int64_t grid = (n_out + kConvTile - 1) / kConvTile;
-  k_conv1d<<<(unsigned)grid, kConvThreads, smem, s>>>(n_out, n_in, Lp, shift, wrev, alpha, x, y, acc);
+  if (sin || sout)
+    k_conv1d<true><<<(unsigned)grid, kConvThreads, smem, s>>>(n_out, n_in, Lp, shift, wrev, alpha, x, y, acc, sin,
+                                                              sout);
+  else
+    k_conv1d<false><<<(unsigned)grid, kConvThreads, smem, s>>>(n_out, n_in, Lp, shift, wrev, alpha, x, y, acc,
+                                                               nullptr, nullptr);
 }
 
 // ------------------------------------------------------------ 2-D convolution
@@ -240,15 +250,18 @@ void launch_conv2d(cudaStream_t s, int64_t Ho, int64_t Wo, int64_t Hi, int64_t W
 // y[i] = alpha * s_i * sum_j A[i, j] x[j]: a warp handles RW rows, so each
 // slice of x it loads is reused RW times; the RW operand loads are issued
 // before any of them is used.
-template <typename T, int RW>
+// SC: x is read as sin * x and the rows are multiplied by sout.
+template <typename T, int RW, bool SC>
 __global__ void __launch_bounds__(256)
 k_gemv_n(int64_t m, int64_t n, int64_t lda, const T* __restrict__ A, const float* __restrict__ rs,
-         float alpha, const float* __restrict__ x, float* __restrict__ y, bool acc) {
+         float alpha, const float* __restrict__ x, float* __restrict__ y, bool acc,
+         const float* __restrict__ sin, const float* __restrict__ sout) {
   constexpr int V = Vec<T>::N;
   const int lane = threadIdx.x & 31;
   const int64_t row0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * RW;
   if (row0 >= m) return;
-  const bool xal = ((reinterpret_cast<uintptr_t>(x) & 15) == 0);
+  const bool xal = ((reinterpret_cast<uintptr_t>(x) & 15) == 0) &&
+                   (!SC || ((reinterpret_cast<uintptr_t>(sin) & 15) == 0));
   float accv[RW];
 #pragma unroll
   for (int r = 0; r < RW; ++r) accv[r] = 0.f;
@@ -258,11 +271,16 @@ k_gemv_n(int64_t m, int64_t n, int64_t lda, const T* __restrict__ A, const float
 #pragma unroll
       for (int q = 0; q < V; q += 4) {
         float4 t = __ldg(reinterpret_cast<const float4*>(x + c + q));
+        if (SC) {
+          const float4 w = __ldg(reinterpret_cast<const float4*>(sin + c + q));
+          t.x *= w.x; t.y *= w.y; t.z *= w.z; t.w *= w.w;
+        }
         xv[q] = t.x; xv[q + 1] = t.y; xv[q + 2] = t.z; xv[q + 3] = t.w;
       }
     } else {
 #pragma unroll
-      for (int q = 0; q < V; ++q) xv[q] = (c + q < n) ? __ldg(x + c + q) : 0.f;
+      for (int q = 0; q < V; ++q)
+        xv[q] = (c + q < n) ? (SC ? __ldg(sin + c + q) * __ldg(x + c + q) : __ldg(x + c + q)) : 0.f;
     }
     uint4 u[RW];
 #pragma unroll
@@ -285,28 +303,33 @@ k_gemv_n(int64_t m, int64_t n, int64_t lda, const T* __restrict__ A, const float
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     int64_t row = row0 + r;
     if (lane == 0 && row < m) {
-      float out = alpha * (rs ? rs[row] * v : v);
+      float out = (SC ? alpha * sout[row] : alpha) * (rs ? rs[row] * v : v);
       y[row] = acc ? y[row] + out : out;
     }
   }
 }
 
+template <typename T>
+static void gemv_n_typed(cudaStream_t s, int64_t m, int64_t n, int64_t lda, const void* A, const float* rs,
+                         float alpha, const float* x, float* y, bool acc, const float* sin, const float* sout) {
+  constexpr int RW = 4;
+  const unsigned grid = (unsigned)((m + 8 * RW - 1) / (8 * RW));
+  if (sin || sout)
+    k_gemv_n<T, RW, true><<<grid, 256, 0, s>>>(m, n, lda, (const T*)A, rs, alpha, x, y, acc, sin, sout);
+  else
+    k_gemv_n<T, RW, false><<<grid, 256, 0, s>>>(m, n, lda, (const T*)A, rs, alpha, x, y, acc, nullptr, nullptr);
+}
+
 void launch_gemv_n(cudaStream_t s, cf_prec p, int64_t m, int64_t n, int64_t lda, const void* A,
-                   const float* rs, float alpha, const float* x, float* y, bool acc) {
+                   const float* rs, float alpha, const float* x, float* y, bool acc, const float* sin,
+                   const float* sout) {
   if (m <= 0) return;
-  if (p == CF_FP32) {
-    constexpr int RW = 4;
-    unsigned grid = (unsigned)((m + 8 * RW - 1) / (8 * RW));
-    k_gemv_n<float, RW><<<grid, 256, 0, s>>>(m, n, lda, (const float*)A, rs, alpha, x, y, acc);
-  } else if (p == CF_BF16) {
-    constexpr int RW = 4;
-    unsigned grid = (unsigned)((m + 8 * RW - 1) / (8 * RW));
-    k_gemv_n<__nv_bfloat16, RW><<<grid, 256, 0, s>>>(m, n, lda, (const __nv_bfloat16*)A, rs, alpha, x, y, acc);
-  } else {
-    constexpr int RW = 4;
-    unsigned grid = (unsigned)((m + 8 * RW - 1) / (8 * RW));
-    k_gemv_n<__nv_fp8_e4m3, RW><<<grid, 256, 0, s>>>(m, n, lda, (const __nv_fp8_e4m3*)A, rs, alpha, x, y, acc);
-  }
+  if (p == CF_FP32)
+    gemv_n_typed<float>(s, m, n, lda, A, rs, alpha, x, y, acc, sin, sout);
+  else if (p == CF_BF16)
+    gemv_n_typed<__nv_bfloat16>(s, m, n, lda, A, rs, alpha, x, y, acc, sin, sout);
+  else
+    gemv_n_typed<__nv_fp8_e4m3>(s, m, n, lda, A, rs, alpha, x, y, acc, sin, sout);
 }
 
 // x^T-side: part[rb, j] = sum_{i in row block rb} A[i, j] (s_i y_i); each
@@ -322,13 +345,14 @@ constexpr int kGemvTUnroll = 8;
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_gemv_t_part(int64_t m, int64_t n, int64_t lda, int64_t rows_per_block, const T* __restrict__ A,
-              const float* __restrict__ rs, const float* __restrict__ yv, float* __restrict__ part) {
+              const float* __restrict__ rs, const float* __restrict__ yv, float* __restrict__ part,
+              const float* __restrict__ sin) {
   constexpr int V = Vec<T>::N;
   __shared__ float sy[kGemvTMaxRows];
   const int64_t r0 = (int64_t)blockIdx.y * rows_per_block;
   const int64_t r1 = (r0 + rows_per_block < m) ? r0 + rows_per_block : m;
   for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x)
-    sy[i - r0] = rs ? rs[i] * yv[i] : yv[i];
+    sy[i - r0] = (rs ? rs[i] * yv[i] : yv[i]) * (sin ? sin[i] : 1.f);
   __syncthreads();
   const int64_t c0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * V;
   if (c0 >= n) return;
@@ -364,12 +388,12 @@ k_gemv_t_part(int64_t m, int64_t n, int64_t lda, int64_t rows_per_block, const T
 }
 
 __global__ void k_gemv_t_reduce(int64_t n, int64_t lda, int nrb, const float* __restrict__ part,
-                                float alpha, float* __restrict__ x, bool acc) {
+                                float alpha, float* __restrict__ x, bool acc, const float* __restrict__ sout) {
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
        j += (int64_t)gridDim.x * blockDim.x) {
     float sum = 0.f;
     for (int b = 0; b < nrb; ++b) sum += part[(int64_t)b * lda + j];
-    float v = alpha * sum;
+    float v = (sout ? alpha * sout[j] : alpha) * sum;
     x[j] = acc ? x[j] + v : v;
   }
 }
@@ -388,7 +412,8 @@ size_t gemv_t_ws_floats(int64_t m, int64_t n, int64_t lda) {
 }
 
 void launch_gemv_t(cudaStream_t s, cf_prec p, int64_t m, int64_t n, int64_t lda, const void* A,
-                   const float* rs, float alpha, const float* x, float* y, bool acc, float* ws) {
+                   const float* rs, float alpha, const float* x, float* y, bool acc, float* ws,
+                   const float* sin, const float* sout) {
   if (n <= 0) return;
   if (m <= 0) {
     if (!acc) launch_fill(s, n, 0.f, y);
@@ -400,12 +425,14 @@ void launch_gemv_t(cudaStream_t s, cf_prec p, int64_t m, int64_t n, int64_t lda,
   const int threads = kGemvTCols / V;
   dim3 grid((unsigned)((n + kGemvTCols - 1) / kGemvTCols), (unsigned)rb);
   if (p == CF_FP32)
-    k_gemv_t_part<float><<<grid, threads, 0, s>>>(m, n, lda, rows_per_block, (const float*)A, rs, x, ws);
+    k_gemv_t_part<float><<<grid, threads, 0, s>>>(m, n, lda, rows_per_block, (const float*)A, rs, x, ws, sin);
   else if (p == CF_BF16)
-    k_gemv_t_part<__nv_bfloat16><<<grid, threads, 0, s>>>(m, n, lda, rows_per_block, (const __nv_bfloat16*)A, rs, x, ws);
+    k_gemv_t_part<__nv_bfloat16><<<grid, threads, 0, s>>>(m, n, lda, rows_per_block, (const __nv_bfloat16*)A, rs, x,
+                                                          ws, sin);
   else
-    k_gemv_t_part<__nv_fp8_e4m3><<<grid, threads, 0, s>>>(m, n, lda, rows_per_block, (const __nv_fp8_e4m3*)A, rs, x, ws);
-  k_gemv_t_reduce<<<grid_for(n, 1), kThreads, 0, s>>>(n, lda, rb, ws, alpha, y, acc);
+    k_gemv_t_part<__nv_fp8_e4m3><<<grid, threads, 0, s>>>(m, n, lda, rows_per_block, (const __nv_fp8_e4m3*)A, rs, x,
+                                                          ws, sin);
+  k_gemv_t_reduce<<<grid_for(n, 1), kThreads, 0, s>>>(n, lda, rb, ws, alpha, y, acc, sout);
 }
 
 // ------------------------------------------------------------ quantisation
@@ -460,11 +487,12 @@ __device__ __forceinline__ float csr_val(const void* __restrict__ val, int32_t k
   return BF16 ? __bfloat162float(__ldg(((const __nv_bfloat16*)val) + k)) : __ldg(((const float*)val) + k);
 }
 
-template <bool BF16>
+// SC: input / output scalings (sin, sout) are applied.
+template <bool BF16, bool SC>
 __global__ void __launch_bounds__(256)
 k_csr(int64_t m, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
       const void* __restrict__ val, float alpha, const float* __restrict__ x,
-      float* __restrict__ y, bool acc) {
+      float* __restrict__ y, bool acc, const float* __restrict__ sin, const float* __restrict__ sout) {
   const int lane = threadIdx.x & 31;
   const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (row >= m) return;
@@ -475,29 +503,41 @@ k_csr(int64_t m, const int32_t* __restrict__ rowptr, const int32_t* __restrict__
     const int32_t c0 = __ldg(col + k), c1 = __ldg(col + k + 32), c2 = __ldg(col + k + 64), c3 = __ldg(col + k + 96);
     const float v0 = csr_val<BF16>(val, k), v1 = csr_val<BF16>(val, k + 32);
     const float v2 = csr_val<BF16>(val, k + 64), v3 = csr_val<BF16>(val, k + 96);
-    s0 = fmaf(v0, __ldg(x + c0), s0);
-    s1 = fmaf(v1, __ldg(x + c1), s1);
-    s2 = fmaf(v2, __ldg(x + c2), s2);
-    s3 = fmaf(v3, __ldg(x + c3), s3);
+    s0 = fmaf(v0, SC ? __ldg(sin + c0) * __ldg(x + c0) : __ldg(x + c0), s0);
+    s1 = fmaf(v1, SC ? __ldg(sin + c1) * __ldg(x + c1) : __ldg(x + c1), s1);
+    s2 = fmaf(v2, SC ? __ldg(sin + c2) * __ldg(x + c2) : __ldg(x + c2), s2);
+    s3 = fmaf(v3, SC ? __ldg(sin + c3) * __ldg(x + c3) : __ldg(x + c3), s3);
   }
-  for (; k < e; k += 32) s0 = fmaf(csr_val<BF16>(val, k), __ldg(x + __ldg(col + k)), s0);
+  for (; k < e; k += 32) {
+    const int32_t c = __ldg(col + k);
+    s0 = fmaf(csr_val<BF16>(val, k), SC ? __ldg(sin + c) * __ldg(x + c) : __ldg(x + c), s0);
+  }
   float sum = (s0 + s1) + (s2 + s3);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
   if (lane == 0) {
-    float out = alpha * sum;
+    float out = (SC ? alpha * __ldg(sout + row) : alpha) * sum;
     y[row] = acc ? y[row] + out : out;
   }
 }
 
-void launch_csr(cudaStream_t s, cf_prec p, int64_t m, const int32_t* rowptr, const int32_t* col,
-                const void* val, float alpha, const float* x, float* y, bool acc) {
+void launch_csr(cudaStream_t s, cf_prec p, int64_t m, int64_t nnz, const int32_t* rowptr, const int32_t* col,
+                const void* val, float alpha, const float* x, float* y, bool acc, const float* sin,
+                const float* sout) {
   if (m <= 0) return;
+  (void)nnz;
   unsigned grid = (unsigned)((m + 7) / 8);
-  if (p == CF_BF16)
-    k_csr<true><<<grid, 256, 0, s>>>(m, rowptr, col, val, alpha, x, y, acc);
-  else
-    k_csr<false><<<grid, 256, 0, s>>>(m, rowptr, col, val, alpha, x, y, acc);
+  // both scalings or none (op_apply folds a product only when both diagonals are stored)
+  if (sin || sout) {
+    if (p == CF_BF16)
+      k_csr<true, true><<<grid, 256, 0, s>>>(m, rowptr, col, val, alpha, x, y, acc, sin, sout);
+    else
+      k_csr<false, true><<<grid, 256, 0, s>>>(m, rowptr, col, val, alpha, x, y, acc, sin, sout);
+  } else if (p == CF_BF16) {
+    k_csr<true, false><<<grid, 256, 0, s>>>(m, rowptr, col, val, alpha, x, y, acc, nullptr, nullptr);
+  } else {
+    k_csr<false, false><<<grid, 256, 0, s>>>(m, rowptr, col, val, alpha, x, y, acc, nullptr, nullptr);
+  }
 }
 
 // ------------------------------------------------------------ small GEMM

@@ -78,17 +78,20 @@ struct EwQueue {
     launch_ew(s, b);
     b.nseg = 0;
   }
-  // y = alpha d x (+ y): nterm 0 is a zero fill.
-  void add(float* y, int64_t n, bool acc, const float* x, const float* d, float alpha, bool fill) {
-    // same output, accumulating, no reads of pending outputs: one more term
+  // y = sout alpha d (sin x) (+ y): nterm 0 is a zero fill.
+  void add(float* y, int64_t n, bool acc, const float* x, const float* d, float alpha, bool fill,
+           const float* sin = nullptr, const float* sout = nullptr) {
+    // same output and output scaling, accumulating, no reads of pending
+    // outputs: one more term
     for (int k = 0; k < b.nseg; ++k) {
       EwSeg& g = b.seg[k];
-      if (!fill && acc && g.y == y && g.n == n && g.nterm < kEwMaxTerms) {
+      if (!fill && acc && g.y == y && g.n == n && g.nterm < kEwMaxTerms && g.sout == sout) {
         bool hazard = false;
         for (int j = 0; j < b.nseg; ++j) hazard |= overlap(x, n, b.seg[j].y, b.seg[j].n);
         if (!hazard) {
           g.x[g.nterm] = x;
           g.d[g.nterm] = d;
+          g.sin[g.nterm] = sin;
           g.alpha[g.nterm] = alpha;
           ++g.nterm;
           return;
@@ -108,31 +111,65 @@ struct EwQueue {
     g.n = n;
     g.acc = acc ? 1 : 0;
     g.nterm = fill ? 0 : 1;
+    g.sout = fill ? nullptr : sout;
     if (!fill) {
       g.x[0] = x;
       g.d[0] = d;
+      g.sin[0] = sin;
       g.alpha[0] = alpha;
     }
   }
 };
 
+// Scalings around a subtree, aligned with its x (in) and y (out); nullptr = 1.
+struct Scales {
+  const float* in = nullptr;
+  const float* out = nullptr;
+  Scales shift(int64_t dx, int64_t dy) const {
+    return Scales{in ? in + dx : nullptr, out ? out + dy : nullptr};
+  }
+};
+
 void op_apply_rec(const cf_op* op, bool trans, float alpha, const float* x, float* y, bool acc,
-                  float* ws, cudaStream_t s, EwQueue& q);
+                  float* ws, cudaStream_t s, EwQueue& q, Scales sc);
+
+// Whether every leaf below takes input / output scalings.
+bool scalable(const cf_op* op) {
+  switch (op->kind) {
+    case OP_DENSE: case OP_CSR: case OP_CONV1D: case OP_DIAG: case OP_ZERO:
+      return true;
+    case OP_VSTACK: case OP_HSTACK: case OP_BLOCKDIAG: case OP_SUM: case OP_SCALE: case OP_ADJOINT:
+      for (const cf_op* p : op->parts)
+        if (!scalable(p)) return false;
+      return true;
+    default:
+      return false;
+  }
+}
 
 }  // namespace
 
-// y = alpha * op(x) + (acc ? y : 0)
+// y = alpha * op(x) + (acc ? y : 0).  An equilibrated operator
+// diag(D) A diag(E) whose leaves all take scalings is applied as A with the
+// two diagonals folded into A's leaf kernels (no separate passes).
 void op_apply(const cf_op* op, bool trans, float alpha, const float* x, float* y, bool acc,
               float* ws, cudaStream_t s) {
   EwQueue q(s);
-  op_apply_rec(op, trans, alpha, x, y, acc, ws, s, q);
+  if (op->kind == OP_PRODUCT && op->parts.size() == 3 && op->parts[0]->kind == OP_DIAG &&
+      op->parts[2]->kind == OP_DIAG && op->parts[0]->d && op->parts[2]->d && scalable(op->parts[1])) {
+    const float* D = op->parts[0]->d;
+    const float* E = op->parts[2]->d;
+    op_apply_rec(op->parts[1], trans, alpha, x, y, acc, ws, s, q, trans ? Scales{D, E} : Scales{E, D});
+  } else {
+    op_apply_rec(op, trans, alpha, x, y, acc, ws, s, q, Scales{});
+  }
   q.flush();
 }
 
 namespace {
 
 void op_apply_rec(const cf_op* op, bool trans, float alpha, const float* x, float* y, bool acc,
-                  float* ws, cudaStream_t s, EwQueue& q) {
+                  float* ws, cudaStream_t s, EwQueue& q, Scales sc) {
   const int64_t out_dim = trans ? op->n : op->m;
   // Elementwise leaves are queued; any other leaf first launches the queue,
   // so operations keep their order wherever they could interact.
@@ -145,26 +182,28 @@ void op_apply_rec(const cf_op* op, bool trans, float alpha, const float* x, floa
       if (!acc) q.add(y, out_dim, false, nullptr, nullptr, 0.f, true);
       return;
     case OP_DIAG:
-      q.add(y, op->n, acc, x, op->d, alpha, false);
+      q.add(y, op->n, acc, x, op->d, alpha, false, sc.in, sc.out);
       return;
     case OP_DENSE:
       if (!trans)
-        launch_gemv_n(s, op->prec, op->m, op->n, op->lda, op->a, op->row_scale, alpha, x, y, acc);
+        launch_gemv_n(s, op->prec, op->m, op->n, op->lda, op->a, op->row_scale, alpha, x, y, acc, sc.in, sc.out);
       else
-        launch_gemv_t(s, op->prec, op->m, op->n, op->lda, op->a, op->row_scale, alpha, x, y, acc, ws);
+        launch_gemv_t(s, op->prec, op->m, op->n, op->lda, op->a, op->row_scale, alpha, x, y, acc, ws, sc.in,
+                      sc.out);
       return;
     case OP_CSR:
       if (!trans)
-        launch_csr(s, op->prec, op->m, op->rowptr, op->col, op->val, alpha, x, y, acc);
+        launch_csr(s, op->prec, op->m, op->nnz, op->rowptr, op->col, op->val, alpha, x, y, acc, sc.in, sc.out);
       else
-        launch_csr(s, op->prec, op->n, op->t_rowptr, op->t_col, op->t_val, alpha, x, y, acc);
+        launch_csr(s, op->prec, op->n, op->nnz, op->t_rowptr, op->t_col, op->t_val, alpha, x, y, acc, sc.in,
+                   sc.out);
       return;
     case OP_CONV1D: {
       const int64_t nx = op->n, ny = op->m;
       if (!trans)
-        launch_conv1d(s, ny, nx, op->Lp, 0, op->w_fwd, alpha, x, y, acc);
+        launch_conv1d(s, ny, nx, op->Lp, 0, op->w_fwd, alpha, x, y, acc, sc.in, sc.out);
       else
-        launch_conv1d(s, nx, ny, op->Lp, op->Lp - 1, op->w_adj, alpha, x, y, acc);
+        launch_conv1d(s, nx, ny, op->Lp, op->Lp - 1, op->w_adj, alpha, x, y, acc, sc.in, sc.out);
       return;
     }
     case OP_CONV2D: {
@@ -177,10 +216,10 @@ void op_apply_rec(const cf_op* op, bool trans, float alpha, const float* x, floa
       return;
     }
     case OP_SCALE:
-      op_apply_rec(op->parts[0], trans, (float)(alpha * op->alpha), x, y, acc, ws, s, q);
+      op_apply_rec(op->parts[0], trans, (float)(alpha * op->alpha), x, y, acc, ws, s, q, sc);
       return;
     case OP_ADJOINT:
-      op_apply_rec(op->parts[0], !trans, alpha, x, y, acc, ws, s, q);
+      op_apply_rec(op->parts[0], !trans, alpha, x, y, acc, ws, s, q, sc);
       return;
     case OP_VSTACK:
     case OP_HSTACK: {
@@ -190,10 +229,10 @@ void op_apply_rec(const cf_op* op, bool trans, float alpha, const float* x, floa
       bool first = true;
       for (const cf_op* p : op->parts) {
         if (split_out) {
-          op_apply_rec(p, trans, alpha, x, y + off, acc, ws, s, q);
+          op_apply_rec(p, trans, alpha, x, y + off, acc, ws, s, q, sc.shift(0, off));
           off += trans ? p->n : p->m;
         } else {
-          op_apply_rec(p, trans, alpha, x + off, y, first ? acc : true, ws, s, q);
+          op_apply_rec(p, trans, alpha, x + off, y, first ? acc : true, ws, s, q, sc.shift(off, 0));
           off += trans ? p->m : p->n;
           first = false;
         }
@@ -204,7 +243,7 @@ void op_apply_rec(const cf_op* op, bool trans, float alpha, const float* x, floa
       int64_t ro = 0, co = 0;
       for (const cf_op* p : op->parts) {
         const int64_t din = trans ? p->m : p->n, dout = trans ? p->n : p->m;
-        op_apply_rec(p, trans, alpha, x + ro, y + co, acc, ws, s, q);
+        op_apply_rec(p, trans, alpha, x + ro, y + co, acc, ws, s, q, sc.shift(ro, co));
         ro += din;
         co += dout;
       }
@@ -213,13 +252,15 @@ void op_apply_rec(const cf_op* op, bool trans, float alpha, const float* x, floa
     case OP_SUM: {
       bool first = true;
       for (const cf_op* p : op->parts) {
-        op_apply_rec(p, trans, alpha, x, y, first ? acc : true, ws, s, q);
+        op_apply_rec(p, trans, alpha, x, y, first ? acc : true, ws, s, q, sc);
         first = false;
       }
       return;
     }
     case OP_PRODUCT: {
       // forward: apply P_k ... P_1 right to left; adjoint: P_1^T first.
+      // (Scalings never reach a product: op_apply folds them only into
+      // trees without products.)
       int64_t inner = 0;
       for (size_t i = 0; i + 1 < op->parts.size(); ++i) inner = std::max(inner, op->parts[i]->n);
       float* buf[2] = {ws, ws + al16((size_t)inner)};
@@ -230,7 +271,7 @@ void op_apply_rec(const cf_op* op, bool trans, float alpha, const float* x, floa
         const cf_op* p = trans ? op->parts[step] : op->parts[k - 1 - step];
         const bool last = step + 1 == k;
         float* dst = last ? y : buf[step & 1];
-        op_apply_rec(p, trans, last ? alpha : 1.f, cur, dst, last ? acc : false, rest, s, q);
+        op_apply_rec(p, trans, last ? alpha : 1.f, cur, dst, last ? acc : false, rest, s, q, Scales{});
         cur = dst;
       }
       return;

@@ -222,21 +222,6 @@ __device__ __forceinline__ float tval(const void* __restrict__ val, int32_t k) {
   return BF16 ? __bfloat162float(__ldg(((const __nv_bfloat16*)val) + k)) : __ldg(((const float*)val) + k);
 }
 
-// Streaming loads of operator data that skip L1 (so that they do not evict
-// the gathered vector) and stay cacheable in L2.
-__device__ __forceinline__ int4 ld_stream_i4(const int32_t* p) {
-  int4 v;
-  asm("ld.global.nc.L1::no_allocate.v4.s32 {%0, %1, %2, %3}, [%4];"
-      : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
-  return v;
-}
-__device__ __forceinline__ uint4 ld_stream_u4(const void* p) {
-  uint4 v;
-  asm("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
-      : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
-  return v;
-}
-
 // CSR rows to groups of L lanes (L a power of two).  A lane takes aligned
 // chunks of 8 entries of its row (the arrays are padded to whole chunks):
 // two 16-byte loads of column indices and one (BF16) or two (FP32) of values

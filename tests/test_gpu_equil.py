@@ -166,3 +166,24 @@ def test_equilibrated_batch_equals_solo(B, ctx):
         np.testing.assert_array_equal(y0, y1)
         np.testing.assert_array_equal(s0, s1)
         assert max(fp64_residuals(prob, x1, y1, s1)) <= 1e-4
+
+
+@pytest.mark.parametrize("engine", ["auto", "graph"])
+def test_equilibrated_serving_equals_solo(B, ctx, engine):
+    rng = np.random.default_rng(78)
+    probs = [synth.deconv(n_x=300, L=30, seed=1), synth.lasso(m_d=300, p=150, seed=2, storage="bf16"),
+             synth.lp(m_d=200, n_x=100, density=0.05, seed=3), synth.mixed_cone_problem(rng),
+             synth.lp(m_d=500, n_x=250, density=0.02, seed=5, storage="bf16")]
+    Ps = [_eq_problem(B, ctx, p) for p in probs]
+    st = B.settings(engine=engine)
+    solo = [B.solve(P, st) for P in Ps]
+    srv = B.Server(ctx, 100 << 20, 4)
+    order = [0, 1, 2, 3, 4, 3, 1]
+    tickets = [(i, srv.submit(Ps[i], st)) for i in order]
+    for i, t in tickets:
+        info, x, y, s = srv.wait(t, Ps[i])
+        assert info["iters"] == solo[i][0]["iters"]
+        np.testing.assert_array_equal(x, solo[i][1])
+        np.testing.assert_array_equal(y, solo[i][2])
+        np.testing.assert_array_equal(s, solo[i][3])
+    srv.close()
