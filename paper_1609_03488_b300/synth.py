@@ -234,6 +234,95 @@ def lasso(m_d=2000, p=1000, support=0.01, noise=0.01, lam_frac=0.1, storage="fp3
                      "x_star": x_star, "storage": storage, "seed": seed}}
 
 
+def _lasso_cone(Dtree, D_mv, D_rmv, m_d, p, rng, support, noise, lam_frac):
+    """The lasso cone form of ``lasso`` around any operator D (``Dtree`` with
+    FP64 products ``D_mv`` / ``D_rmv`` for the observation and lam)."""
+    x_star = np.zeros(p)
+    k = max(1, int(round(support * p)))
+    idx = rng.choice(p, size=k, replace=False)
+    x_star[idx] = rng.standard_normal(k)
+    b_obs = D_mv(x_star) + noise * rng.standard_normal(m_d)
+    lam = lam_frac * np.abs(D_rmv(b_obs)).max()
+    r2 = np.sqrt(2.0)
+    A = vstack([
+        hstack([eye(p), scale(-1.0, eye(p)), zero(p, 1)]),
+        hstack([scale(-1.0, eye(p)), scale(-1.0, eye(p)), zero(p, 1)]),
+        hstack([zero(1, p), zero(1, p), scale(-1.0, eye(1))]),
+        hstack([zero(1, p), zero(1, p), scale(-1.0, eye(1))]),
+        hstack([scale(-r2, Dtree), zero(m_d, p), zero(m_d, 1)]),
+    ])
+    b = np.concatenate([np.zeros(2 * p), [1.0, -1.0], -r2 * b_obs])
+    c = np.concatenate([np.zeros(p), lam * np.ones(p), [1.0]])
+    return {"A": A, "b": b, "c": c, "cone": {"z": 0, "l": 2 * p, "q": [m_d + 2]},
+            "family": "lasso", "meta": {"m_d": m_d, "p": p, "lam": lam, "b_obs": b_obs, "x_star": x_star}}
+
+
+def lasso_sparse(m_d=2000, p=1000, density=0.01, support=0.01, noise=0.01, lam_frac=0.1, storage="fp32",
+                 seed=BASE_SEED + 5):
+    """The sparse-matrix lasso of Section 5.2: D sparse with the given
+    density (the text's 1%), N(0,1) values scaled by 1/sqrt(m_d density) so
+    that columns have unit expected norm as in the dense case; same cone form
+    as ``lasso``."""
+    rng = rng_for(seed)
+    rowptr, col, val = random_csr(rng, m_d, p, density)
+    val = (val / np.sqrt(m_d * density)).astype(np.float32)
+    vq = val.astype(np.float64)   # the observation uses the float32 values, as in ``lasso``
+    rows = np.repeat(np.arange(m_d), np.diff(rowptr))
+    mv = lambda x: np.bincount(rows, weights=vq * x[col], minlength=m_d)
+    rmv = lambda y: np.bincount(col, weights=vq * y[rows], minlength=p)
+    out = _lasso_cone(csr(m_d, p, rowptr, col, val, storage), mv, rmv, m_d, p, rng, support, noise, lam_frac)
+    out["meta"].update({"density": density, "storage": storage, "seed": seed, "operator": "csr"})
+    return out
+
+
+def lasso_conv(p=1000, L=None, sigma=None, support=0.01, noise=0.01, lam_frac=0.1, seed=BASE_SEED + 6):
+    """The convolution lasso of Section 5.2: D x = k * x (full convolution)
+    with a Gaussian kernel of length L (default p) and standard deviation
+    sigma (default L/10), so m_d = p + L - 1; same cone form as ``lasso``."""
+    rng = rng_for(seed)
+    L = p if L is None else L
+    sigma = L / 10.0 if sigma is None else sigma
+    kernel = gaussian_kernel(L, sigma).astype(np.float32)
+    k64 = kernel.astype(np.float64)
+    m_d = p + L - 1
+    mv = lambda x: np.convolve(k64, x)
+    rmv = lambda y: np.correlate(y, k64, mode="valid")
+    out = _lasso_cone(conv1d(kernel, p), mv, rmv, m_d, p, rng, support, noise, lam_frac)
+    out["meta"].update({"L": L, "sigma": sigma, "kernel": kernel, "seed": seed, "operator": "conv1d"})
+    return out
+
+
+def deconv2d(h=32, w=32, kh=7, kw=7, sigma=None, support=0.05, noise=0.01, seed=BASE_SEED + 7):
+    """Nonnegative 2-D deconvolution (image deblurring, the 2-D convolution
+    case Section 2 motivates): minimise ||K x - b||_2 s.t. x >= 0 for an
+    h x w image x (row-major) and the full 2-D convolution K with a sampled
+    kh x kw Gaussian (normalised to sum 1); cone form as ``deconv``."""
+    from scipy.signal import convolve2d
+    rng = rng_for(seed)
+    sigma = max(kh, kw) / 4.0 if sigma is None else sigma
+    gy = np.exp(-((np.arange(kh) - (kh - 1) / 2.0) ** 2) / (2 * sigma * sigma))
+    gx = np.exp(-((np.arange(kw) - (kw - 1) / 2.0) ** 2) / (2 * sigma * sigma))
+    K = np.outer(gy, gx)
+    K = (K / K.sum()).astype(np.float32)
+    n_x = h * w
+    x_hat = sparse_nonneg_signal(rng, n_x, support)
+    Ho, Wo = h + kh - 1, w + kw - 1
+    b_obs = convolve2d(x_hat.reshape(h, w), K.astype(np.float64), mode="full").ravel()
+    b_obs = b_obs + noise * rng.standard_normal(Ho * Wo)
+    m_obs = Ho * Wo
+    A = vstack([
+        hstack([scale(-1.0, eye(n_x)), zero(n_x, 1)]),
+        hstack([zero(1, n_x), scale(-1.0, eye(1))]),
+        hstack([scale(-1.0, conv2d(K, h, w)), zero(m_obs, 1)]),
+    ])
+    b = np.concatenate([np.zeros(n_x), [0.0], -b_obs])
+    c = np.zeros(n_x + 1)
+    c[-1] = 1.0
+    return {"A": A, "b": b, "c": c, "cone": {"z": 0, "l": n_x, "q": [m_obs + 1]},
+            "family": "deconv2d",
+            "meta": {"h": h, "w": w, "kernel": K, "x_hat": x_hat, "b_obs": b_obs, "seed": seed}}
+
+
 def lp(m_d=400, n_x=200, density=0.02, storage="fp32", seed=BASE_SEED + 4):
     """Sparse LP: minimise c^T x s.t. D x <= b, x >= 0, made feasible and
     bounded by construction (b = D x0 + slack, c = -D^T y0 with x0, slack,

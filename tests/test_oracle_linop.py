@@ -126,3 +126,10 @@ def test_paper_lasso_size_and_nnz():
     assert p["A"]["n"] == g["variables"]
     assert p["A"]["m"] == g["constraints"]
     assert linop.nnz(p["A"]) == g["nnz"]
+
+
+def test_paper_convolution_lasso_size():
+    g = json.load(open(GOLDEN))["lasso_conv"]
+    p = synth.lasso_conv(p=g["p"], L=g["L"], seed=1)
+    assert (p["A"]["n"], p["A"]["m"]) == (g["variables"], g["constraints"])
+    assert synth.cone_dims(p["cone"]) == g["constraints"]
