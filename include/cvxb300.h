@@ -144,7 +144,9 @@ typedef struct {
   int32_t csr_nnz_per_lane;/* CSR rows get the fewest lanes (a power of two,
                               1..32) that hold the average row at this many
                               nonzeros per lane (16) */
-  int32_t reserved;
+  int32_t ctas_per_sm;     /* team CTAs that share an SM: 1, 2 (threads <= 512)
+                              or 4 (threads 256) -- the registers of a thread
+                              shrink to fit (1) */
   double team_bytes;       /* problems whose operator pass reads at least this
                               many bytes run on a whole cluster team; smaller
                               ones on one CTA (256e3) */
@@ -347,10 +349,10 @@ typedef struct {
 /* Autotuner of the team engine (a schedule search; the paper has no
  * counterpart -- it solves one problem at a time): times `iters` ADMM
  * iterations (2 CG steps each, no residual checks) of the batch's
- * team-engine problems under candidate schedules -- threads per CTA and CSR
- * lanes per row first, then the cluster size and the size threshold between
- * cluster teams and one-CTA teams -- and stores the fastest in the problems'
- * context.  The problems must share one context; their iterates are
+ * team-engine problems under candidate schedules -- threads per CTA x CTAs
+ * per SM and CSR lanes per row first (24), then the cluster size and the size
+ * threshold between cluster teams and one-CTA teams (9) -- and stores the
+ * fastest in the problems' context.  The problems must share one context; their iterates are
  * overwritten and their setup is redone at the next solve.  info may be
  * NULL. */
 cf_err solve_batch_tune(cf_problem* const* probs, int32_t count, int32_t iters, cf_tune_info* info);

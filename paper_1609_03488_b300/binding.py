@@ -51,11 +51,11 @@ ENGINE = {"auto": CF_ENGINE_AUTO, "graph": CF_ENGINE_GRAPH, "team": CF_ENGINE_TE
 
 class cf_schedule(C.Structure):
     _fields_ = [("cluster", C.c_int32), ("threads", C.c_int32), ("csr_nnz_per_lane", C.c_int32),
-                ("reserved", C.c_int32), ("team_bytes", C.c_double), ("auto_max_bytes", C.c_double),
+                ("ctas_per_sm", C.c_int32), ("team_bytes", C.c_double), ("auto_max_bytes", C.c_double),
                 ("batch_max_bytes", C.c_double)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class cf_tune_info(C.Structure):
@@ -200,7 +200,7 @@ def set_schedule(ctx, **kw):
     s = cf_schedule()
     check(lib.cf_ctx_get_schedule(ctx.h, C.byref(s)), "cf_ctx_get_schedule")
     for k, v in kw.items():
-        if k == "reserved" or not hasattr(s, k):
+        if not hasattr(s, k):
             raise KeyError(k)
         setattr(s, k, v)
     check(lib.cf_ctx_set_schedule(ctx.h, C.byref(s)), "cf_ctx_set_schedule")

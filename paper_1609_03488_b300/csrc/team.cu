@@ -505,12 +505,12 @@ __device__ void term_conv(const Team& tm, const Term& t, const float* x, float* 
 
 // y = the flattened operator applied to x (terms in order).  Compiled once
 // per CTA size (not inlined at each call) so that the term loops get
-// registers of their own; CTAs of 1024 threads (64 registers a thread) keep
-// one CSR chunk (8 entries) a lane in flight, smaller CTAs two.
-template <int MaxT>
+// registers of their own; with 64 registers a thread (1024 threads on an SM)
+// a lane keeps one CSR chunk (8 entries) in flight, with 128 or more two.
+template <int MaxT, int MinB>
 __device__ __noinline__ void apply(const Team& tm, const Term* terms, int nt, const float* x, float* y,
                                    float* scratch, float* dsm, int lanes) {
-  constexpr int UC = MaxT >= 1024 ? 1 : 2;  // CSR chunks in flight per lane
+  constexpr int UC = 65536 / (MaxT * MinB) >= 128 ? 2 : 1;  // CSR chunks in flight per lane
   for (int k = 0; k < nt; ++k) {
     const Term& t = terms[k];
     if (t.sync) tsync(tm);
@@ -554,7 +554,7 @@ __device__ __noinline__ void apply(const Team& tm, const Term* terms, int nt, co
 // CG on (I + A^T A) z = rhs from the z held, with gz = G z carried (setup
 // starts at z = 0; iterations warm-start with the carried G z).  mode
 // CG_ITER also carries az = A z.  k_outer: the ADMM iteration (tolerance).
-template <int MaxT>
+template <int MaxT, int MinB>
 __device__ __noinline__ void cg_run(const Team& tm, Shared& sh, int& ph, float* dsm, int mode, float* z,
                                     int k_outer) {
   const Prob& P = sh.P;
@@ -609,9 +609,9 @@ __device__ __noinline__ void cg_run(const Team& tm, Shared& sh, int& ph, float* 
   bool cont = sh.sc.cg_cont != 0;
   while (cont) {
     // p (vector partition, followed by a sum or a barrier) -> t = A p -> q = A^T t
-    apply<MaxT>(tm, P.fwd, P.nfwd, p, t, P.scratch, dsm, P.lanes);
+    apply<MaxT, MinB>(tm, P.fwd, P.nfwd, p, t, P.scratch, dsm, P.lanes);
     tsync(tm);
-    apply<MaxT>(tm, P.adj, P.nadj, t, q, P.scratch, dsm, P.lanes);
+    apply<MaxT, MinB>(tm, P.adj, P.nadj, t, q, P.scratch, dsm, P.lanes);
     tsync(tm);
     {
       Acc2 b[1];
@@ -749,7 +749,7 @@ __device__ void soc_norms(const Team& tm, Shared& sh, int& ph, float af, float a
   });
 }
 
-template <int MaxT>
+template <int MaxT, int MinB>
 __device__ void solve_one(const Team& tm, Shared& sh, float* dsm) {
   const unsigned long long t_start = gtimer();
   const Prob& P = sh.P;
@@ -783,11 +783,11 @@ __device__ void solve_one(const Team& tm, Shared& sh, float* dsm) {
       P.rhs[i] = __ldg(P.cf + i);
     });
     tsync(tm);
-    apply<MaxT>(tm, P.adj_m, P.nadj_m, P.bf, P.rhs, P.scratch, dsm, P.lanes);  // rhs = c - A^T b
+    apply<MaxT, MinB>(tm, P.adj_m, P.nadj_m, P.bf, P.rhs, P.scratch, dsm, P.lanes);  // rhs = c - A^T b
     tsync(tm);
-    cg_run<MaxT>(tm, sh, ph, dsm, CG_SETUP, P.gx, 0);
+    cg_run<MaxT, MinB>(tm, sh, ph, dsm, CG_SETUP, P.gx, 0);
     tsync(tm);
-    apply<MaxT>(tm, P.fwd, P.nfwd, P.gx, P.gy, P.scratch, dsm, P.lanes);  // A g_x
+    apply<MaxT, MinB>(tm, P.fwd, P.nfwd, P.gx, P.gy, P.scratch, dsm, P.lanes);  // A g_x
     tsync(tm);
     Acc2 a[1];
     each(tm, m, [&](int64_t i) {
@@ -825,10 +825,10 @@ __device__ void solve_one(const Team& tm, Shared& sh, float* dsm) {
     TV4(v, n) st4(P.rhs, v, ld4v(P.ux, v));
     TTAIL(i, n) P.rhs[i] = P.ux[i];
     tsync(tm);
-    apply<MaxT>(tm, P.adj_m, P.nadj_m, P.wy, P.rhs, P.scratch, dsm, P.lanes);
+    apply<MaxT, MinB>(tm, P.adj_m, P.nadj_m, P.wy, P.rhs, P.scratch, dsm, P.lanes);
     tsync(tm);
     // ---- z_x by CG, warm-started at the previous z_x
-    cg_run<MaxT>(tm, sh, ph, dsm, CG_ITER, P.zx, sh.sc.k);
+    cg_run<MaxT, MinB>(tm, sh, ph, dsm, CG_ITER, P.zx, sh.sc.k);
     // ---- z_y = w_y + A z_x (carried); u~_tau; then tau, kappa, the
     // iteration counter and this iteration's decisions
     {
@@ -916,8 +916,8 @@ __device__ void solve_one(const Team& tm, Shared& sh, float* dsm) {
     // ---- residuals and certificates
     if (chk && !sh.sc.stop) {
       tsync(tm);
-      apply<MaxT>(tm, P.fwd, P.nfwd, P.ux, P.cm, P.scratch, dsm, P.lanes);
-      apply<MaxT>(tm, P.adj, P.nadj, P.uy, P.cn, P.scratch, dsm, P.lanes);
+      apply<MaxT, MinB>(tm, P.fwd, P.nfwd, P.ux, P.cm, P.scratch, dsm, P.lanes);
+      apply<MaxT, MinB>(tm, P.adj, P.nadj, P.uy, P.cn, P.scratch, dsm, P.lanes);
       tsync(tm);
       // sums of k_resid (solver.cu): weighted by 1/D, 1/E when equilibrated
       const float tf = sh.sc.tau_f;
@@ -983,9 +983,9 @@ __device__ void solve_one(const Team& tm, Shared& sh, float* dsm) {
     if (ref) {
       if (threadIdx.x == 0) ++sh.sc.refreshes;
       tsync(tm);
-      apply<MaxT>(tm, P.fwd, P.nfwd, P.zx, P.az, P.scratch, dsm, P.lanes);
+      apply<MaxT, MinB>(tm, P.fwd, P.nfwd, P.zx, P.az, P.scratch, dsm, P.lanes);
       tsync(tm);
-      apply<MaxT>(tm, P.adj, P.nadj, P.az, P.gz, P.scratch, dsm, P.lanes);
+      apply<MaxT, MinB>(tm, P.adj, P.nadj, P.az, P.gz, P.scratch, dsm, P.lanes);
       tsync(tm);
       each(tm, n, [&](int64_t i) { P.gz[i] = P.zx[i] + P.gz[i]; });  // G z = lam z + A^T A z, lam = 1
     }
@@ -1063,8 +1063,8 @@ __device__ void load_prob(Shared& sh, const Prob* src) {
 
 // Persistent kernel: cluster teams take problems order[0, nbig), then every
 // CTA takes problems order[nbig, nbig + nsmall) alone.
-template <int MaxT>
-__global__ void __launch_bounds__(MaxT) k_team(const Prob* __restrict__ probs, const int32_t* __restrict__ order,
+template <int MaxT, int MinB>
+__global__ void __launch_bounds__(MaxT, MinB) k_team(const Prob* __restrict__ probs, const int32_t* __restrict__ order,
                                                int32_t nbig, int32_t nsmall, unsigned int* counters,
                                                int32_t cluster) {
   extern __shared__ __align__(16) float dsm[];
@@ -1083,7 +1083,7 @@ __global__ void __launch_bounds__(MaxT) k_team(const Prob* __restrict__ probs, c
       cl.sync();
       if (it >= nbig) break;
       load_prob(sh, probs + order[it]);
-      solve_one<MaxT>(tm, sh, dsm);
+      solve_one<MaxT, MinB>(tm, sh, dsm);
     }
   }
   tm.C = 1;
@@ -1097,7 +1097,7 @@ __global__ void __launch_bounds__(MaxT) k_team(const Prob* __restrict__ probs, c
     __syncthreads();
     if (it >= nsmall) break;
     load_prob(sh, probs + order[nbig + it]);
-    solve_one<MaxT>(tm, sh, dsm);
+    solve_one<MaxT, MinB>(tm, sh, dsm);
   }
 }
 
@@ -1419,15 +1419,15 @@ void fill_prob(cf_problem* P, const cf_schedule& s, bool do_setup, bool tune, Pr
 }
 
 struct Launch {
-  int C = 1, T = 512;
+  int C = 1, T = 512, B = 1;  // cluster size, threads per CTA, CTAs per SM the registers allow
   int64_t grid = 1;
   size_t smem = 0;
 };
 
-template <int MaxT>
+template <int MaxT, int MinB>
 cf_err launch_k(const Launch& L, const Prob* probs, const int32_t* order, int32_t nbig, int32_t nsmall,
                 unsigned int* counters, cudaStream_t s) {
-  auto kern = k_team<MaxT>;
+  auto kern = k_team<MaxT, MinB>;
   if (L.smem > 48 * 1024) CF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem));
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)L.grid);
@@ -1447,9 +1447,9 @@ cf_err launch_k(const Launch& L, const Prob* probs, const int32_t* order, int32_
   return CF_OK;
 }
 
-template <int MaxT>
+template <int MaxT, int MinB>
 cf_err max_grid(const Launch& L, int sm_count, int64_t* out) {
-  auto kern = k_team<MaxT>;
+  auto kern = k_team<MaxT, MinB>;
   if (L.smem > 48 * 1024) CF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem));
   if (L.C == 1) {
     int nb = 0;
@@ -1474,17 +1474,24 @@ cf_err max_grid(const Launch& L, int sm_count, int64_t* out) {
   return CF_OK;
 }
 
+template <int T, int B>
+cf_err dispatch_tb(const Launch& L, bool query, int sm_count, int64_t* grid, const Prob* probs,
+                   const int32_t* order, int32_t nbig, int32_t nsmall, unsigned int* counters, cudaStream_t s) {
+  return query ? max_grid<T, B>(L, sm_count, grid) : launch_k<T, B>(L, probs, order, nbig, nsmall, counters, s);
+}
+
 cf_err dispatch(const Launch& L, bool query, int sm_count, int64_t* grid, const Prob* probs,
                 const int32_t* order, int32_t nbig, int32_t nsmall, unsigned int* counters, cudaStream_t s) {
-  switch (L.T) {
-    case 256:
-      return query ? max_grid<256>(L, sm_count, grid) : launch_k<256>(L, probs, order, nbig, nsmall, counters, s);
-    case 512:
-      return query ? max_grid<512>(L, sm_count, grid) : launch_k<512>(L, probs, order, nbig, nsmall, counters, s);
-    case 1024:
-      return query ? max_grid<1024>(L, sm_count, grid) : launch_k<1024>(L, probs, order, nbig, nsmall, counters, s);
+  const int key = L.T * 8 + L.B;
+  switch (key) {
+    case 256 * 8 + 1: return dispatch_tb<256, 1>(L, query, sm_count, grid, probs, order, nbig, nsmall, counters, s);
+    case 256 * 8 + 2: return dispatch_tb<256, 2>(L, query, sm_count, grid, probs, order, nbig, nsmall, counters, s);
+    case 256 * 8 + 4: return dispatch_tb<256, 4>(L, query, sm_count, grid, probs, order, nbig, nsmall, counters, s);
+    case 512 * 8 + 1: return dispatch_tb<512, 1>(L, query, sm_count, grid, probs, order, nbig, nsmall, counters, s);
+    case 512 * 8 + 2: return dispatch_tb<512, 2>(L, query, sm_count, grid, probs, order, nbig, nsmall, counters, s);
+    case 1024 * 8 + 1: return dispatch_tb<1024, 1>(L, query, sm_count, grid, probs, order, nbig, nsmall, counters, s);
   }
-  return fail(CF_E_INVALID, "team engine: threads per CTA must be 256, 512 or 1024");
+  return fail(CF_E_INVALID, "team engine: unsupported threads per CTA x CTAs per SM");
 }
 
 // Launch table layout: counters (2), order (count), then the entries.
@@ -1532,6 +1539,7 @@ cf_err enqueue(cf_ctx* ctx, const cf_schedule& s, char* dev, size_t count, int32
                size_t smem, cudaStream_t st) {
   Launch L;
   L.T = s.threads;
+  L.B = s.ctas_per_sm;
   L.C = nbig > 0 ? s.cluster : 1;
   L.smem = smem;
   int64_t cap = 1;
@@ -1655,6 +1663,7 @@ cf_schedule default_schedule() {
   s.cluster = 4;
   s.threads = 512;
   s.csr_nnz_per_lane = 16;
+  s.ctas_per_sm = 1;
   s.team_bytes = 256e3;
   s.auto_max_bytes = 1e6;
   s.batch_max_bytes = 48e6;
@@ -1668,6 +1677,11 @@ bool schedule_valid(const cf_schedule& s, std::string* why) {
   }
   if (s.threads != 256 && s.threads != 512 && s.threads != 1024) {
     *why = "threads must be 256, 512 or 1024";
+    return false;
+  }
+  if (!((s.ctas_per_sm == 1) || (s.ctas_per_sm == 2 && s.threads <= 512) ||
+        (s.ctas_per_sm == 4 && s.threads == 256))) {
+    *why = "ctas_per_sm must be 1, 2 (threads <= 512) or 4 (threads 256)";
     return false;
   }
   if (s.csr_nnz_per_lane < 1 || s.csr_nnz_per_lane > 64) {
@@ -1786,11 +1800,13 @@ extern "C" cf_err solve_batch_tune(cf_problem* const* probs, int32_t count, int3
     cf_schedule b1 = held;
     b1.cluster = 1;
     double b1_ms = 1e300;
-    for (int T : {256, 512, 1024})
+    const int shapes[6][2] = {{256, 1}, {256, 2}, {256, 4}, {512, 1}, {512, 2}, {1024, 1}};
+    for (const auto& tb : shapes)
       for (int npl : {8, 16, 32, 64}) {
         cf_schedule c = held;
         c.cluster = 1;
-        c.threads = T;
+        c.threads = tb[0];
+        c.ctas_per_sm = tb[1];
         c.csr_nnz_per_lane = npl;
         CF_TRY(timed(c, &ms));
         if (ms < b1_ms) {

@@ -46,6 +46,8 @@ SCHEDULES = {
     "cluster2": dict(cluster=2, threads=512, team_bytes=0.0),
     "cluster4_lanes1": dict(cluster=4, threads=256, team_bytes=0.0, csr_nnz_per_lane=64),
     "cluster8": dict(cluster=8, threads=1024, team_bytes=0.0),
+    "cta512x2": dict(cluster=1, threads=512, ctas_per_sm=2),
+    "cta256x4_cluster2": dict(cluster=2, threads=256, ctas_per_sm=4, team_bytes=0.0),
 }
 
 FAMILIES = {
@@ -127,7 +129,7 @@ def test_autotuner_installs_a_schedule_that_solves(B):
     probs = _lp_batch(16, 902)
     Ps = [B.cone_problem_create(ctx, p) for p in probs]
     info = B.solve_batch_tune(Ps, iters=10)
-    assert info["problems"] == 16 and info["candidates"] == 2 + 12 + 9
+    assert info["problems"] == 16 and info["candidates"] == 2 + 24 + 9
     assert info["best_ms"] > 0 and info["best_ms"] <= info["default_ms"]
     got = B.get_schedule(ctx)
     assert got == info["best"]
@@ -172,7 +174,8 @@ def test_auto_routing_and_unsupported_problems(B):
 def test_schedule_validation(B):
     ctx = _ctx(B)
     assert B.get_schedule(ctx)["team_bytes"] == 256e3 and B.get_schedule(ctx)["auto_max_bytes"] == 1e6
-    for bad in (dict(cluster=3), dict(threads=128), dict(csr_nnz_per_lane=0), dict(team_bytes=-1.0)):
+    for bad in (dict(cluster=3), dict(threads=128), dict(csr_nnz_per_lane=0), dict(team_bytes=-1.0),
+                dict(ctas_per_sm=3), dict(threads=1024, ctas_per_sm=2)):
         with pytest.raises(B.CfError) as e:
             B.set_schedule(ctx, **bad)
         assert e.value.code == B.CF_E_INVALID
