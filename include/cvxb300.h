@@ -318,6 +318,23 @@ cf_err solve_batch(cf_problem* const* probs, int32_t count, const cf_settings* s
  * [1, 1024]; CF_E_STATE if the problem is already equilibrated. */
 cf_err cone_problem_equilibrate(cf_problem* p, int32_t iters, int32_t probes, uint64_t seed);
 
+/* Mixed-precision refinement (the BF16/FP8 accuracy reading beside Section
+ * 5.2's lasso operands): the problem keeps A as its instance and, from the
+ * next solve on, every CG step of the ADMM iterations applies inner -- an
+ * operator of A's shape, normally A stored in BF16 or FP8 -- instead of A.
+ * The carried A z_x and A^T A z_x then advance by inner's increments; the
+ * right-hand side w_x - A^T w_y, the setup (g = M^{-1} h), the residual and
+ * certificate tests, and the exact recomputation of the carried vectors
+ * every 50 iterations keep applying A, so the iteration's fixed points are
+ * those of the problem with A.  inner is referenced, not copied (it may be
+ * destroyed by the caller afterwards); NULL turns refinement off.  An
+ * equilibrated problem scales inner by the same D, E (also when it is
+ * equilibrated later).  Problems with an inner operator run on the graph
+ * engine only (CF_ENGINE_AUTO picks it; CF_ENGINE_TEAM is CF_E_INVALID).
+ * CF_E_INVALID: NULL p, inner's shape differs from A's, or inner belongs to
+ * another context. */
+cf_err cone_problem_set_inner(cf_problem* p, const cf_op* inner);
+
 /* The equilibration of a problem: D (m floats), E (n floats) -- host or
  * device buffers, may be NULL -- and sigma, rho (all 1 without
  * equilibration). */

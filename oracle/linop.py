@@ -111,18 +111,20 @@ def densify(op):
 
 # ------------------------------------------------------------ matrix-free
 def _leaf_matrix(op):
+    # cached per storage: trees that share a leaf's data may store it differently
     cache = op.setdefault("_oracle_cache", {})
-    if "M" not in cache:
+    key = ("M", op.get("storage", "fp32"))
+    if key not in cache:
         if op["kind"] == "dense":
-            cache["M"] = quant.dense_values(op["data"], op["storage"])
+            cache[key] = quant.dense_values(op["data"], op["storage"])
         else:
             import scipy.sparse as sp
             vals = np.asarray(op["val"], dtype=np.float32)
             if op.get("storage", "fp32") == "bf16":
                 vals = quant.bf16_round(vals)
-            cache["M"] = sp.csr_matrix((vals.astype(np.float64), op["col"], op["rowptr"]),
+            cache[key] = sp.csr_matrix((vals.astype(np.float64), op["col"], op["rowptr"]),
                                        shape=(op["m"], op["n"]))
-    return cache["M"]
+    return cache[key]
 
 
 def apply(op, x, adjoint=False):

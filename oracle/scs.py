@@ -113,19 +113,65 @@ class _LinSys:
         return z
 
 
-def subspace_step(op, b, c, g_x, g_y, hg, w, zx):
+def subspace_step(op, b, c, g_x, g_y, hg, w, zx, azx=None):
     """``u~ = (I + Q)^{-1} w`` given ``z_x`` solving
     ``(I + A^T A) z_x = w_x - A^T w_y``::
 
         z_y    = w_y + A z_x
         u~_tau = (w_tau + c^T z_x + b^T z_y) / (1 + h^T g)
         u~_xy  = z - u~_tau g
+
+    ``azx``: the value to use for ``A z_x`` (the carried one of the
+    refinement mode) instead of applying ``A``.
     """
     n, m = op.n, op.m
     w_y, w_tau = w[n:n + m], w[-1]
-    zy = w_y + op.mv(zx)
+    zy = w_y + (op.mv(zx) if azx is None else azx)
     ut_tau = (w_tau + c @ zx + b @ zy) / (1.0 + hg)
     return np.concatenate([zx - ut_tau * g_x, zy - ut_tau * g_y, [ut_tau]])
+
+
+def cg_carried(inner, rhs, zx, az, gz, stop_abs, max_steps, fixed_steps=None):
+    """The CG recurrence of Section 4.2 for ``(I + A^T A) z = rhs`` from
+    ``z = zx`` in the mixed-precision refinement mode (reading): ``az`` and
+    ``gz`` are the values carried for ``A zx`` and ``A^T A zx`` (exact after a
+    refresh), the initial residual is ``rhs - zx - gz``, and every step applies
+    the inner operand ``A'`` (a lower-precision copy of ``A``)::
+
+        t = A' p;  q = p + A'^T t;  a = r^T r / p^T q
+        zx += a p;  r -= a q;  az += a t;  gz += a A'^T t
+
+    Stops as ``cg.cg_recurrence`` does.  Returns ``(zx, az, gz, steps)``
+    (new arrays)."""
+    zx, az, gz = zx.copy(), az.copy(), gz.copy()
+    r = rhs - zx - gz
+    p = r.copy()
+    rr = float(r @ r)
+    k = 0
+    while True:
+        if fixed_steps is not None:
+            if k >= fixed_steps:
+                break
+        elif not (np.sqrt(rr) > stop_abs and k < max_steps):
+            break
+        t = inner.mv(p)
+        atat = inner.rmv(t)
+        q = p + atat
+        pq = float(p @ q)
+        a = rr / pq if pq > 0 else 0.0
+        zx += a * p
+        r -= a * q
+        az += a * t
+        gz += a * atat
+        rr_new = float(r @ r)
+        beta = rr_new / rr if rr > 0 else 0.0
+        p = r + beta * p
+        rr = rr_new
+        k += 1
+    return zx, az, gz, k
+
+
+REFINE_REFRESH = 50   # iterations between exact A z_x, A^T A z_x in refinement mode (reading)
 
 
 def setup(op, b, c, ls):
@@ -137,7 +183,8 @@ def setup(op, b, c, ls):
 
 def solve(A, b, c, cone, *, eps=1e-4, eps_infeas=None, alpha=1.5, max_iters=100000,
           check_interval=10, linsys="direct", cg_fixed_steps=None, cg_max_steps=50,
-          cg_tol_rel=1.0, cg_tol_exp=1.5, cg_tol_min=1e-12, trajectory=0, equil=None):
+          cg_tol_rel=1.0, cg_tol_exp=1.5, cg_tol_min=1e-12, trajectory=0, equil=None,
+          inner=None, refresh_interval=REFINE_REFRESH):
     """Run SCS on ``min c^T x s.t. A x + s = b, s in K`` in float64.
 
     ``linsys="direct"`` solves the subspace step exactly (Cholesky of
@@ -161,6 +208,17 @@ def solve(A, b, c, cone, *, eps=1e-4, eps_infeas=None, alpha=1.5, max_iters=1000
     factors), and the point returned is the original one.  ``u``, ``v`` and the
     trajectory stay in the scaled coordinates.
 
+    ``inner`` (an ``Operator`` or operator tree of ``A``'s shape, normally
+    ``A`` stored in BF16 or FP8) turns on mixed-precision refinement
+    (reading; needs ``linsys="cg"``): the CG steps apply ``inner`` through
+    ``cg_carried``, which carries ``A z_x`` and ``A^T A z_x`` along, while the
+    right-hand side ``w_x - A^T w_y``, the setup, the termination tests and,
+    every ``refresh_interval`` iterations, an exact recomputation of the two
+    carried vectors use ``A``.  Both sides of the first CG residual then agree
+    with ``A`` up to the drift since the last refresh, so the fixed points are
+    those of the problem with ``A``.  (With ``equil``, ``inner`` is scaled by
+    the same ``D``, ``E``.)
+
     Returns a dict with ``x, y, s, status, iters, pobj, dobj, pri, dual, gap,
     u, v, cg_steps``, the wall times ``t_setup`` / ``t_iter`` of the setup and
     of the iterations, and, if ``trajectory`` > 0, the first ``trajectory``
@@ -180,6 +238,15 @@ def solve(A, b, c, cone, *, eps=1e-4, eps_infeas=None, alpha=1.5, max_iters=1000
     back = (op0, b0, c0, Dv, Ev, sigma, rho)
     if eps_infeas is None:
         eps_infeas = eps
+    opi = None
+    if inner is not None:
+        if linsys != "cg":
+            raise ValueError("refinement (inner) needs linsys='cg'")
+        opi = inner if isinstance(inner, Operator) else Operator(inner)
+        if (opi.m, opi.n) != (m, n):
+            raise ValueError("inner operator shape differs from A's")
+        if equil is not None:
+            opi = equil_mod.ScaledOperator(opi, Dv, Ev)
     t0 = time.perf_counter()
     ls = _LinSys(op, "direct" if linsys == "direct" else "cg")
 
@@ -191,6 +258,7 @@ def solve(A, b, c, cone, *, eps=1e-4, eps_infeas=None, alpha=1.5, max_iters=1000
     u[-1] = 1.0
     v[-1] = 1.0
     zx = np.zeros(n)
+    az, gz = np.zeros(m), np.zeros(n)     # carried A z_x, A^T A z_x (refinement)
     traj_u, traj_v = [], []
     cg_steps = 0
     status = MAX_ITERS
@@ -205,11 +273,15 @@ def solve(A, b, c, cone, *, eps=1e-4, eps_infeas=None, alpha=1.5, max_iters=1000
         else:
             thr = max(cg_tol_min,
                       cg_tol_rel * float(np.linalg.norm(rhs)) * (k + 1.0) ** (-cg_tol_exp))
-            zx, steps, _ = cg_mod.cg_recurrence(ls.gram, rhs, zx, stop_abs=thr,
-                                                max_steps=cg_max_steps,
-                                                fixed_steps=cg_fixed_steps)
+            if opi is None:
+                zx, steps, _ = cg_mod.cg_recurrence(ls.gram, rhs, zx, stop_abs=thr,
+                                                    max_steps=cg_max_steps,
+                                                    fixed_steps=cg_fixed_steps)
+            else:
+                zx, az, gz, steps = cg_carried(opi, rhs, zx, az, gz, thr, cg_max_steps,
+                                               cg_fixed_steps)
             cg_steps += steps
-        ut = subspace_step(op, b, c, g_x, g_y, hg, w, zx)
+        ut = subspace_step(op, b, c, g_x, g_y, hg, w, zx, None if opi is None else az)
         u_hat = alpha * ut + (1.0 - alpha) * u
         pre = u_hat - v
         u_new = np.empty_like(u)
@@ -230,6 +302,9 @@ def solve(A, b, c, cone, *, eps=1e-4, eps_infeas=None, alpha=1.5, max_iters=1000
             if st is not None:
                 status = st
                 break
+        if opi is not None and it % refresh_interval == 0:
+            az = op.mv(zx)
+            gz = op.rmv(az)
 
     t2 = time.perf_counter()
     tau = u[-1]
@@ -284,7 +359,8 @@ def problem_solve(prob, equilibrate=None, **kw):
     """``solve`` on a generator problem dict (uses its operator tree).
     ``equilibrate``: None, or a dict of ``equil.equilibrate`` keyword
     arguments (``iters``, ``probes``, ``seed``) to scale the data first; the
-    scalings are returned under ``"equil"``."""
+    scalings are returned under ``"equil"``.  ``inner`` may be given as an
+    operator tree (the refinement mode of ``solve``)."""
     if equilibrate is None:
         return solve(prob["A"], prob["b"], prob["c"], prob["cone"], **kw)
     op = Operator(prob["A"])

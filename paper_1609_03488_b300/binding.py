@@ -113,6 +113,7 @@ _sig = {
     "cf_problem_team_info": (C.c_int, [P, C.POINTER(C.c_int32), C.POINTER(C.c_double), C.c_char_p,
                                        C.c_size_t]),
     "cone_problem_equilibrate": (C.c_int, [P, C.c_int32, C.c_int32, C.c_uint64]),
+    "cone_problem_set_inner": (C.c_int, [P, P]),
     "cf_problem_scaling": (C.c_int, [P, P, P, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "cg_solve": (C.c_int, [P, C.c_double, P, P, C.c_int32, C.c_double, C.POINTER(C.c_int32),
                            C.POINTER(C.c_double)]),
@@ -417,6 +418,15 @@ def solve_batch(problems, st=None):
 def equilibrate(problem, iters=10, probes=8, seed=0x5EED):
     """cone_problem_equilibrate: scale the problem's data (see the header)."""
     check(lib.cone_problem_equilibrate(problem.h, int(iters), int(probes), int(seed)), "cone_problem_equilibrate")
+
+
+def set_inner(problem, inner):
+    """cone_problem_set_inner: ``inner`` is an Operator, an operator tree
+    (built here, e.g. ``synth.with_storage(prob["A"], "fp8")``) or None."""
+    if isinstance(inner, dict):
+        inner = build_operator(problem.ctx, inner)
+    check(lib.cone_problem_set_inner(problem.h, inner.h if inner is not None else None), "cone_problem_set_inner")
+    return inner
 
 
 def scaling(problem):

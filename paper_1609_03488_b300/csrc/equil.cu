@@ -242,6 +242,15 @@ extern "C" cf_err cone_problem_equilibrate(cf_problem* P, int32_t iters, int32_t
   P->eq_einv = einv;
   P->A_orig = P->A;  // keeps its reference
   P->A = prod;
+  if (P->inner) {
+    // refinement: the inner operator takes the same diagonals
+    cf_op* parts[3] = {prod->parts[0], P->inner, prod->parts[2]};
+    cf_op* wrapped = nullptr;
+    r = operator_compose(P->ctx, CF_PRODUCT, parts, 3, 1.0, &wrapped);
+    if (r != CF_OK) return r;
+    P->inner_orig = P->inner;  // keeps its reference
+    P->inner = wrapped;
+  }
   // new operator: new workspace sizes, graphs, team plan and setup
   release_state(P);
   team::release(P);

@@ -35,7 +35,8 @@ struct Req {
 };
 
 size_t problem_bytes(cf_problem* p) {
-  return problem_state_bytes(p) + p->persist_bytes + op_tree_bytes(p->A);
+  return problem_state_bytes(p) + p->persist_bytes + op_tree_bytes(p->A) +
+         (p->inner ? op_tree_bytes(p->inner) : 0);
 }
 
 }  // namespace

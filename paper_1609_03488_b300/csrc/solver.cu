@@ -787,8 +787,11 @@ void emit_cg_step(const CgBufs& b, int mode, const Conds& cd, cudaStream_t s) {
   k_cg_p<<<grid_for(b.n), kThreads, 0, s>>>(b.ctl, b.n, b.r, b.p, mode, cd.cg, cd.in_graph);
 }
 
-CgBufs cg_bufs(cf_problem* P, float* z) {
-  return CgBufs{P->ctl, P->A, P->n, P->m, z, P->rhs, P->r, P->p, P->qv, P->t, P->ws, P->gz, P->az, P->part};
+// CG buffers on z; the ADMM iterations' CG steps apply the inner operator
+// when one is set (the setup's always apply A).
+CgBufs cg_bufs(cf_problem* P, float* z, bool iter = false) {
+  const cf_op* A = iter && P->inner ? P->inner : P->A;
+  return CgBufs{P->ctl, A, P->n, P->m, z, P->rhs, P->r, P->p, P->qv, P->t, P->ws, P->gz, P->az, P->part};
 }
 
 // ---- the pieces of the setup and of one ADMM iteration
@@ -907,7 +910,7 @@ cf_err build_iter_graph(cf_problem* P) {
   cudaGraph_t C = nullptr;
   CF_TRY(add_cond(B, tail, cd.cg, cudaGraphCondTypeWhile, &cgn, &C));
   CF_TRY(seg_begin(s, C, {}));
-  emit_cg_step(cg_bufs(P, P->zx), CG_ITER, cd, s);
+  emit_cg_step(cg_bufs(P, P->zx, true), CG_ITER, cd, s);
   CF_TRY(seg_end(s, &tmp));
   CF_TRY(seg_begin(s, B, {cgn}));
   emit_post_cg(P, cd, s);
@@ -976,7 +979,7 @@ cf_err run_iterations_host(cf_problem* P) {
   cudaStream_t s = P->stream;
   Conds cd;
   cd.in_graph = 0;
-  const CgBufs cb = cg_bufs(P, P->zx);
+  const CgBufs cb = cg_bufs(P, P->zx, true);
   const Settings& st = P->ctl_host->st;
   const int cg_cap = st.cg_fixed > 0 ? st.cg_fixed : st.cg_max;
   Flags f;
@@ -1007,11 +1010,17 @@ cf_err run_iterations_host(cf_problem* P) {
 }  // namespace
 
 // ------------------------------------------------------------ state
+size_t solver_ws_floats(const cf_problem* P) {
+  size_t w = std::max(op_ws_floats(P->A, false), op_ws_floats(P->A, true));
+  if (P->inner) w = std::max(w, std::max(op_ws_floats(P->inner, false), op_ws_floats(P->inner, true)));
+  return w;
+}
+
 size_t problem_state_bytes(const cf_problem* P) {
   const size_t n = P->n, m = P->m, N = n + m + 1;
   auto f = [](size_t k) { return align_up(k * sizeof(float), 256); };
   auto d = [](size_t k) { return align_up(k * sizeof(double), 256); };
-  size_t wsf = std::max(op_ws_floats(P->A, false), op_ws_floats(P->A, true));
+  size_t wsf = solver_ws_floats(P);
   size_t b = 0;
   b += 9 * f(n);            // ux zx rhs r p q gx cn gz
   b += 8 * f(m);            // uy vs wy t zy gy cm az
@@ -1045,7 +1054,7 @@ cf_err ensure_state(cf_problem* P) {
   P->uy = takef(m); P->vs = takef(m); P->wy = takef(m); P->t = takef(m);
   P->zy = takef(m); P->gy = takef(m); P->cm = takef(m);
   P->gz = takef(n); P->az = takef(m);
-  P->ws = takef(std::max(op_ws_floats(P->A, false), op_ws_floats(P->A, true)));
+  P->ws = takef(solver_ws_floats(P));
   P->team_scratch = takef(std::max<size_t>(team::scratch_floats(P), 1));
   P->part = taked((size_t)kMaxRedBlocks * kRedSlots);
   P->chunk_n2 = taked((size_t)std::max<int64_t>(P->nchunk, 1));
@@ -1465,6 +1474,8 @@ void cf_problem_destroy(cf_problem* P) {
   team::release(P);
   if (P->eq) cudaFree(P->eq);
   if (P->A_orig) cf_op_destroy(P->A_orig);
+  if (P->inner) cf_op_destroy(P->inner);
+  if (P->inner_orig) cf_op_destroy(P->inner_orig);
   if (P->bf) cudaFree(P->bf);  // base of the persistent block
   if (P->ctl_host) cudaFreeHost(P->ctl_host);
   if (P->flags_host) cudaFreeHost(P->flags_host);
@@ -1473,6 +1484,44 @@ void cf_problem_destroy(cf_problem* P) {
   if (P->stream) cudaStreamDestroy(P->stream);
   if (P->A) cf_op_destroy(P->A);
   delete P;
+}
+
+cf_err cone_problem_set_inner(cf_problem* P, const cf_op* inner) {
+  if (!P) return fail(CF_E_INVALID, "cone_problem_set_inner: NULL problem");
+  if (inner && (inner->m != P->m || inner->n != P->n))
+    return fail(CF_E_INVALID, "cone_problem_set_inner: inner operator is " + std::to_string(inner->m) + " x " +
+                                  std::to_string(inner->n) + ", A is " + std::to_string(P->m) + " x " +
+                                  std::to_string(P->n));
+  if (inner && inner->ctx != P->ctx)
+    return fail(CF_E_INVALID, "cone_problem_set_inner: inner operator belongs to another context");
+  std::lock_guard<std::mutex> lk(P->mtx);
+  DevGuard guard(P->device);
+  if (P->stream) CF_CUDA(cudaStreamSynchronize(P->stream));
+  cf_op* wrapped = nullptr;
+  if (inner && P->A_orig) {
+    // equilibrated: the same diagonals as A's (parts 0 and 2 of D A E)
+    cf_op* parts[3] = {P->A->parts[0], const_cast<cf_op*>(inner), P->A->parts[2]};
+    CF_TRY(operator_compose(P->ctx, CF_PRODUCT, parts, 3, 1.0, &wrapped));
+  }
+  if (P->inner) cf_op_destroy(P->inner);
+  if (P->inner_orig) cf_op_destroy(P->inner_orig);
+  P->inner = P->inner_orig = nullptr;
+  if (inner) {
+    op_retain(const_cast<cf_op*>(inner));
+    if (wrapped) {
+      P->inner = wrapped;
+      P->inner_orig = const_cast<cf_op*>(inner);
+    } else {
+      P->inner = const_cast<cf_op*>(inner);
+    }
+  }
+  // new workspace sizes and graphs; the team plan records the refusal
+  release_state(P);
+  team::release(P);
+  cf_err r = team::plan_problem(P);
+  P->setup_done = false;
+  P->setup_sig = 0;
+  return r;
 }
 
 cf_err solve(cf_problem* P, const cf_settings* st, double* x, double* y, double* s,

@@ -91,10 +91,17 @@ struct cf_problem {
   float *eq_d = nullptr, *eq_dinv = nullptr, *eq_e = nullptr, *eq_einv = nullptr;
   double sigma = 1.0, rho = 1.0;
   cf_op* A_orig = nullptr;
+  // mixed-precision refinement: the operator the ADMM iterations' CG steps
+  // apply (nullptr: A); equilibrated, diag(D) inner diag(E) with the user's
+  // operator kept in inner_orig
+  cf_op* inner = nullptr;
+  cf_op* inner_orig = nullptr;
 };
 
 namespace cf {
 size_t problem_state_bytes(const cf_problem* p);
+// Workspace floats of every operator the solver applies (A and inner).
+size_t solver_ws_floats(const cf_problem* p);
 cf_err ensure_state(cf_problem* p);
 void release_state(cf_problem* p);
 // join_ctx: make the context stream wait for this solve right away (single

@@ -1263,6 +1263,10 @@ cf_err plan_problem(cf_problem* P) {
     pl.why = "more than " + std::to_string(kMaxSeg) + " second-order cones";
     return CF_OK;
   }
+  if (P->inner) {
+    pl.why = "an inner operator (mixed-precision refinement) runs on the graph engine";
+    return CF_OK;
+  }
   // an equilibrated operator diag(D) A diag(E): A's terms with the scalings
   // folded in (inputs scaled by E forward / D adjoint, outputs by D / E)
   const cf_op* core = P->A;

@@ -78,6 +78,17 @@ def zero(m, n):
     return {"kind": "zero", "m": int(m), "n": int(n)}
 
 
+def with_storage(tree, storage):
+    """A copy of an operator tree whose dense and CSR leaves are stored in
+    ``storage`` (the data arrays are shared, not copied): the lower-precision
+    inner operand of the refinement mode, built from the float32 instance."""
+    if tree["kind"] in ("dense", "csr"):
+        return {k: v for k, v in tree.items() if not k.startswith("_")} | {"storage": storage}
+    if "parts" in tree:
+        return {**tree, "parts": [with_storage(p, storage) for p in tree["parts"]]}
+    return tree
+
+
 def scale(alpha, part):
     return {"kind": "scale", "alpha": float(alpha), "parts": [part],
             "m": part["m"], "n": part["n"]}

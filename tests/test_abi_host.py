@@ -88,6 +88,8 @@ def test_null_arguments_are_rejected_without_a_device():
     assert b.lib.solve(None, None, None, None, None, None, None, None) == b.CF_E_INVALID
     assert b.lib.cone_problem_create(None, None, None, 0, None, 0, None, C.byref(h)) == b.CF_E_INVALID
     assert b.lib.serve_wait(None, 1, 0, None, None, None, None) == b.CF_E_INVALID
+    assert b.lib.cone_problem_set_inner(None, None) == b.CF_E_INVALID
+    assert "NULL problem" in b.cf_last_error()
     b.lib.cf_op_destroy(None)
     b.lib.cf_problem_destroy(None)
     b.lib.serve_destroy(None)
