@@ -43,6 +43,9 @@ METRIC = "ADMM iters/s"
 # source it was taken on.
 EQUIL = dict(iters=10, probes=8, seed=0x5EED)
 CONV_NCU = {"traffic_bytes": 4029184, "src_sha256_16": "f372736cf1cfc748"}
+FFT_NCU = {"traffic_bytes": None, "src_sha256_16": None}
+FFT_N = 4096
+FFT_AUTO_LP = (256, 2048)   # padded tap counts for which the library's auto method takes the FFT
 FP32_LANES_PER_SM = 128
 L2_FLUSH_BYTES = 256 << 20
 
@@ -83,14 +86,19 @@ def parse():
                     help="deconv / lp-batch: matrix-free equilibration of each problem (10 Ruiz steps x 8 probes)")
     ap.add_argument("--cg-tol-rel", type=float, default=None,
                     help="CG tolerance prefactor (default: 10 for the equilibrated large deconvolution, else the library's 1)")
+    ap.add_argument("--conv", default="auto", choices=["auto", "direct", "fft"],
+                    help="deconv: how the 1-D convolution leaf is evaluated (auto: FFT for 256..2048 taps)")
     ap.add_argument("--host-loop", action="store_true",
                     help="launch the same kernels from the host instead of one CUDA graph per solve "
                          "(for profilers that cannot see kernels inside graph conditional nodes)")
     return ap.parse_args()
 
 
-def conv_src_sha():
+def conv_src_sha(fft=False):
     import hashlib
+    if fft:
+        src = open(os.path.join(ROOT, "paper_1609_03488_b300", "csrc", "k_fftconv.cu")).read()
+        return hashlib.sha256(src.encode()).hexdigest()[:16]
     src = open(os.path.join(ROOT, "paper_1609_03488_b300", "csrc", "k_leaf.cu")).read()
     a = src.index("// ------------------------------------------------------------ 1-D convolution")
     b = src.index("// ------------------------------------------------------------ 2-D convolution")
@@ -618,11 +626,14 @@ def main():
 
     W = WORKLOAD_SMALL if small else WORKLOAD
     eq = args.equil == "on"
-    # CG prefactor per workload (measured): 10 on the equilibrated n=1e6
-    # deconvolution (1280 iterations / 0.69 s to 1e-4 vs 1980 / 3.3 s at 1),
-    # 1 on the small one (750 iterations vs 2090 at 10)
-    cg_rel = args.cg_tol_rel if args.cg_tol_rel is not None else (10.0 if (eq and not small) else 1.0)
+    # CG prefactor per workload (measured): 30 on the equilibrated n=1e6
+    # deconvolution (time to 1e-4 with the FFT convolution at 1 / 3 / 10 / 30:
+    # 2.08 / 3.71 / 0.93 / 0.51 s; 2090 / 4090 / 2080 / 2120 iterations; the
+    # direct sum: 2.50 / 5.55 / 0.59 / 0.75 s), 1 on the small one (750
+    # iterations vs 2090 at 10)
+    cg_rel = args.cg_tol_rel if args.cg_tol_rel is not None else (30.0 if (eq and not small) else 1.0)
     prob = synth.deconv(**{**W, "seed": W["seed"] + rank})
+    prob["A"] = synth.with_conv_method(prob["A"], args.conv)
     n, m = prob["A"]["n"], prob["A"]["m"]
     # a dedicated (non-default) stream: the library launches on it and the
     # CUDA events below are recorded on it
@@ -674,7 +685,7 @@ def main():
     value = it_total / (t_max / 1e3)
 
     # ---- dominant kernel: the 1-D convolution, timed live on the same stream
-    conv = B.cf_op_conv1d(ctx, prob["meta"]["kernel"], W["n_x"])
+    conv = B.cf_op_conv1d(ctx, prob["meta"]["kernel"], W["n_x"], args.conv)
     L = W["L"]
     xin = torch.rand(W["n_x"], device=dev)
     yin = torch.rand(W["n_x"] + L - 1, device=dev)
@@ -697,21 +708,36 @@ def main():
     torch.cuda.synchronize()
     t_fwd = e0.elapsed_time(e1) / reps / 1e3
     t_adj = e2.elapsed_time(e3) / reps / 1e3
-    flops_fwd = 2.0 * L * (W["n_x"] + L - 1)
-    flops_adj = 2.0 * L * W["n_x"]
+    direct_fwd = 2.0 * L * (W["n_x"] + L - 1)
+    direct_adj = 2.0 * L * W["n_x"]
+    Lp = (L + 15) // 16 * 16
+    fft = args.conv == "fft" or (args.conv == "auto" and FFT_AUTO_LP[0] <= Lp <= FFT_AUTO_LP[1])
+    if fft:
+        # overlap-save: per pair of segments one complex FFT_N-point transform
+        # each way (5 N log2 N flops, the usual count) and the spectrum product
+        v = FFT_N - Lp + 1
+        per_pair = 2 * 5 * FFT_N * np.log2(FFT_N) + 6 * FFT_N
+        flops_fwd = per_pair * np.ceil((W["n_x"] + L - 1) / (2 * v))
+        flops_adj = per_pair * np.ceil(W["n_x"] / (2 * v))
+    else:
+        flops_fwd, flops_adj = direct_fwd, direct_adj
     achieved = (flops_fwd + flops_adj) / (t_fwd + t_adj) / 1e12
     pk = peaks()
     sm_count = ctx.sm_count
     sm_max = pk.get("sm_max_mhz", 2032.0)
     alu_peak = sm_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-    roofline = {"bound": "alu", "kernel": "k_conv1d", "achieved": achieved, "peak": alu_peak,
-                "unit": "TFLOP/s", "frac": achieved / alu_peak,
-                "traffic": (CONV_NCU["traffic_bytes"] if conv_src_sha() == CONV_NCU["src_sha256_16"] and not small
+    ncu = FFT_NCU if fft else CONV_NCU
+    roofline = {"bound": "alu", "kernel": "k_conv1d_fft" if fft else "k_conv1d", "achieved": achieved,
+                "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved / alu_peak,
+                "traffic": (ncu["traffic_bytes"] if conv_src_sha(fft) == ncu["src_sha256_16"] and not small
                             else None),
                 "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
                 "peak_source": f"derived: {sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x {sm_max:.0f} MHz (max SM clock of measured)",
                 "per_launch_ms": {"forward": 1e3 * t_fwd, "adjoint": 1e3 * t_adj},
-                "flops_per_launch": {"forward": flops_fwd, "adjoint": flops_adj}}
+                "flops_per_launch": {"forward": flops_fwd, "adjoint": flops_adj},
+                "flops_definition": ("FFT method: pairs x (2 x 5 N log2 N + 6 N), N = 4096" if fft
+                                     else "direct sum: 2 L per output"),
+                "direct_sum_equivalent_TFLOPs": (direct_fwd + direct_adj) / (t_fwd + t_adj) / 1e12}
 
     team = all(i["kernel_launches"] == 1 for i in infos)
     if team:

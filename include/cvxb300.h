@@ -208,8 +208,19 @@ cf_err cf_op_csr(cf_ctx* ctx, int64_t m, int64_t n, int64_t nnz, const int32_t* 
                  const int32_t* col, const float* val, cf_prec storage, cf_op** out);
 
 /* Full 1-D convolution with a length-L kernel: (k * x)[i] = sum_l k[l] x[i-l],
- * an (n + L - 1) x n operator (Section 5.3's c * x). */
+ * an (n + L - 1) x n operator (Section 5.3's c * x).  Same as
+ * cf_op_conv1d_method with CF_CONV_AUTO. */
 cf_err cf_op_conv1d(cf_ctx* ctx, int64_t n, const float* kernel, int64_t L, cf_op** out);
+
+/* How a 1-D convolution leaf is evaluated: the direct sum (FP32 FMAs over
+ * the taps), or overlap-save FFTs of 4096 points in FP32 (Section 2's
+ * FFT-based convolution; taps padded to a multiple of 16 must number at most
+ * 2048, else CF_E_INVALID).  CF_CONV_AUTO takes the FFT for 256 to 2048
+ * padded taps.  The FFT's error is bounded in the 2-norm of each
+ * 4096-sample input segment rather than entry by entry. */
+typedef enum { CF_CONV_AUTO = 0, CF_CONV_DIRECT = 1, CF_CONV_FFT = 2 } cf_conv_method;
+cf_err cf_op_conv1d_method(cf_ctx* ctx, int64_t n, const float* kernel, int64_t L, int32_t method,
+                           cf_op** out);
 
 /* Full 2-D convolution of an h x w image (row-major) with a kh x kw kernel:
  * Y[a, b] = sum_{p,q} K[p, q] X[a-p, b-q], output (h+kh-1) x (w+kw-1). */

@@ -92,6 +92,7 @@ _sig = {
     "cf_op_dense": (C.c_int, [P, C.c_int64, C.c_int64, P, C.c_int, PP]),
     "cf_op_csr": (C.c_int, [P, C.c_int64, C.c_int64, C.c_int64, P, P, P, C.c_int, PP]),
     "cf_op_conv1d": (C.c_int, [P, C.c_int64, P, C.c_int64, PP]),
+    "cf_op_conv1d_method": (C.c_int, [P, C.c_int64, P, C.c_int64, C.c_int32, PP]),
     "cf_op_conv2d": (C.c_int, [P, C.c_int64, C.c_int64, P, C.c_int64, C.c_int64, PP]),
     "cf_op_diag": (C.c_int, [P, C.c_int64, P, PP]),
     "cf_op_zero": (C.c_int, [P, C.c_int64, C.c_int64, PP]),
@@ -309,9 +310,14 @@ def cf_op_csr(ctx, m, n, rowptr, col, val, storage="fp32"):
                               PREC[storage]))
 
 
-def cf_op_conv1d(ctx, kernel, n):
+CONV_METHOD = {"auto": 0, "direct": 1, "fft": 2}
+
+
+def cf_op_conv1d(ctx, kernel, n, method="auto"):
+    """1-D full convolution leaf; method "auto", "direct" or "fft"
+    (cf_op_conv1d_method)."""
     kernel = _f32(kernel)
-    return Operator(ctx, _new("cf_op_conv1d", ctx.h, n, _ptr(kernel), kernel.size))
+    return Operator(ctx, _new("cf_op_conv1d_method", ctx.h, n, _ptr(kernel), kernel.size, CONV_METHOD[method]))
 
 
 def cf_op_conv2d(ctx, kernel, h, w):
@@ -344,7 +350,7 @@ def build_operator(ctx, node):
         return cf_op_csr(ctx, node["m"], node["n"], node["rowptr"], node["col"], node["val"],
                          node.get("storage", "fp32"))
     if k == "conv1d":
-        return cf_op_conv1d(ctx, node["kernel"], node["n"])
+        return cf_op_conv1d(ctx, node["kernel"], node["n"], node.get("method", "auto"))
     if k == "conv2d":
         return cf_op_conv2d(ctx, node["kernel"], node["h"], node["w"])
     if k == "diag":

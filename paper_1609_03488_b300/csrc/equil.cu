@@ -51,9 +51,15 @@ __global__ void k_sqacc(int64_t n, const float* __restrict__ scale, const float*
   }
 }
 
-// One CTA per second-order cone block: every row gets the block's mean.
-__global__ void k_block_mean(const int64_t* __restrict__ lohi, float* __restrict__ acc) {
-  const int64_t lo = lohi[2 * blockIdx.x], hi = lohi[2 * blockIdx.x + 1];
+// Every row of a second-order cone block gets the block's mean, in three
+// launches over chunks of at most kMeanChunk rows (chunk c: rows
+// [ch[3c], ch[3c + 1]) of block ch[3c + 2]): per-chunk FP64 sums, per-block
+// sums of its chunks in chunk order, then the fill.
+constexpr int64_t kMeanChunk = 16384;
+
+__global__ void k_block_part(const int64_t* __restrict__ ch, const float* __restrict__ acc,
+                             double* __restrict__ part) {
+  const int64_t lo = ch[3 * blockIdx.x], hi = ch[3 * blockIdx.x + 1];
   __shared__ double sh[32];
   double s = 0.0;
   for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) s += (double)acc[i];
@@ -63,11 +69,25 @@ __global__ void k_block_mean(const int64_t* __restrict__ lohi, float* __restrict
   if (threadIdx.x < 32) {
     double t = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
     for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
-    if (threadIdx.x == 0) sh[0] = t / (double)(hi - lo);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
   }
-  __syncthreads();
-  const float mean = (float)sh[0];
-  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) acc[i] = mean;
+}
+
+// bk[3b], bk[3b + 1]: first chunk and chunk count of block b; bk[3b + 2]: rows
+__global__ void k_block_final(int64_t nblk, const int64_t* __restrict__ bk, const double* __restrict__ part,
+                              float* __restrict__ mean) {
+  const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (b >= nblk) return;
+  double s = 0.0;
+  for (int64_t c = bk[3 * b]; c < bk[3 * b] + bk[3 * b + 1]; ++c) s += part[c];
+  mean[b] = (float)(s / (double)bk[3 * b + 2]);
+}
+
+__global__ void k_block_fill(const int64_t* __restrict__ ch, const float* __restrict__ mean,
+                             float* __restrict__ acc) {
+  const int64_t lo = ch[3 * blockIdx.x], hi = ch[3 * blockIdx.x + 1];
+  const float v = mean[ch[3 * blockIdx.x + 2]];
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) acc[i] = v;
 }
 
 // s[i] <- clip(s[i] / (acc[i] / K)^(1/4)); a row / column whose estimated
@@ -173,18 +193,37 @@ extern "C" cf_err cone_problem_equilibrate(cf_problem* P, int32_t iters, int32_t
     float* racc = yout + align_up(m, 64);
     float* ws = racc + align_up(m, 64);
     double* part = (double*)(ws + align_up(wsf, 64));
-    // second-order cone blocks
-    std::vector<int64_t> lohi;
+    // second-order cone blocks, in chunks: table ch (lo, hi, block) per
+    // chunk, bk (first chunk, chunks, rows) per block, then the per-chunk
+    // sums (double) and per-block means (float) -- one allocation
+    std::vector<int64_t> ch, bk;
     int64_t off = P->z + P->l;
-    for (int64_t q : P->q) {
-      lohi.push_back(off);
-      lohi.push_back(off + q);
+    for (size_t b = 0; b < P->q.size(); ++b) {
+      const int64_t q = P->q[b];
+      bk.push_back((int64_t)ch.size() / 3);
+      for (int64_t s = 0; s < q; s += kMeanChunk) {
+        ch.push_back(off + s);
+        ch.push_back(off + std::min(q, s + kMeanChunk));
+        ch.push_back((int64_t)b);
+      }
+      bk.push_back((int64_t)ch.size() / 3 - bk.back());
+      bk.push_back(q);
       off += q;
     }
+    const int64_t nchunk = (int64_t)ch.size() / 3, nblk = (int64_t)P->q.size();
     int64_t* lohi_dev = nullptr;
-    if (!lohi.empty()) {
-      CF_CUDA(cudaMalloc((void**)&lohi_dev, lohi.size() * sizeof(int64_t)));
-      CF_CUDA(cudaMemcpy(lohi_dev, lohi.data(), lohi.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+    int64_t *ch_dev = nullptr, *bk_dev = nullptr;
+    double* part_dev = nullptr;
+    float* mean_dev = nullptr;
+    if (nblk > 0) {
+      const size_t words = ch.size() + bk.size() + (size_t)nchunk + (size_t)nblk;  // 8-byte words
+      CF_CUDA(cudaMalloc((void**)&lohi_dev, words * sizeof(int64_t)));
+      ch_dev = lohi_dev;
+      bk_dev = ch_dev + ch.size();
+      part_dev = (double*)(bk_dev + bk.size());
+      mean_dev = (float*)(part_dev + nchunk);
+      CF_CUDA(cudaMemcpy(ch_dev, ch.data(), ch.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+      CF_CUDA(cudaMemcpy(bk_dev, bk.data(), bk.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
     }
     const unsigned gm = (unsigned)grid_for(m), gn = (unsigned)grid_for(n);
     k_fill1<<<gm, kThreads, 0, st>>>(m, d);
@@ -201,7 +240,11 @@ extern "C" cf_err cone_problem_equilibrate(cf_problem* P, int32_t iters, int32_t
         op_apply(P->A, true, 1.f, yin, xout, false, ws, st);
         k_sqacc<<<gn, kThreads, 0, st>>>(n, ev, xout, cacc);
       }
-      if (!lohi.empty()) k_block_mean<<<(unsigned)(lohi.size() / 2), 1024, 0, st>>>(lohi_dev, racc);
+      if (nblk > 0) {
+        k_block_part<<<(unsigned)nchunk, 256, 0, st>>>(ch_dev, racc, part_dev);
+        k_block_final<<<(unsigned)((nblk + 127) / 128), 128, 0, st>>>(nblk, bk_dev, part_dev, mean_dev);
+        k_block_fill<<<(unsigned)nchunk, 256, 0, st>>>(ch_dev, mean_dev, racc);
+      }
       k_ruiz<<<gm, kThreads, 0, st>>>(m, 1.f / (float)probes, racc, d);
       k_ruiz<<<gn, kThreads, 0, st>>>(n, 1.f / (float)probes, cacc, ev);
       CF_CUDA(cudaGetLastError());

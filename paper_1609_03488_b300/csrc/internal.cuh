@@ -102,6 +102,9 @@ struct cf_op {
   // forward map and for the adjoint (whose taps are k reversed)
   int64_t L = 0, Lp = 0;
   float *w_fwd = nullptr, *w_adj = nullptr;
+  // conv1d by overlap-save FFTs (when chosen): the twiddle table and the
+  // spectra of the forward and adjoint taps (see k_fftconv.cu)
+  float2 *fft_tw = nullptr, *fft_hf = nullptr, *fft_ha = nullptr;
   // conv2d
   int64_t h = 0, w = 0, kh = 0, kw = 0;
   float *k2_fwd = nullptr, *k2_adj = nullptr;
@@ -169,6 +172,17 @@ void launch_diag(cudaStream_t s, int64_t n, const float* d, float alpha, const f
 void launch_conv1d(cudaStream_t s, int64_t n_out, int64_t n_in, int64_t Lp, int64_t shift,
                    const float* wrev, float alpha, const float* x, float* y, bool acc,
                    const float* sin = nullptr, const float* sout = nullptr);
+// The same operation as launch_conv1d by overlap-save FFTs of kFftConvN
+// points (Lp <= kFftConvMaxLp); H = the spectrum of the taps in the kernel's
+// order, scaled by 1 / kFftConvN; tw = the kernel's twiddle tables
+// (kFftConvTw values; k_fftconv.cu gives both layouts).
+constexpr int kFftConvN = 4096;
+constexpr int kFftConvMaxLp = 2048;
+constexpr int kFftConvAutoMinLp = 256;  // CF_CONV_AUTO uses the FFT from here on
+constexpr int kFftConvTw = kFftConvN + 256;
+void launch_conv1d_fft(cudaStream_t s, int64_t n_out, int64_t n_in, int64_t Lp, int64_t shift, const float2* H,
+                       const float2* tw, float alpha, const float* x, float* y, bool acc,
+                       const float* sin = nullptr, const float* sout = nullptr);
 void launch_conv2d(cudaStream_t s, int64_t Ho, int64_t Wo, int64_t Hi, int64_t Wi, int64_t kh,
                    int64_t kw, int64_t sh, int64_t sw, const float* kern, float alpha,
                    const float* x, float* y, bool acc);

@@ -3,6 +3,8 @@
 // transformation: the adjoint of a composition is formed node by node --
 // vstack <-> hstack, products reversed -- and never materialised).
 #include <algorithm>
+#include <cmath>
+#include <complex>
 #include <cstring>
 #include <memory>
 
@@ -15,7 +17,8 @@ void op_retain(cf_op* op) { op->refs.fetch_add(1); }
 static void op_free(cf_op* op) {
   for (cf_op* p : op->parts) cf_op_destroy(p);
   void* bufs[] = {op->a, op->row_scale, op->rowptr, op->col, op->t_rowptr, op->t_col,
-                  op->val, op->t_val, op->w_fwd, op->w_adj, op->k2_fwd, op->k2_adj, op->d};
+                  op->val, op->t_val, op->w_fwd, op->w_adj, op->k2_fwd, op->k2_adj, op->d,
+                  op->fft_tw, op->fft_hf, op->fft_ha};
   {
     DevGuard g(op->device);
     for (void* b : bufs)
@@ -200,10 +203,17 @@ void op_apply_rec(const cf_op* op, bool trans, float alpha, const float* x, floa
       return;
     case OP_CONV1D: {
       const int64_t nx = op->n, ny = op->m;
-      if (!trans)
+      if (op->fft_tw) {
+        if (!trans)
+          launch_conv1d_fft(s, ny, nx, op->Lp, 0, op->fft_hf, op->fft_tw, alpha, x, y, acc, sc.in, sc.out);
+        else
+          launch_conv1d_fft(s, nx, ny, op->Lp, op->Lp - 1, op->fft_ha, op->fft_tw, alpha, x, y, acc, sc.in,
+                            sc.out);
+      } else if (!trans) {
         launch_conv1d(s, ny, nx, op->Lp, 0, op->w_fwd, alpha, x, y, acc, sc.in, sc.out);
-      else
+      } else {
         launch_conv1d(s, nx, ny, op->Lp, op->Lp - 1, op->w_adj, alpha, x, y, acc, sc.in, sc.out);
+      }
       return;
     }
     case OP_CONV2D: {
@@ -454,15 +464,81 @@ cf_err cf_op_csr(cf_ctx* ctx, int64_t m, int64_t n, int64_t nnz, const int32_t* 
   return finish(op, run(), out);
 }
 
+namespace {
+
+// In-place radix-2 FFT in double (natural order in and out), sign -1.
+void fft_host(std::vector<std::complex<double>>& a) {
+  const size_t n = a.size();
+  for (size_t i = 1, j = 0; i < n; ++i) {
+    size_t bit = n >> 1;
+    for (; j & bit; bit >>= 1) j ^= bit;
+    j ^= bit;
+    if (i < j) std::swap(a[i], a[j]);
+  }
+  for (size_t len = 2; len <= n; len <<= 1)
+    for (size_t i = 0; i < n; i += len)
+      for (size_t k = 0; k < len / 2; ++k) {
+        const std::complex<double> w = std::polar(1.0, -2.0 * M_PI * (double)k / (double)len);
+        const std::complex<double> u = a[i + k], v = a[i + k + len / 2] * w;
+        a[i + k] = u + v;
+        a[i + k + len / 2] = u - v;
+      }
+}
+
+// Spectrum of h[v] = wrev[Lp - 1 - v] (zero-padded to kFftConvN) in the FFT
+// kernel's order, scaled by 1 / kFftConvN: after the forward transform, the
+// value at position p = 16 t + q (q0 256 + q1 16 + q2 in base 16) is
+// H[q0 + 16 q1 + 256 q2], and thread t reads its q-th factor at q 256 + t.
+std::vector<float2> fft_taps(const std::vector<float>& wrev) {
+  const int64_t Lp = (int64_t)wrev.size();
+  std::vector<std::complex<double>> h(kFftConvN, 0.0);
+  for (int64_t v = 0; v < Lp; ++v) h[v] = wrev[Lp - 1 - v];
+  fft_host(h);
+  std::vector<float2> out(kFftConvN);
+  for (int p = 0; p < kFftConvN; ++p) {
+    const int k = (p >> 8) + ((p >> 4) & 15) * 16 + (p & 15) * 256;
+    const std::complex<double> v = h[k] / (double)kFftConvN;
+    out[(p & 15) * 256 + (p >> 4)] = make_float2((float)v.real(), (float)v.imag());
+  }
+  return out;
+}
+
+// The FFT kernel's twiddles: W4096^(t q) at q 256 + t (t < 256, q < 16), then
+// W256^(j q) at 4096 + q 16 + j (j, q < 16), W_N = exp(-2 pi i / N).
+std::vector<float2> fft_twiddles() {
+  std::vector<float2> tw(kFftConvTw);
+  auto w = [](int64_t e, int64_t n) {
+    const double th = -2.0 * M_PI * (double)(e % n) / (double)n;
+    return make_float2((float)std::cos(th), (float)std::sin(th));
+  };
+  for (int q = 0; q < 16; ++q)
+    for (int t = 0; t < 256; ++t) tw[q * 256 + t] = w((int64_t)t * q, 4096);
+  for (int q = 0; q < 16; ++q)
+    for (int j = 0; j < 16; ++j) tw[4096 + q * 16 + j] = w((int64_t)j * q, 256);
+  return tw;
+}
+
+}  // namespace
+
 cf_err cf_op_conv1d(cf_ctx* ctx, int64_t n, const float* kernel, int64_t L, cf_op** out) {
-  if (!ctx || !out || !kernel || n <= 0 || L <= 0)
+  return cf_op_conv1d_method(ctx, n, kernel, L, CF_CONV_AUTO, out);
+}
+
+cf_err cf_op_conv1d_method(cf_ctx* ctx, int64_t n, const float* kernel, int64_t L, int32_t method, cf_op** out) {
+  if (!ctx || !out || !kernel || n <= 0 || L <= 0 || method < CF_CONV_AUTO || method > CF_CONV_FFT)
     return fail(CF_E_INVALID, "cf_op_conv1d: bad arguments");
+  const int64_t Lp_ = (int64_t)align_up((size_t)L, 16);
+  if (method == CF_CONV_FFT && Lp_ > kFftConvMaxLp)
+    return fail(CF_E_INVALID, "cf_op_conv1d: the FFT method takes kernels of at most " +
+                                  std::to_string(kFftConvMaxLp) + " taps");
+  const bool use_fft = method == CF_CONV_FFT ||
+                       (method == CF_CONV_AUTO && Lp_ >= kFftConvAutoMinLp && Lp_ <= kFftConvMaxLp);
   DevGuard g(ctx->device);
   std::vector<float> k(L);
   CF_TRY(copy_any(k.data(), kernel, L * sizeof(float), ctx->stream));
   cf_op* op = new_op(ctx, OP_CONV1D, n + L - 1, n);
   op->L = L;
-  op->Lp = (int64_t)align_up((size_t)L, 16);
+  op->Lp = Lp_;
   // forward taps w = k padded with zeros to Lp; stored reversed.
   // adjoint taps w' = k reversed (w'[l] = k[L-1-l]); padding zeros at the end
   // shift nothing because the adjoint kernel is called with shift Lp - 1.
@@ -477,6 +553,15 @@ cf_err cf_op_conv1d(cf_ctx* ctx, int64_t n, const float* kernel, int64_t L, cf_o
     CF_TRY(dev_alloc(&op->w_adj, op->Lp, &op->device_bytes));
     CF_CUDA(cudaMemcpy(op->w_fwd, wf.data(), op->Lp * 4, cudaMemcpyHostToDevice));
     CF_CUDA(cudaMemcpy(op->w_adj, wa.data(), op->Lp * 4, cudaMemcpyHostToDevice));
+    if (use_fft) {
+      const std::vector<float2> tw = fft_twiddles(), hf = fft_taps(wf), ha = fft_taps(wa);
+      CF_TRY(dev_alloc(&op->fft_tw, kFftConvTw, &op->device_bytes));
+      CF_TRY(dev_alloc(&op->fft_hf, kFftConvN, &op->device_bytes));
+      CF_TRY(dev_alloc(&op->fft_ha, kFftConvN, &op->device_bytes));
+      CF_CUDA(cudaMemcpy(op->fft_tw, tw.data(), kFftConvTw * sizeof(float2), cudaMemcpyHostToDevice));
+      CF_CUDA(cudaMemcpy(op->fft_hf, hf.data(), kFftConvN * sizeof(float2), cudaMemcpyHostToDevice));
+      CF_CUDA(cudaMemcpy(op->fft_ha, ha.data(), kFftConvN * sizeof(float2), cudaMemcpyHostToDevice));
+    }
     return CF_OK;
   };
   return finish(op, run(), out);

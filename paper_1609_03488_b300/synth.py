@@ -50,10 +50,12 @@ def csr(m, n, rowptr, col, val, storage="fp32"):
             "storage": storage}
 
 
-def conv1d(kernel, n):
+def conv1d(kernel, n, method="auto"):
+    """Full 1-D convolution leaf; ``method`` ("auto", "direct", "fft") only
+    selects how the library evaluates it."""
     kernel = np.ascontiguousarray(kernel, dtype=np.float32)
     return {"kind": "conv1d", "m": int(n) + kernel.size - 1, "n": int(n),
-            "kernel": kernel}
+            "kernel": kernel, "method": method}
 
 
 def conv2d(kernel, h, w):
@@ -76,6 +78,16 @@ def eye(n):
 
 def zero(m, n):
     return {"kind": "zero", "m": int(m), "n": int(n)}
+
+
+def with_conv_method(tree, method):
+    """A copy of an operator tree whose 1-D convolution leaves are evaluated
+    by ``method`` ("auto", "direct" or "fft"); same operator."""
+    if tree["kind"] == "conv1d":
+        return {k: v for k, v in tree.items() if not k.startswith("_")} | {"method": method}
+    if "parts" in tree:
+        return {**tree, "parts": [with_conv_method(p, method) for p in tree["parts"]]}
+    return tree
 
 
 def with_storage(tree, storage):

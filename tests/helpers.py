@@ -17,6 +17,30 @@ def assert_fp32_matvec(y, ref, absref, k, what=""):
                            f"worst ratio {np.max(err / bound):.3g}")
 
 
+def assert_fft_conv(y, ref, kernel, x, what="", n_fft=4096):
+    """Error bounds of a float32 overlap-save FFT convolution with n_fft-point
+    transforms.  The FFT error analysis (radix-2 levels, twiddles accurate to
+    u; Higham, Accuracy and Stability of Numerical Algorithms, Thm 24.2)
+    bounds the 2-norm error of each transform by log2(n_fft) eta ||.||,
+    eta ~ (4 sqrt2 + 1) u; a forward transform, the product with the
+    spectrum (|H| <= ||h||_1) and the inverse give, per output block,
+    ||err||_2 <= (2 log2(n_fft) eta + 2u) ||h||_1 ||seg||_2 with ||seg||_2 <=
+    sqrt2 ||x||_2 (two overlapping segments per transform).  Asserted
+    entrywise with a factor 1.5 of slack, plus a few roundings of the output;
+    and the RMS error, which grows like u sqrt(log2 n_fft) on average, below
+    1e-5 of ||y||."""
+    lg = np.log2(n_fft)
+    eta = (4 * np.sqrt(2) + 1) * U32
+    blk = 1.5 * (2 * lg * eta + 2 * U32) * np.abs(np.asarray(kernel, np.float64)).sum() \
+        * np.sqrt(2) * np.linalg.norm(np.asarray(x, np.float64))
+    err = np.abs(np.asarray(y, dtype=np.float64) - ref)
+    bound = blk + 4 * U32 * np.abs(ref)
+    bad = err > bound
+    assert not bad.any(), f"{what}: {bad.sum()} entries exceed the FFT bound; worst ratio {np.max(err / bound):.3g}"
+    rms = np.linalg.norm(err) / max(np.linalg.norm(ref), 1e-300)
+    assert rms <= 1e-5, f"{what}: relative 2-norm error {rms:.3g}"
+
+
 def rel(a, b):
     return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300)
 

@@ -40,6 +40,11 @@ def ctx(B):
 
 FAMILIES = {
     "deconv": lambda: synth.deconv(n_x=300, L=30, seed=synth.BASE_SEED + 1),
+    # 304 padded taps: the graph engine evaluates the convolution by FFTs
+    # with the scalings folded in.  (sigma = 3: with the default sigma = L/10
+    # the iteration itself amplifies 1e-7 relative operator noise to ~1e-5
+    # by iterate 20, in FP64 as well, whatever the convolution method.)
+    "deconv_fft": lambda: synth.deconv(n_x=3000, L=300, sigma=3.0, seed=synth.BASE_SEED + 1),
     "lasso_fp8": lambda: synth.lasso(m_d=301, p=151, seed=synth.BASE_SEED + 3, storage="fp8"),
     "lp_bf16": lambda: synth.lp(m_d=301, n_x=151, density=0.05, seed=synth.BASE_SEED + 4, storage="bf16"),
     "mixed": lambda: synth.mixed_cone_problem(np.random.default_rng(402), n=8, soc_sizes=(3, 1, 5), z=2, l=4),
@@ -137,6 +142,21 @@ def test_equilibration_cuts_the_small_deconvolution_iterations(B, ctx, engine):
     assert plain["status_name"] == eqd["status_name"] == "solved"
     assert eqd["iters"] * 4 < plain["iters"], (eqd["iters"], plain["iters"])
     assert abs(eqd["iters"] - ref["iters"]) <= 2 * 10, (eqd["iters"], ref["iters"])
+
+
+@pytest.mark.parametrize("method", ["direct", "fft"])
+def test_equilibrated_fft_deconvolution_solution(B, ctx, method):
+    """The scaled FFT convolution inside a whole solve: n = 2000, L = 400,
+    against scipy's NNLS; both evaluation methods reach it."""
+    prob = synth.deconv(n_x=2000, L=400, seed=synth.BASE_SEED + 9)
+    prob["A"] = synth.with_conv_method(prob["A"], method)
+    K = linop.densify(prob["A"]["parts"][2]["parts"][0]["parts"][0])
+    _, nnls = so.nnls(K, prob["meta"]["b_obs"], maxiter=50000)
+    P = _eq_problem(B, ctx, prob)
+    info, x, y, s = B.solve(P, B.settings(eps=2e-5, max_iters=300000, engine="graph"))
+    assert info["status_name"] == "solved", info
+    assert max(fp64_residuals(prob, x, y, s)) <= 1e-4, fp64_residuals(prob, x, y, s)
+    assert objective_rel_err(prob["c"] @ x, nnls) <= 1e-4, (prob["c"] @ x, nnls)
 
 
 def test_equilibrate_arguments_and_state(B, ctx):

@@ -3,13 +3,15 @@ adjoints per Section 4.1) against the FP64 oracle, through the C ABI.
 
 Float32 results are held to the rigorous bound of a float32 sum of k
 products, |y - y*| <= gamma_{k+2} (|A| |x|); stored BF16/FP8 operands must
-match the oracle's quantiser bit for bit."""
+match the oracle's quantiser bit for bit.  1-D convolutions evaluated by
+overlap-save FFTs are held to the FFT's error bound instead
+(tests.helpers.assert_fft_conv)."""
 import numpy as np
 import pytest
 
 from oracle import linop, quant
 from paper_1609_03488_b300 import synth
-from tests.helpers import assert_fp32_matvec
+from tests.helpers import assert_fft_conv, assert_fp32_matvec
 
 pytestmark = pytest.mark.gpu
 
@@ -74,14 +76,73 @@ def _check(B, ctx, tree, k_fwd, k_adj, seed=0, what=""):
 def test_conv1d(B, ctx, n, L):
     rng = np.random.default_rng(n + L)
     k = rng.standard_normal(L).astype(np.float32)
-    _check(B, ctx, synth.conv1d(k, n), L, L, what=f"conv1d n={n} L={L}")
+    _check(B, ctx, synth.conv1d(k, n, method="direct"), L, L, what=f"conv1d n={n} L={L}")
 
 
-def test_conv1d_full_size_large_deconvolution(B, ctx):
+def _check_fft(B, ctx, k, n, method="fft", seed=0, what=""):
+    rng = np.random.default_rng(seed)
+    tree = synth.conv1d(k, n, method=method)
+    op = B.build_operator(ctx, tree)
+    x = rng.standard_normal(n).astype(np.float32)
+    y = rng.standard_normal(n + k.size - 1).astype(np.float32)
+    assert_fft_conv(op.apply(x), linop.apply(tree, x.astype(np.float64)), k, x, what + " forward")
+    assert_fft_conv(op.apply(y, adjoint=True), linop.apply(tree, y.astype(np.float64), adjoint=True), k, y,
+                    what + " adjoint")
+    return op, x, y
+
+
+# one output, a single pair, ragged tails around the 2V-output pairs
+# (V = 4097 - Lp), the largest kernel (2048 taps, V = 2049), tiny kernels
+@pytest.mark.parametrize("n,L", [(1, 1000), (5, 16), (1000, 100), (3000, 1000), (6177, 1000), (6178, 1000),
+                                 (20000, 2048), (70001, 1000), (4099, 257), (100, 3)])
+def test_conv1d_fft(B, ctx, n, L):
+    rng = np.random.default_rng(7 * n + L)
+    k = rng.standard_normal(L).astype(np.float32)
+    _check_fft(B, ctx, k, n, what=f"conv1d fft n={n} L={L}")
+
+
+def test_conv1d_method_selection(B, ctx):
+    """auto = FFT for 256..2048 padded taps (bitwise), direct below; the FFT
+    method refuses longer kernels."""
+    rng = np.random.default_rng(5)
+    x = rng.standard_normal(9000).astype(np.float32)
+    for L, auto_is in ((240, "direct"), (241, "fft"), (2048, "fft"), (2049, "direct")):
+        k = rng.standard_normal(L).astype(np.float32)
+        a = B.build_operator(ctx, synth.conv1d(k, 9000, method="auto")).apply(x)
+        b = B.build_operator(ctx, synth.conv1d(k, 9000, method=auto_is)).apply(x)
+        np.testing.assert_array_equal(a, b)
+    with pytest.raises(B.CfError) as e:
+        B.build_operator(ctx, synth.conv1d(rng.standard_normal(2049).astype(np.float32), 100, method="fft"))
+    assert e.value.code == B.CF_E_INVALID
+
+
+def test_conv1d_fft_adjoint_identity_and_accumulate(B, ctx):
+    rng = np.random.default_rng(6)
+    k = rng.standard_normal(700).astype(np.float32)
+    op, x, y = _check_fft(B, ctx, k, 15000, what="conv1d fft n=15000")
+    lhs = float(op.apply(x).astype(np.float64) @ y)
+    rhs = float(x.astype(np.float64) @ op.apply(y, adjoint=True))
+    assert abs(lhs - rhs) <= 1e-5 * np.linalg.norm(op.apply(x)) * np.linalg.norm(y)
+    import torch
+    dev = torch.device("cuda", 0)
+    xd = torch.from_numpy(x).to(dev)
+    yd = torch.from_numpy(y).to(dev)
+    ws = torch.empty(max(op.workspace_bytes(False) // 4, 1), device=dev)
+    op.apply_async(xd, yd, alpha=-0.5, accumulate=True, workspace=ws)   # y - 0.5 A x
+    torch.cuda.synchronize()
+    want = y.astype(np.float64) - 0.5 * linop.apply(synth.conv1d(k, 15000), x.astype(np.float64))
+    assert_fft_conv(yd.cpu().numpy(), want, 0.5 * k, x, "accumulate")
+
+
+@pytest.mark.parametrize("method", ["direct", "fft"])
+def test_conv1d_full_size_large_deconvolution(B, ctx, method):
     """The n = 1e6, L = 1000 (sigma = 100) Gaussian operator of the large
-    deconvolution workload, both directions, every output."""
+    deconvolution workload, both directions, every output, both methods."""
     k = synth.gaussian_kernel(1000, 100.0).astype(np.float32)
-    _check(B, ctx, synth.conv1d(k, 1_000_000), 1000, 1000, what="conv1d 1e6")
+    if method == "direct":
+        _check(B, ctx, synth.conv1d(k, 1_000_000, method="direct"), 1000, 1000, what="conv1d 1e6")
+    else:
+        _check_fft(B, ctx, k, 1_000_000, what="conv1d fft 1e6")
 
 
 @pytest.mark.parametrize("h,w,kh,kw", [(1, 5, 2, 3), (30, 40, 5, 7), (64, 50, 31, 17), (17, 19, 64, 1)])
