@@ -180,6 +180,7 @@ constexpr int kFftConvN = 4096;
 constexpr int kFftConvMaxLp = 2048;
 constexpr int kFftConvAutoMinLp = 256;  // CF_CONV_AUTO uses the FFT from here on
 constexpr int kFftConvTw = kFftConvN + 256;
+cf_err conv1d_fft_prepare(int device);  // once per device before the first launch (not during capture)
 void launch_conv1d_fft(cudaStream_t s, int64_t n_out, int64_t n_in, int64_t Lp, int64_t shift, const float2* H,
                        const float2* tw, float alpha, const float* x, float* y, bool acc,
                        const float* sin = nullptr, const float* sout = nullptr);

@@ -28,6 +28,8 @@
 // tw[q 256 + t], stage 1's W256^(j q) at tw[4096 + q 16 + j]; the spectrum is
 // stored the same way, H[q 256 + t] for the value thread t multiplies into its
 // q-th output.
+#include <mutex>
+
 #include "devutil.cuh"
 
 namespace cf {
@@ -86,6 +88,14 @@ __device__ __forceinline__ void dft16(float2 (&a)[16]) {
 }
 #define XQ(a, q) a[4 * ((q) & 3) + ((q) >> 2)]
 
+// 4-byte asynchronous global -> shared copies (no registers held while in flight)
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // Forward stage on positions base + r * stride (r < 16): DFT16, output q
 // times twq[16 q] (this thread's twiddle for q), stored back at base + q * stride.
 __device__ __forceinline__ void dif_stage(float2* buf, int base, int stride, const float2* __restrict__ twq) {
@@ -119,9 +129,22 @@ k_conv1d_fft(int64_t n_out, int64_t n_in, int Lp, int64_t D, const float2* __res
              const float2* __restrict__ tw, float alpha, const float* __restrict__ x, float* __restrict__ y,
              bool acc, const float* __restrict__ sin, const float* __restrict__ sout) {
   __shared__ __align__(16) float2 buf[kN + kN / 16];
+  extern __shared__ float tail[];  // acc: y, SC: sout, over this pair's outputs
   const int t = threadIdx.x;
   const int V = kN - Lp + 1;
   const int64_t i0 = (int64_t)blockIdx.x * 2 * V;  // first output of the pair
+  // what the epilogue reads besides the transform is copied in now, while the
+  // transform runs
+  const int nout = (int)(n_out - i0 < 2 * (int64_t)V ? n_out - i0 : 2 * (int64_t)V);
+  float* ys = tail;
+  float* ss = tail + (acc ? 2 * V : 0);
+  if (acc || SC) {
+    for (int j = t; j < nout; j += kT) {
+      if (acc) cp_async4(ys + j, y + i0 + j);
+      if (SC) cp_async4(ss + j, sout + i0 + j);
+    }
+    cp_async_commit();
+  }
   // forward stage 0, straight from global: segment A in the real parts,
   // segment B (V outputs later) in the imaginary parts
   {
@@ -162,6 +185,7 @@ k_conv1d_fft(int64_t n_out, int64_t n_in, int Lp, int64_t D, const float2* __res
   __syncthreads();
   // inverse stage 1
   dit_stage(buf, 256 * (t >> 4) + (t & 15), 16, tw + 4096 + (t & 15));
+  if (acc || SC) cp_async_wait_all();
   __syncthreads();
   // inverse stage 0, straight to global: natural position p = t + 256 r
   {
@@ -177,14 +201,14 @@ k_conv1d_fft(int64_t n_out, int64_t n_in, int Lp, int64_t D, const float2* __res
       const int p = t + 256 * r;
       if (p < Lp - 1) continue;  // wrapped part of the circular convolution
       const float2 c = XQ(a, r);
-      const int64_t ia = i0 + p - (Lp - 1), ib = ia + V;
-      if (ia < n_out) {
-        const float v = (SC ? alpha * __ldg(sout + ia) : alpha) * c.x;
-        y[ia] = acc ? y[ia] + v : v;
+      const int ja = p - (Lp - 1), jb = ja + V;
+      if (ja < nout) {
+        const float v = (SC ? alpha * ss[ja] : alpha) * c.x;
+        y[i0 + ja] = acc ? ys[ja] + v : v;
       }
-      if (ib < n_out) {
-        const float v = (SC ? alpha * __ldg(sout + ib) : alpha) * c.y;
-        y[ib] = acc ? y[ib] + v : v;
+      if (jb < nout) {
+        const float v = (SC ? alpha * ss[jb] : alpha) * c.y;
+        y[i0 + jb] = acc ? ys[jb] + v : v;
       }
     }
   }
@@ -193,6 +217,25 @@ k_conv1d_fft(int64_t n_out, int64_t n_in, int Lp, int64_t D, const float2* __res
 
 }  // namespace
 
+// The dynamic tail needs more than the default 48 KB of shared memory next
+// to the static transform buffer: the limit is raised once per device, at
+// operator creation (outside any stream capture).
+cf_err conv1d_fft_prepare(int device) {
+  constexpr int kMaxDevices = 64;
+  static std::once_flag once[kMaxDevices];
+  static cudaError_t err[kMaxDevices];
+  if (device < 0 || device >= kMaxDevices) return fail(CF_E_INVALID, "conv1d FFT: device index out of range");
+  std::call_once(once[device], [device] {
+    const int lim = 2 * 2 * (kN - 16 + 1) * (int)sizeof(float);
+    err[device] = cudaFuncSetAttribute(k_conv1d_fft<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    if (err[device] == cudaSuccess)
+      err[device] = cudaFuncSetAttribute(k_conv1d_fft<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  });
+  if (err[device] != cudaSuccess)
+    return fail(CF_E_CUDA, std::string("conv1d FFT: shared memory limit: ") + cudaGetErrorString(err[device]));
+  return CF_OK;
+}
+
 void launch_conv1d_fft(cudaStream_t s, int64_t n_out, int64_t n_in, int64_t Lp, int64_t shift, const float2* H,
                        const float2* tw, float alpha, const float* x, float* y, bool acc, const float* sin,
                        const float* sout) {
@@ -200,11 +243,14 @@ void launch_conv1d_fft(cudaStream_t s, int64_t n_out, int64_t n_in, int64_t Lp, 
   const int64_t V = kN - Lp + 1;
   const int64_t pairs = (n_out + 2 * V - 1) / (2 * V);
   const int64_t D = Lp - 1 - shift;
-  if (sin || sout)
-    k_conv1d_fft<true><<<(unsigned)pairs, kT, 0, s>>>(n_out, n_in, (int)Lp, D, H, tw, alpha, x, y, acc, sin, sout);
+  const bool sc = sin || sout;
+  const size_t dyn = (size_t)((acc ? 2 * V : 0) + (sc ? 2 * V : 0)) * sizeof(float);
+  if (sc)
+    k_conv1d_fft<true><<<(unsigned)pairs, kT, dyn, s>>>(n_out, n_in, (int)Lp, D, H, tw, alpha, x, y, acc, sin,
+                                                        sout);
   else
-    k_conv1d_fft<false><<<(unsigned)pairs, kT, 0, s>>>(n_out, n_in, (int)Lp, D, H, tw, alpha, x, y, acc, nullptr,
-                                                       nullptr);
+    k_conv1d_fft<false><<<(unsigned)pairs, kT, dyn, s>>>(n_out, n_in, (int)Lp, D, H, tw, alpha, x, y, acc,
+                                                         nullptr, nullptr);
 }
 
 }  // namespace cf

@@ -554,6 +554,7 @@ cf_err cf_op_conv1d_method(cf_ctx* ctx, int64_t n, const float* kernel, int64_t 
     CF_CUDA(cudaMemcpy(op->w_fwd, wf.data(), op->Lp * 4, cudaMemcpyHostToDevice));
     CF_CUDA(cudaMemcpy(op->w_adj, wa.data(), op->Lp * 4, cudaMemcpyHostToDevice));
     if (use_fft) {
+      CF_TRY(conv1d_fft_prepare(ctx->device));
       const std::vector<float2> tw = fft_twiddles(), hf = fft_taps(wf), ha = fft_taps(wa);
       CF_TRY(dev_alloc(&op->fft_tw, kFftConvTw, &op->device_bytes));
       CF_TRY(dev_alloc(&op->fft_hf, kFftConvN, &op->device_bytes));
