@@ -163,6 +163,19 @@ struct EwBatch {
 };
 void launch_ew(cudaStream_t s, const EwBatch& b);
 
+#ifdef __CUDACC__
+// Row i of an elementwise segment.
+__device__ __forceinline__ float ew_value(const EwSeg& g, int64_t i) {
+  float v = g.acc ? g.y[i] : 0.f;
+  const float so = g.sout ? g.sout[i] : 1.f;
+  for (int k = 0; k < g.nterm; ++k) {
+    const float xv = g.sin[k] ? g.sin[k][i] * g.x[k][i] : g.x[k][i];
+    v = fmaf(g.sout ? g.alpha[k] * so : g.alpha[k], g.d[k] ? g.d[k][i] * xv : xv, v);
+  }
+  return v;
+}
+#endif
+
 // ---- leaf launchers (kernels in k_*.cu)
 void launch_fill(cudaStream_t s, int64_t n, float v, float* y);
 void launch_diag(cudaStream_t s, int64_t n, const float* d, float alpha, const float* x, float* y,

@@ -25,15 +25,8 @@ __global__ void k_diag(int64_t n, const float* __restrict__ d, float alpha,
 __global__ void k_ew(EwBatch b) {
   const EwSeg& g = b.seg[blockIdx.y];
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    float v = g.acc ? g.y[i] : 0.f;
-    const float so = g.sout ? g.sout[i] : 1.f;
-    for (int k = 0; k < g.nterm; ++k) {
-      const float xv = g.sin[k] ? g.sin[k][i] * g.x[k][i] : g.x[k][i];
-      v = fmaf(g.sout ? g.alpha[k] * so : g.alpha[k], g.d[k] ? g.d[k][i] * xv : xv, v);
-    }
-    g.y[i] = v;
-  }
+       i += (int64_t)gridDim.x * blockDim.x)
+    g.y[i] = ew_value(g, i);
 }
 
 void launch_ew(cudaStream_t s, const EwBatch& b) {

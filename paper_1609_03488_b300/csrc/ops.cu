@@ -84,14 +84,17 @@ struct EwQueue {
   // y = sout alpha d (sin x) (+ y): nterm 0 is a zero fill.
   void add(float* y, int64_t n, bool acc, const float* x, const float* d, float alpha, bool fill,
            const float* sin = nullptr, const float* sout = nullptr) {
-    // same output and output scaling, accumulating, no reads of pending
-    // outputs: one more term
+    // same output and output scaling (a pending zero fill has no terms to
+    // scale and takes this one's), accumulating, no reads of pending outputs:
+    // one more term
     for (int k = 0; k < b.nseg; ++k) {
       EwSeg& g = b.seg[k];
-      if (!fill && acc && g.y == y && g.n == n && g.nterm < kEwMaxTerms && g.sout == sout) {
+      const bool bare_fill = g.nterm == 0 && !g.acc;
+      if (!fill && acc && g.y == y && g.n == n && g.nterm < kEwMaxTerms && (g.sout == sout || bare_fill)) {
         bool hazard = false;
         for (int j = 0; j < b.nseg; ++j) hazard |= overlap(x, n, b.seg[j].y, b.seg[j].n);
         if (!hazard) {
+          if (bare_fill) g.sout = sout;
           g.x[g.nterm] = x;
           g.d[g.nterm] = d;
           g.sin[g.nterm] = sin;

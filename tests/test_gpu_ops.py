@@ -134,6 +134,29 @@ def test_conv1d_fft_adjoint_identity_and_accumulate(B, ctx):
     assert_fft_conv(yd.cpu().numpy(), want, 0.5 * k, x, "accumulate")
 
 
+def test_deconv_tree_with_fft_convolution(B, ctx):
+    """The cone-form deconvolution operator with an FFT (and a direct)
+    convolution leaf: the -I blocks' rows are exact and the convolution rows
+    meet the FFT bound, both directions."""
+    prob = synth.deconv(n_x=5000, L=300, seed=12)
+    k = prob["meta"]["kernel"]
+    n_x = 5000
+    rng = np.random.default_rng(13)
+    for method in ("fft", "direct"):
+        tree = synth.with_conv_method(prob["A"], method)
+        op = B.build_operator(ctx, tree)
+        x = rng.standard_normal(tree["n"]).astype(np.float32)
+        y = rng.standard_normal(tree["m"]).astype(np.float32)
+        fx, fy = op.apply(x), op.apply(y, adjoint=True)
+        np.testing.assert_array_equal(fx[:n_x], -x[:n_x])
+        assert fx[n_x] == -x[n_x]
+        ref = linop.apply(tree, x.astype(np.float64))
+        assert_fft_conv(fx[n_x + 1:], ref[n_x + 1:], k, x[:n_x], f"deconv tree {method} forward")
+        ref = linop.apply(tree, y.astype(np.float64), adjoint=True)
+        assert fy[n_x] == -y[n_x]
+        assert_fft_conv(fy[:n_x], ref[:n_x], k, y[n_x + 1:], f"deconv tree {method} adjoint")
+
+
 @pytest.mark.parametrize("method", ["direct", "fft"])
 def test_conv1d_full_size_large_deconvolution(B, ctx, method):
     """The n = 1e6, L = 1000 (sigma = 100) Gaussian operator of the large
