@@ -112,6 +112,36 @@ __device__ bool grid_sum(double (&v)[NV], double* part, unsigned int* counter) {
   for (int64_t i = ((n) & ~(int64_t)3) + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; \
        i < (n); i += (int64_t)gridDim.x * blockDim.x)
 
+// ------------------------------------------------------------ problem data
+// b, c (float64, already on the device) -> float32 copies, per-CTA float64
+// sums of b_i^2 and c_i^2 (summed on the host in CTA order), and a flag set
+// when an entry is not finite.
+constexpr int kPrepGrid = 296;
+__global__ void k_prep_data(int64_t m, int64_t n, const double* __restrict__ bd, const double* __restrict__ cd,
+                            float* __restrict__ bf, float* __restrict__ cf, double* __restrict__ part,
+                            int* __restrict__ bad) {
+  double v[2] = {0.0, 0.0};
+  int nf = 0;
+  GRID_STRIDE(i, m) {
+    const double x = bd[i];
+    nf |= !isfinite(x);
+    v[0] = fma(x, x, v[0]);
+    bf[i] = (float)x;
+  }
+  GRID_STRIDE(i, n) {
+    const double x = cd[i];
+    nf |= !isfinite(x);
+    v[1] = fma(x, x, v[1]);
+    cf[i] = (float)x;
+  }
+  if (nf) atomicOr(bad, 1);
+  block_sum<2>(v);
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = v[0];
+    part[2 * blockIdx.x + 1] = v[1];
+  }
+}
+
 // ------------------------------------------------------------ iteration start
 __global__ void k_init(Ctl* c, int64_t n, int64_t m, float* ux, float* uy, float* vs, float* zx,
                        float* gz, float* az, const double* warm) {
@@ -1379,17 +1409,6 @@ cf_err cone_problem_create(cf_ctx* ctx, const cf_op* A, const double* b, int64_t
   P->l = K->l;
   P->q.assign(K->q, K->q + K->nq);
   auto run = [&]() -> cf_err {
-    std::vector<double> hb(m), hc(n);
-    CF_TRY(copy_any(hb.data(), b, m * sizeof(double), ctx->stream));
-    CF_TRY(copy_any(hc.data(), c, n * sizeof(double), ctx->stream));
-    double nb = 0, nc = 0;
-    for (double v : hb) nb += v * v;
-    for (double v : hc) nc += v * v;
-    for (double v : hb) if (!std::isfinite(v)) return fail(CF_E_INVALID, "cone_problem_create: b not finite");
-    for (double v : hc) if (!std::isfinite(v)) return fail(CF_E_INVALID, "cone_problem_create: c not finite");
-    P->nb = std::sqrt(nb);
-    P->nc = std::sqrt(nc);
-    std::vector<float> fb(hb.begin(), hb.end()), fc(hc.begin(), hc.end());
     // cone tables
     std::vector<int32_t> cseg, sc0, snc;
     std::vector<int64_t> cr0, cr1, shead;
@@ -1430,8 +1449,42 @@ cf_err cone_problem_create(cf_ctx* ctx, const cf_op* A, const double* b, int64_t
     P->seg_head = (int64_t*)take(nsg * 8);
     P->seg_c0 = (int32_t*)take(nsg * 4);
     P->seg_nc = (int32_t*)take(nsg * 4);
-    CF_CUDA(cudaMemcpy(P->bf, fb.data(), m * 4, cudaMemcpyHostToDevice));
-    CF_CUDA(cudaMemcpy(P->cf, fc.data(), n * 4, cudaMemcpyHostToDevice));
+    // b and c: float64 to the device (host or device source), converted,
+    // normed and checked there
+    {
+      cudaStream_t st = ctx->stream;
+      const size_t tb = align_up((size_t)(m + n) * 8, 256) + align_up(2 * kPrepGrid * 8, 256) + 256;
+      char* tmp = nullptr;
+      CF_CUDA(cudaMallocAsync((void**)&tmp, tb, st));
+      double* bd = (double*)tmp;
+      double* cd = bd + m;
+      double* part = (double*)(tmp + align_up((size_t)(m + n) * 8, 256));
+      int* bad = (int*)(tmp + align_up((size_t)(m + n) * 8, 256) + align_up(2 * kPrepGrid * 8, 256));
+      std::vector<double> hp(2 * kPrepGrid);
+      int hbad = 0;
+      auto prep = [&]() -> cf_err {
+        CF_CUDA(cudaMemcpyAsync(bd, b, m * sizeof(double), cudaMemcpyDefault, st));
+        CF_CUDA(cudaMemcpyAsync(cd, c, n * sizeof(double), cudaMemcpyDefault, st));
+        CF_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), st));
+        k_prep_data<<<kPrepGrid, kThreads, 0, st>>>(m, n, bd, cd, P->bf, P->cf, part, bad);
+        CF_CUDA(cudaGetLastError());
+        CF_CUDA(cudaMemcpyAsync(hp.data(), part, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CF_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CF_CUDA(cudaStreamSynchronize(st));
+        return CF_OK;
+      };
+      const cf_err pr = prep();
+      cudaFreeAsync(tmp, st);
+      if (pr != CF_OK) return pr;
+      if (hbad) return fail(CF_E_INVALID, "cone_problem_create: b or c not finite");
+      double nb = 0, nc = 0;
+      for (int k = 0; k < kPrepGrid; ++k) {
+        nb += hp[2 * k];
+        nc += hp[2 * k + 1];
+      }
+      P->nb = std::sqrt(nb);
+      P->nc = std::sqrt(nc);
+    }
     if (P->nchunk) {
       CF_CUDA(cudaMemcpy(P->chunk_r0, cr0.data(), P->nchunk * 8, cudaMemcpyHostToDevice));
       CF_CUDA(cudaMemcpy(P->chunk_r1, cr1.data(), P->nchunk * 8, cudaMemcpyHostToDevice));
@@ -1443,9 +1496,12 @@ cf_err cone_problem_create(cf_ctx* ctx, const cf_op* A, const double* b, int64_t
     CF_CUDA(cudaStreamCreateWithFlags(&P->stream, cudaStreamNonBlocking));
     CF_CUDA(cudaEventCreateWithFlags(&P->ev_in, cudaEventDisableTiming));
     CF_CUDA(cudaEventCreateWithFlags(&P->ev_out, cudaEventDisableTiming));
-    CF_CUDA(cudaMallocHost((void**)&P->ctl_host, sizeof(Ctl)));
-    std::memset(P->ctl_host, 0, sizeof(Ctl));
-    CF_CUDA(cudaMallocHost((void**)&P->flags_host, 64));
+    // one pinned block: the control block's mirror, then the loop flags
+    char* pin = nullptr;
+    CF_CUDA(cudaMallocHost((void**)&pin, align_up(sizeof(Ctl), 64) + 64));
+    std::memset(pin, 0, align_up(sizeof(Ctl), 64) + 64);
+    P->ctl_host = (Ctl*)pin;
+    P->flags_host = pin + align_up(sizeof(Ctl), 64);
     return CF_OK;
   };
   cf_err r = run();
@@ -1477,8 +1533,7 @@ void cf_problem_destroy(cf_problem* P) {
   if (P->inner) cf_op_destroy(P->inner);
   if (P->inner_orig) cf_op_destroy(P->inner_orig);
   if (P->bf) cudaFree(P->bf);  // base of the persistent block
-  if (P->ctl_host) cudaFreeHost(P->ctl_host);
-  if (P->flags_host) cudaFreeHost(P->flags_host);
+  if (P->ctl_host) cudaFreeHost(P->ctl_host);  // the flags share its block
   if (P->ev_in) cudaEventDestroy(P->ev_in);
   if (P->ev_out) cudaEventDestroy(P->ev_out);
   if (P->stream) cudaStreamDestroy(P->stream);
