@@ -43,7 +43,9 @@ METRIC = "ADMM iters/s"
 # source it was taken on.
 EQUIL = dict(iters=10, probes=8, seed=0x5EED)
 CONV_NCU = {"traffic_bytes": 4029184, "src_sha256_16": "f372736cf1cfc748"}
-FFT_NCU = {"traffic_bytes": None, "src_sha256_16": None}
+# the same for k_conv1d_fft: an unscaled forward launch of this workload
+# (profiles/conv1d_fft_large_deconvolution.md)
+FFT_NCU = {"traffic_bytes": 4107264, "src_sha256_16": "68543effff9f908a"}
 FFT_N = 4096
 FFT_AUTO_LP = (256, 2048)   # padded tap counts for which the library's auto method takes the FFT
 FP32_LANES_PER_SM = 128
