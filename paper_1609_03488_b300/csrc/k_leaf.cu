@@ -22,11 +22,48 @@ __global__ void k_diag(int64_t n, const float* __restrict__ d, float alpha,
 
 // blockIdx.y selects the segment; segments are independent (the host only
 // batches operations without data hazards between them).
+// Whether every array of a segment starts on a 16-byte boundary.
+__device__ __forceinline__ bool ew_aligned16(const EwSeg& g) {
+  uintptr_t a = reinterpret_cast<uintptr_t>(g.y) | reinterpret_cast<uintptr_t>(g.sout);
+  for (int k = 0; k < g.nterm; ++k)
+    a |= reinterpret_cast<uintptr_t>(g.x[k]) | reinterpret_cast<uintptr_t>(g.d[k]) |
+         reinterpret_cast<uintptr_t>(g.sin[k]);
+  return (a & 15) == 0;
+}
+
+// Rows 4v .. 4v + 3 of a segment with 16-byte loads; per row the arithmetic
+// of ew_value, operation for operation.
+__device__ __forceinline__ float4 ew_value4(const EwSeg& g, int64_t v) {
+  float4 out = g.acc ? ld4(g.y, v) : make_float4(0.f, 0.f, 0.f, 0.f);
+  const float4 so = g.sout ? ld4(g.sout, v) : make_float4(1.f, 1.f, 1.f, 1.f);
+  for (int k = 0; k < g.nterm; ++k) {
+    float4 xv = ld4(g.x[k], v);
+    if (g.sin[k]) {
+      const float4 sv = ld4(g.sin[k], v);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) el(xv, e) = elc(sv, e) * elc(xv, e);
+    }
+    if (g.d[k]) {
+      const float4 dv = ld4(g.d[k], v);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) el(xv, e) = elc(dv, e) * elc(xv, e);
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) el(out, e) = fmaf(g.sout ? g.alpha[k] * elc(so, e) : g.alpha[k], elc(xv, e), el(out, e));
+  }
+  return out;
+}
+
 __global__ void k_ew(EwBatch b) {
   const EwSeg& g = b.seg[blockIdx.y];
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    g.y[i] = ew_value(g, i);
+  const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t head = 0;
+  if (ew_aligned16(g)) {
+    const int64_t n4 = g.n >> 2;
+    for (int64_t v = t0; v < n4; v += stride) st4(g.y, v, ew_value4(g, v));
+    head = n4 << 2;
+  }
+  for (int64_t i = head + t0; i < g.n; i += stride) g.y[i] = ew_value(g, i);
 }
 
 void launch_ew(cudaStream_t s, const EwBatch& b) {
