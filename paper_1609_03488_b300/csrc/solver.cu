@@ -427,12 +427,24 @@ __global__ void k_soc_norm(const Ctl* c, const int32_t* __restrict__ chunk_seg,
   const int64_t r0 = chunk_r0[ch], r1 = chunk_r1[ch];
   const float a = (float)c->st.alpha, a1 = (float)(1.0 - c->st.alpha), ut = (float)c->ut_tau;
   Acc2 a0;
-  for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
-    float pi = y_pre(a, a1, ut, zy[i], gy[i], uy[i], vs[i]);
+  auto row = [&](int64_t i, float pi) {
     if (i == head)
       seg_p0[sg] = (double)pi;
     else
       a0.add_prod(pi, pi);
+  };
+  // 16-byte loads over the chunk's 4-aligned interior, single rows at its edges
+  const int64_t q0 = (r0 + 3) & ~(int64_t)3, q1 = r1 & ~(int64_t)3;
+  const int64_t e0 = q0 < q1 ? q0 : r1;
+  for (int64_t i = r0 + threadIdx.x; i < e0; i += blockDim.x) row(i, y_pre(a, a1, ut, zy[i], gy[i], uy[i], vs[i]));
+  if (q0 < q1) {
+#pragma unroll 2
+    for (int64_t v = (q0 >> 2) + threadIdx.x; v < (q1 >> 2); v += blockDim.x) {
+      const float4 z4 = ld4(zy, v), g4 = ld4(gy, v), u4 = ld4(uy, v), s4 = ld4(vs, v);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) row(4 * v + k, y_pre(a, a1, ut, elc(z4, k), elc(g4, k), elc(u4, k), elc(s4, k)));
+    }
+    for (int64_t i = q1 + threadIdx.x; i < r1; i += blockDim.x) row(i, y_pre(a, a1, ut, zy[i], gy[i], uy[i], vs[i]));
   }
   double v[1] = {a0.value()};
   block_sum<1>(v);
