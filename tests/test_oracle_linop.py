@@ -133,3 +133,29 @@ def test_paper_convolution_lasso_size():
     p = synth.lasso_conv(p=g["p"], L=g["L"], seed=1)
     assert (p["A"]["n"], p["A"]["m"]) == (g["variables"], g["constraints"])
     assert synth.cone_dims(p["cone"]) == g["constraints"]
+
+
+def test_storage_variants_of_one_tree_keep_their_own_values():
+    """Trees that share a leaf's data but store it differently (the float32
+    instance and its BF16 / FP8 inner copies) are applied with their own
+    dequantised values, whichever was applied first: the oracle's per-leaf
+    cache is keyed by the storage."""
+    from oracle import quant
+    rng = np.random.default_rng(9)
+    prob = synth.lasso(m_d=50, p=20, seed=9)
+    x = rng.standard_normal(prob["A"]["n"])
+    y32 = linop.apply(prob["A"], x)                      # fills the float32 cache first
+    for storage in ("bf16", "fp8"):
+        t = synth.with_storage(prob["A"], storage)
+        D = quant.dense_values(prob["meta"]["D"], storage)
+        yq = linop.apply(t, x)
+        p = prob["meta"]["p"]
+        np.testing.assert_allclose(yq[-50:], -np.sqrt(2.0) * (D @ x[:p]), rtol=1e-12, atol=1e-12)
+        assert np.abs(yq - y32).max() > 1e-6
+    np.testing.assert_array_equal(linop.apply(prob["A"], x), y32)
+    # the convolution method switch changes nothing in the operator
+    dec = synth.deconv(n_x=40, L=9, seed=3)
+    z = rng.standard_normal(dec["A"]["n"])
+    for method in ("direct", "fft"):
+        np.testing.assert_array_equal(linop.apply(synth.with_conv_method(dec["A"], method), z),
+                                      linop.apply(dec["A"], z))
