@@ -597,23 +597,36 @@ __global__ void k_resid(Ctl* c, int64_t n, int64_t m, const float* __restrict__ 
   const double tau = c->tau;
   const float tf = (float)tau;
   Acc2 s0, s1, s2, s3, s4, s5;
-  GRID_STRIDE(i, m) {
-    const float w = dinv ? dinv[i] : 1.f;
-    const float e = cm[i] + vs[i];
-    const float d = w * fmaf(-bf[i], tf, e);
+  auto row_y = [&](float w, float cmi, float vsi, float bfi, float uyi) {
+    const float e = cmi + vsi;
+    const float d = w * fmaf(-bfi, tf, e);
     const float we = w * e;
     s0.add_prod(d, d);
     s1.add_prod(we, we);
-    s2.add_prod(bf[i], uy[i]);
-  }
-  GRID_STRIDE(i, n) {
-    const float w = einv ? einv[i] : 1.f;
-    const float d = w * fmaf(cf[i], tf, cn[i]);
-    const float wc = w * cn[i];
+    s2.add_prod(bfi, uyi);
+  };
+  auto row_x = [&](float w, float cni, float cfi, float uxi) {
+    const float d = w * fmaf(cfi, tf, cni);
+    const float wc = w * cni;
     s3.add_prod(d, d);
     s4.add_prod(wc, wc);
-    s5.add_prod(cf[i], ux[i]);
+    s5.add_prod(cfi, uxi);
+  };
+  const float4 one4 = make_float4(1.f, 1.f, 1.f, 1.f);
+  VEC4_LOOP(v, m >> 2) {
+    const float4 w = dinv ? ld4(dinv, v) : one4;
+    const float4 a = ld4(cm, v), b = ld4(vs, v), c4 = ld4(bf, v), u = ld4(uy, v);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) row_y(elc(w, k), elc(a, k), elc(b, k), elc(c4, k), elc(u, k));
   }
+  TAIL_LOOP(i, m) row_y(dinv ? dinv[i] : 1.f, cm[i], vs[i], bf[i], uy[i]);
+  VEC4_LOOP(v, n >> 2) {
+    const float4 w = einv ? ld4(einv, v) : one4;
+    const float4 a = ld4(cn, v), c4 = ld4(cf, v), u = ld4(ux, v);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) row_x(elc(w, k), elc(a, k), elc(c4, k), elc(u, k));
+  }
+  TAIL_LOOP(i, n) row_x(einv ? einv[i] : 1.f, cn[i], cf[i], ux[i]);
   double v[6] = {s0.value(), s1.value(), s2.value(), s3.value(), s4.value(), s5.value()};
   if (grid_sum<6>(v, part, &c->red_count) && threadIdx.x == 0) {
     const double sig = c->sigma, rho = c->rho;
