@@ -587,6 +587,26 @@ def run_paper_deconv(args, B, ctx, torch):
 
 
 # ------------------------------------------------------------------ ours
+def replica_problem(workload, rank):
+    """The deconvolution instance rank `rank` solves: the same shape on every
+    rank, its own seed (independent replicas; no data crosses ranks)."""
+    return synth.deconv(**{**workload, "seed": workload["seed"] + rank})
+
+
+def reduce_over_ranks(ms, iters, dist, device):
+    """Whole-job numbers of a replicated run: every rank times its own
+    replica, the job's time is the slowest rank's and its work the sum over
+    ranks (weak scaling).  Without a process group, the rank's own numbers."""
+    if dist is None:
+        return float(ms), float(iters)
+    import torch
+    tt = torch.tensor([float(ms)], device=device, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    it = torch.tensor([float(iters)], device=device, dtype=torch.float64)
+    dist.all_reduce(it, op=dist.ReduceOp.SUM)
+    return float(tt.item()), float(it.item())
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -634,7 +654,7 @@ def main():
     # direct sum: 2.50 / 5.55 / 0.59 / 0.75 s), 1 on the small one (750
     # iterations vs 2090 at 10)
     cg_rel = args.cg_tol_rel if args.cg_tol_rel is not None else (30.0 if (eq and not small) else 1.0)
-    prob = synth.deconv(**{**W, "seed": W["seed"] + rank})
+    prob = replica_problem(W, rank)
     prob["A"] = synth.with_conv_method(prob["A"], args.conv)
     n, m = prob["A"]["n"], prob["A"]["m"]
     # a dedicated (non-default) stream: the library launches on it and the
@@ -675,15 +695,7 @@ def main():
             infos.append(info)
         barrier()
     ms = sum(a.elapsed_time(b) for a, b in ev)
-    t_max = ms
-    it_total = iters
-    if dist is not None:
-        tt = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-        it = torch.tensor([iters], device=dev, dtype=torch.float64)
-        dist.all_reduce(it, op=dist.ReduceOp.SUM)
-        it_total = float(it.item())
+    t_max, it_total = reduce_over_ranks(ms, iters, dist, dev)
     value = it_total / (t_max / 1e3)
 
     # ---- dominant kernel: the 1-D convolution, timed live on the same stream
