@@ -50,3 +50,28 @@ def test_fft_bound_accepts_float32_fft_and_rejects_planted_mistakes(kind):
     for name, yb in bad.items():
         with pytest.raises(AssertionError):
             assert_fft_conv(yb, ref, k, x, name)
+
+
+def test_fp32_matvec_bound_accepts_float32_sums_and_rejects_planted_mistakes():
+    """The entrywise bound gamma_{k+2} (|A| |x|) of the direct kernels: a
+    float32 matrix-vector product (any summation order) passes; a dropped
+    column, a wrong-sign entry and a product rounded to bfloat16 fail."""
+    from tests.helpers import assert_fp32_matvec
+    rng = np.random.default_rng(5)
+    m, n = 300, 2000
+    A = rng.standard_normal((m, n)).astype(np.float32)
+    x = rng.standard_normal(n).astype(np.float32)
+    ref = A.astype(np.float64) @ x.astype(np.float64)
+    absref = np.abs(A).astype(np.float64) @ np.abs(x).astype(np.float64)
+    y = np.zeros(m, np.float32)
+    for j in range(n):                       # sequential float32 sum: the worst order
+        y = (y + A[:, j] * x[j]).astype(np.float32)
+    assert_fp32_matvec(y, ref, absref, n, "float32 sum")
+    assert_fp32_matvec(A @ x, ref, absref, n, "float32 BLAS")
+    j = int(np.argmax(np.abs(x)))
+    bad = {"dropped column": y - A[:, j] * x[j],
+           "sign": y - 2 * A[:, j] * x[j],
+           "bf16": (y.view(np.uint32) & 0xFFFF0000).view(np.float32)}
+    for name, yb in bad.items():
+        with pytest.raises(AssertionError):
+            assert_fp32_matvec(yb, ref, absref, n, name)
