@@ -280,7 +280,13 @@ cf_err cf_op_workspace_bytes(const cf_op* op, int32_t adjoint, size_t* bytes);
  * capture.  All calls share the one array: calls whose GPU work overlaps
  * (different streams, or different host threads) race and give wrong results;
  * serialize them.  Each call writes every scratch element before reading it,
- * so the contents left by the previous call do not matter. */
+ * so the contents left by the previous call do not matter.  x must be ready on
+ * `stream`: when x was written on another stream, the caller orders the two
+ * (an event, or passing the producing stream here).  An error already pending
+ * on the calling thread is returned as CF_E_CUDA and left in place.  The
+ * array's device address is cached per device for the life of the process:
+ * do not use this entry point after cudaDeviceReset or a re-creation of the
+ * device's primary context. */
 cf_err cf_op_apply_static(cf_op* op, int32_t adjoint, float alpha, const float* x, float* y,
                           int32_t accumulate, void* stream);
 

@@ -51,6 +51,10 @@ struct cf_server {
   std::vector<Req*> running;
   std::unordered_map<cf_ticket, Req*> all;
   std::vector<cf_problem*> resident;  // LRU order: front = oldest
+  // bytes charged to `used` for each resident problem, recorded when it was
+  // admitted; eviction returns exactly this amount even if the problem's
+  // size changed since (equilibration or an inner operator set in between)
+  std::unordered_map<cf_problem*, size_t> charged;
   size_t used = 0;
   bool stopping = false;
   cf_ticket next = 1;
@@ -70,10 +74,27 @@ struct cf_server {
     resident.push_back(p);
   }
 
-  // Make room for p; true if it fits (after evicting idle residents).
+  // Drop p from the resident set, returning the bytes it was charged.
+  void uncharge(cf_problem* p) {
+    auto it = std::find(resident.begin(), resident.end(), p);
+    if (it != resident.end()) resident.erase(it);
+    auto c = charged.find(p);
+    if (c != charged.end()) {
+      used -= std::min(used, c->second);
+      charged.erase(c);
+    }
+  }
+
+  // Make room for p; true if it fits (after evicting idle residents).  A
+  // resident problem whose size changed since it was charged is re-charged
+  // at its current size.
   bool make_room(cf_problem* p) {
-    if (is_resident(p)) return true;
     const size_t need = problem_bytes(p);
+    if (is_resident(p)) {
+      auto c = charged.find(p);
+      if (c != charged.end() && c->second == need) return true;
+      uncharge(p);                     // its state stays allocated until re-admitted
+    }
     while (used + need > budget) {
       cf_problem* victim = nullptr;
       for (cf_problem* q : resident)
@@ -82,8 +103,7 @@ struct cf_server {
           break;
         }
       if (!victim) return false;
-      resident.erase(std::find(resident.begin(), resident.end(), victim));
-      used -= problem_bytes(victim);
+      uncharge(victim);
       std::lock_guard<std::mutex> lk(victim->mtx);
       release_state(victim);
     }
@@ -97,7 +117,11 @@ struct cf_server {
       if (is_running(r->p)) break;  // same problem: wait for its previous request
       if (!make_room(r->p)) break;
       queue.pop_front();
-      if (!is_resident(r->p)) used += problem_bytes(r->p);
+      if (!is_resident(r->p)) {
+        const size_t b = problem_bytes(r->p);
+        charged[r->p] = b;
+        used += b;
+      }
       touch(r->p);
       r->plock = std::unique_lock<std::mutex>(r->p->mtx);
       cudaSetDevice(ctx->device);

@@ -19,7 +19,10 @@ float* g_scratch_ptr[kMaxDevices] = {};
 
 // Device address of g_static_scratch on `device` (which must be current).
 // In host code the symbol's name is only a host-side stand-in, so the address
-// is looked up once per device and cached.
+// is looked up once per device and cached.  The cache lives as long as the
+// process: after cudaDeviceReset (or a release and re-creation of the
+// device's primary context) the module is loaded again and the cached address
+// is stale, so this entry point must not be used across such a reset.
 cf_err scratch_for(int device, float** out) {
   if (device < 0 || device >= kMaxDevices) return cf::fail(CF_E_INVALID, "cf_op_apply_static: device index out of range");
   std::lock_guard<std::mutex> lk(g_mu);
@@ -46,6 +49,11 @@ extern "C" cf_err cf_op_apply_static(cf_op* op, int32_t adjoint, float alpha, co
                                       std::to_string(kStaticScratchBytes) + "-byte static array");
   if (!cf::is_device_ptr(x) || !cf::is_device_ptr(y))
     return cf::fail(CF_E_INVALID, "cf_op_apply_static: x and y must be device memory");
+  // an error left pending by earlier work on this thread is reported, not
+  // cleared: it belongs to the caller
+  const cudaError_t pending = cudaPeekAtLastError();
+  if (pending != cudaSuccess)
+    return cf::cuda_fail(pending, "cf_op_apply_static: pending CUDA error from earlier work", __FILE__, __LINE__);
   int prev = -1;
   cudaGetDevice(&prev);
   const int dev = op->device;
@@ -56,7 +64,6 @@ extern "C" cf_err cf_op_apply_static(cf_op* op, int32_t adjoint, float alpha, co
     // Every scratch element the kernels read is written earlier in the same
     // call, so nothing needs clearing between calls.
     cudaStream_t s = stream ? (cudaStream_t)stream : op->ctx->stream;
-    cudaGetLastError();  // report only this call's launch errors below
     cf::op_apply(op, tr, alpha, x, y, accumulate != 0, scratch, s);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) r = cf::cuda_fail(e, "cf_op_apply_static launch", __FILE__, __LINE__);

@@ -3,8 +3,11 @@ not allocate GPU memory (their framework's allocator owns the device memory,
 or a cudaMalloc/cudaFree in their loop would stall the GPU).
 
 It must give the same y = A x / A^T x as the allocating entry point
-cf_op_apply, on two calls in a row (the shared static scratch keeps the
-previous call's contents).  This file is collected last on purpose."""
+cf_op_apply, on two calls in a row, with an unrelated operator's scratch
+left in the shared static array between them.  Calls go on torch's current
+stream (the binding's default), so they are ordered after the torch kernels
+that fill their inputs and outputs.  This file is collected last on
+purpose."""
 import numpy as np
 import pytest
 
@@ -52,6 +55,20 @@ def test_static_apply_matches_allocating_apply(B, ctx, storage):
         got_t, got = out_t.cpu().numpy(), out.cpu().numpy()
         np.testing.assert_array_equal(got_t, want_t)    # same kernels, same order: bitwise
         np.testing.assert_array_equal(got, want)
+        if call == 0:
+            # leave unrelated values in the shared array before the second
+            # call: a product whose intermediate is larger than the dense
+            # adjoint's partial sums
+            k = 300_000
+            other = B.operator_compose(ctx, "product", [
+                B.cf_op_dense(ctx, rng.standard_normal((8, k)).astype(np.float32), "fp32"),
+                B.cf_op_diag(ctx, k, rng.random(k).astype(np.float32))])
+            assert other.workspace_bytes() > op.workspace_bytes(adjoint=True)
+            xo = torch.from_numpy(rng.standard_normal(k).astype(np.float32)).cuda()
+            yo = torch.empty(8, device="cuda")
+            other.apply_static(xo, yo)
+            torch.cuda.synchronize()
+            np.testing.assert_array_equal(yo.cpu().numpy(), other.apply(xo.cpu().numpy()))
         # and within the float32 bound of the FP64 oracle
         ref = linop.apply(tree, yv.astype(np.float64), adjoint=True)
         absT = np.abs(linop.densify(tree))
