@@ -112,27 +112,36 @@ typedef struct {
                          iterations (CF_ENGINE_AUTO). */
 } cf_settings;
 
-/* The solver has two programs for the same iteration:
+/* The solver has three programs for the same iteration:
  *  - the graph engine: one CUDA graph per solve whose kernels each spread
  *    one step over the whole GPU (large problems);
  *  - the team engine: one persistent kernel in which a team of CTAs (one CTA,
  *    or a thread-block cluster) runs a problem's whole solve, synchronising
  *    with barriers instead of kernel boundaries, and a batch is one launch
  *    whose teams take problems from a longest-first work queue (small and
- *    medium problems, batches, serving).
- * Both compute the same iteration; their float32 rounding differs (other
- * reduction partitions).  The team engine supports operator trees of dense,
- * CSR, 1-D convolution (<= 2048 taps), diagonal and zero leaves under vstack,
- * hstack, blockdiag, sum, scale and adjoint, with at most 4 second-order
- * cones and dense leaves of at most 16384 columns. */
+ *    medium problems, batches, serving);
+ *  - the grid engine: the team engine's solve with every SM in the team
+ *    (one cooperative launch, one CTA per SM, grid-wide barriers and
+ *    reductions): one large problem's whole solve in one launch.
+ * All compute the same iteration; their float32 rounding differs (other
+ * reduction partitions).  The team and grid engines support operator trees
+ * of dense, CSR, 1-D convolution (direct sums up to 2048 taps, or overlap-save
+ * FFTs), diagonal and zero leaves under vstack, hstack, blockdiag, sum, scale
+ * and adjoint, with at most 4 second-order cones and dense leaves of at most
+ * 16384 columns. */
 typedef enum {
   CF_ENGINE_AUTO = 0,  /* team engine when the problem is supported and one
                           operator pass is at most the schedule's
                           auto_max_bytes (batch_max_bytes inside
                           solve_batch); graph engine otherwise */
   CF_ENGINE_GRAPH = 1, /* always the graph engine */
-  CF_ENGINE_TEAM = 2   /* always the team engine (CF_E_INVALID if the
+  CF_ENGINE_TEAM = 2,  /* always the team engine (CF_E_INVALID if the
                           problem is not supported) */
+  CF_ENGINE_GRID = 3   /* the grid engine for single solves (CF_E_INVALID if
+                          the problem is not supported); inside solve_batch it
+                          means CF_ENGINE_TEAM and in serving CF_ENGINE_AUTO.
+                          Each grid-wide barrier wait is bounded: if one gives
+                          up, the solve returns CF_E_CUDA. */
 } cf_engine;
 
 /* Launch schedule of the team engine, held by the context.  A problem's
@@ -415,6 +424,16 @@ cf_err serve_wait(cf_server* srv, cf_ticket t, int64_t timeout_ns, double* x, do
                   cf_info* info);
 /* Stop admitting, cancel queued requests, wait for running ones, free. */
 void serve_destroy(cf_server* srv);
+
+/* ------------------------------------------------------------ measurement
+ * The paper has no counterpart; this is a measurement helper.  Fused
+ * multiply-add rate of the context's GPU in float32 (fp64 == 0) or float64
+ * (fp64 != 0), in flop/s (an FMA counts 2): a full-occupancy grid of
+ * independent FMA chains, timed with CUDA events on the context stream (best
+ * of 3 launches of ~10 ms after one warm-up).  It is the measured denominator
+ * of the ALU-bound rooflines (the convolution leaves).  Blocks until done;
+ * allocates a few KB of stream-ordered scratch. */
+cf_err cf_measure_fma_rate(cf_ctx* ctx, int32_t fp64, double* flops_per_s);
 
 /* Text of the calling thread's last error ("" if none). */
 const char* cf_last_error(void);

@@ -45,8 +45,8 @@ class cf_settings(C.Structure):
                 ("host_loop", C.c_int32), ("engine", C.c_int32)]
 
 
-CF_ENGINE_AUTO, CF_ENGINE_GRAPH, CF_ENGINE_TEAM = 0, 1, 2
-ENGINE = {"auto": CF_ENGINE_AUTO, "graph": CF_ENGINE_GRAPH, "team": CF_ENGINE_TEAM}
+CF_ENGINE_AUTO, CF_ENGINE_GRAPH, CF_ENGINE_TEAM, CF_ENGINE_GRID = 0, 1, 2, 3
+ENGINE = {"auto": CF_ENGINE_AUTO, "graph": CF_ENGINE_GRAPH, "team": CF_ENGINE_TEAM, "grid": CF_ENGINE_GRID}
 
 
 class cf_schedule(C.Structure):
@@ -122,6 +122,7 @@ _sig = {
     "serve_submit": (C.c_int, [P, P, C.POINTER(cf_settings), C.POINTER(C.c_int64)]),
     "serve_wait": (C.c_int, [P, C.c_int64, C.c_int64, P, P, P, C.POINTER(cf_info)]),
     "serve_destroy": (None, [P]),
+    "cf_measure_fma_rate": (C.c_int, [P, C.c_int32, C.POINTER(C.c_double)]),
     "cf_last_error": (C.c_char_p, []),
 }
 for _name, (_res, _args) in _sig.items():
@@ -223,6 +224,12 @@ class Context:
     def sm_count(self):
         return lib.cf_ctx_sm_count(self.h)
 
+    def fma_rate(self, fp64=False):
+        """cf_measure_fma_rate: measured FMA rate of the GPU in flop/s."""
+        v = C.c_double()
+        check(lib.cf_measure_fma_rate(self.h, 1 if fp64 else 0, C.byref(v)), "cf_measure_fma_rate")
+        return v.value
+
     def close(self):
         if self.h:
             lib.cf_ctx_destroy(self.h)
@@ -265,7 +272,12 @@ class Operator:
 
     def apply_static(self, x, y, adjoint=False, alpha=1.0, accumulate=False, stream=None):
         """cf_op_apply_static on device tensors (scratch from the library's
-        static device array; nothing is allocated)."""
+        static device array; nothing is allocated).  Without ``stream`` the
+        call is enqueued on torch's current stream of x's device, so it is
+        ordered after the torch kernels that produced x and y."""
+        if stream is None and hasattr(x, "device"):
+            import torch
+            stream = torch.cuda.current_stream(x.device).cuda_stream
         check(lib.cf_op_apply_static(self.h, 1 if adjoint else 0, float(alpha), _ptr(x), _ptr(y),
                                      1 if accumulate else 0, C.c_void_p(stream) if stream else None),
               "cf_op_apply_static")

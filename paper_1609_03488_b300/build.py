@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "lib")
 LIBNAME = "libcvxb300.so"
 SOURCES = ["api.cu", "ops.cu", "k_leaf.cu", "k_fftconv.cu", "solver.cu", "serve.cu", "static_apply.cu", "team.cu",
-           "equil.cu"]
+           "equil.cu", "peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "--expt-relaxed-constexpr"]

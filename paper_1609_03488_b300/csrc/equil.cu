@@ -233,11 +233,16 @@ extern "C" cf_err cone_problem_equilibrate(cf_problem* P, int32_t iters, int32_t
       CF_CUDA(cudaMemsetAsync(cacc, 0, n * sizeof(float), st));
       for (int k = 0; k < probes; ++k) {
         const uint64_t base = (uint64_t)(t * probes + k) << 32;
+        // the probes' products are squared and summed into row / column
+        // norm estimates: convolutions by the direct sum, whose float32 error
+        // is bounded entry by entry (an FFT's is bounded per segment, which
+        // on the small entries of a random-sign product of a wide kernel is
+        // ~1e-5 relative and moves the scalings by as much)
         k_probe<<<gn, kThreads, 0, st>>>(n, seed, base, ev, xin);
-        op_apply(P->A, false, 1.f, xin, yout, false, ws, st);
+        op_apply(P->A, false, 1.f, xin, yout, false, ws, st, /*direct_conv=*/true);
         k_sqacc<<<gm, kThreads, 0, st>>>(m, d, yout, racc);
         k_probe<<<gm, kThreads, 0, st>>>(m, seed, base + (uint64_t)n, d, yin);
-        op_apply(P->A, true, 1.f, yin, xout, false, ws, st);
+        op_apply(P->A, true, 1.f, yin, xout, false, ws, st, /*direct_conv=*/true);
         k_sqacc<<<gn, kThreads, 0, st>>>(n, ev, xout, cacc);
       }
       if (nblk > 0) {

@@ -137,8 +137,11 @@ size_t op_ws_floats(const cf_op* op, bool trans);
 // Device bytes of the whole tree (shared parts counted once per reference).
 size_t op_tree_bytes(const cf_op* op);
 // y = alpha * op(x) + (acc ? y : 0), op(x) = A x or A^T x; ws: op_ws_floats floats.
+// direct_conv: 1-D convolution leaves use the direct sum even where the leaf
+// is evaluated by FFTs (entrywise float32 accuracy instead of a per-segment
+// 2-norm bound).
 void op_apply(const cf_op* op, bool trans, float alpha, const float* x, float* y, bool acc,
-              float* ws, cudaStream_t s);
+              float* ws, cudaStream_t s, bool direct_conv = false);
 void op_retain(cf_op* op);
 
 // ---- elementwise segments: y = sout * sum_k alpha_k d_k sin_k x_k (+ y if

@@ -76,6 +76,7 @@ bool overlap(const float* a, int64_t na, const float* b, int64_t nb) {
 struct EwQueue {
   EwBatch b{};
   cudaStream_t s;
+  bool direct_conv = false;  // evaluate FFT-method convolution leaves by the direct sum
   explicit EwQueue(cudaStream_t st) : s(st) { b.nseg = 0; }
   void flush() {
     launch_ew(s, b);
@@ -159,8 +160,9 @@ bool scalable(const cf_op* op) {
 // diag(D) A diag(E) whose leaves all take scalings is applied as A with the
 // two diagonals folded into A's leaf kernels (no separate passes).
 void op_apply(const cf_op* op, bool trans, float alpha, const float* x, float* y, bool acc,
-              float* ws, cudaStream_t s) {
+              float* ws, cudaStream_t s, bool direct_conv) {
   EwQueue q(s);
+  q.direct_conv = direct_conv;
   if (op->kind == OP_PRODUCT && op->parts.size() == 3 && op->parts[0]->kind == OP_DIAG &&
       op->parts[2]->kind == OP_DIAG && op->parts[0]->d && op->parts[2]->d && scalable(op->parts[1])) {
     const float* D = op->parts[0]->d;
@@ -206,7 +208,7 @@ void op_apply_rec(const cf_op* op, bool trans, float alpha, const float* x, floa
       return;
     case OP_CONV1D: {
       const int64_t nx = op->n, ny = op->m;
-      if (op->fft_tw) {
+      if (op->fft_tw && !q.direct_conv) {
         if (!trans)
           launch_conv1d_fft(s, ny, nx, op->Lp, 0, op->fft_hf, op->fft_tw, alpha, x, y, acc, sc.in, sc.out);
         else

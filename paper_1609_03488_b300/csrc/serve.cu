@@ -199,6 +199,9 @@ cf_err serve_submit(cf_server* s, cf_problem* p, const cf_settings* st, cf_ticke
     cf_settings_default(&cs);
   std::string why;
   if (!settings_valid(&cs, &why)) return fail(CF_E_INVALID, "serve_submit: " + why);
+  // a grid-engine solve holds every SM: served solves overlap, so they run
+  // on the other programs
+  if (cs.engine == CF_ENGINE_GRID) cs.engine = CF_ENGINE_AUTO;
   if (problem_bytes(p) > s->budget) return fail(CF_E_INVALID, "serve_submit: problem exceeds the memory budget");
   std::lock_guard<std::mutex> lk(s->mu);
   if (s->stopping) return fail(CF_E_STATE, "serve_submit: server is stopping");

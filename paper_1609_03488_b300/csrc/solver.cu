@@ -1165,9 +1165,11 @@ bool settings_valid(const cf_settings* st, std::string* why) {
   if (!(st->cg_tol_rel >= 0) || !(st->cg_tol_min >= 0) || !std::isfinite(st->cg_tol_exp))
     return bad("CG tolerance parameters must be >= 0");
   if (st->host_loop != 0 && st->host_loop != 1) return bad("host_loop must be 0 or 1");
-  if (st->engine != CF_ENGINE_AUTO && st->engine != CF_ENGINE_GRAPH && st->engine != CF_ENGINE_TEAM)
-    return bad("engine must be CF_ENGINE_AUTO, CF_ENGINE_GRAPH or CF_ENGINE_TEAM");
-  if (st->host_loop && st->engine == CF_ENGINE_TEAM) return bad("host_loop runs the graph engine's kernels");
+  if (st->engine != CF_ENGINE_AUTO && st->engine != CF_ENGINE_GRAPH && st->engine != CF_ENGINE_TEAM &&
+      st->engine != CF_ENGINE_GRID)
+    return bad("engine must be CF_ENGINE_AUTO, CF_ENGINE_GRAPH, CF_ENGINE_TEAM or CF_ENGINE_GRID");
+  if (st->host_loop && (st->engine == CF_ENGINE_TEAM || st->engine == CF_ENGINE_GRID))
+    return bad("host_loop runs the graph engine's kernels");
   return true;
 }
 
@@ -1220,12 +1222,15 @@ cf_err solve_launch(cf_problem* P, const cf_settings* st_in, double* x, double* 
   CF_TRY(ensure_state(P));
   write_settings(P, &st, warm_uv != nullptr);
   P->ran_setup = false;
-  if (engine == CF_ENGINE_TEAM) {
+  if (engine == CF_ENGINE_TEAM || engine == CF_ENGINE_GRID) {
     P->x_out = x;
     P->y_out = y;
     P->s_out = s;
     P->uv_out = uv_out;
-    CF_TRY(team::solo_launch(P, &st, warm_uv, join_ctx));
+    if (engine == CF_ENGINE_GRID)
+      CF_TRY(team::grid_launch(P, &st, warm_uv, join_ctx));
+    else
+      CF_TRY(team::solo_launch(P, &st, warm_uv, join_ctx));
     P->setup_ns_last = P->ran_setup ? now_ns() - t0 : 0;
     return CF_OK;
   }
@@ -1280,6 +1285,10 @@ cf_err solve_finish(cf_problem* P, cf_info* info) {
   if (P->uv_out) CF_TRY(copy_any(P->uv_out, P->uv_dev, 2 * N * sizeof(double), P->stream));
   CF_CUDA(cudaStreamSynchronize(P->stream));
   const Ctl& c = *P->ctl_host;
+  if (P->last_engine == CF_ENGINE_GRID && c.grid_abort) {
+    P->setup_done = false;  // g = M^-1 h may be incomplete: the next solve recomputes it
+    return fail(CF_E_CUDA, "solve: a grid-wide barrier wait of the grid engine gave up (the solve was abandoned)");
+  }
   if (info) {
     std::memset(info, 0, sizeof(*info));
     info->status = c.status;
@@ -1298,7 +1307,7 @@ cf_err solve_finish(cf_problem* P, cf_info* info) {
     info->kappa = c.kappa;
     info->setup_ns = P->setup_ns_last;
     info->solve_ns = t1 - P->t_launch;
-    if (P->last_engine == CF_ENGINE_TEAM) {
+    if (P->last_engine == CF_ENGINE_TEAM || P->last_engine == CF_ENGINE_GRID) {
       info->kernel_launches = P->team_launches;  // the whole solve is one persistent launch
       info->device_ns = c.t_end - c.t_start;
     } else {

@@ -31,6 +31,7 @@ struct Ctl {
   int cg_go, do_check, do_refresh, outer_go;
   unsigned int red_count;
   long long t_start, t_end;  // team engine: device clock (ns) at the solve's start and end
+  int grid_abort;            // grid team: a barrier wait gave up (the solve failed)
 };
 
 struct KernelCounts {
@@ -82,8 +83,9 @@ struct cf_problem {
   float* team_scratch = nullptr;  // adjoint dense partials (in the state arena)
   void* team_buf = nullptr;       // device launch table of solo launches
   void* team_buf_host = nullptr;  // pinned staging of that table
+  void* grid_buf = nullptr;       // grid team: barrier words and partial sums
   int setup_sig = 0;              // program that computed g: 0 none, 1 graph, >= 2 team
-  int last_engine = 0;            // CF_ENGINE_GRAPH or CF_ENGINE_TEAM
+  int last_engine = 0;            // CF_ENGINE_GRAPH, CF_ENGINE_TEAM or CF_ENGINE_GRID
   int64_t team_launches = 0;      // kernels attributed to this problem's last solve
   // equilibration (cone_problem_equilibrate): the solver's A is then
   // diag(D) A_orig diag(E), bf / cf hold sigma D b / rho E c
@@ -111,14 +113,17 @@ cf_err solve_launch(cf_problem* p, const cf_settings* st, double* x, double* y, 
 cf_err solve_finish(cf_problem* p, cf_info* info);
 bool settings_valid(const cf_settings* st, std::string* why);
 void write_settings(cf_problem* p, const cf_settings* st, bool warm);
-// Engine a solve of p with st runs on (CF_ENGINE_GRAPH or CF_ENGINE_TEAM), or
-// CF_E_INVALID when st asks for the team engine and p is not supported.
+// Engine a solve of p with st runs on (CF_ENGINE_GRAPH, CF_ENGINE_TEAM or
+// CF_ENGINE_GRID), or CF_E_INVALID when st asks for a team program and p is
+// not supported.
 cf_err pick_engine(cf_problem* p, const cf_settings* st, int* engine, bool in_batch = false);
 namespace team {
 // Flattens p's operator (at problem creation) and uploads the term lists.
 cf_err plan_problem(cf_problem* p);
 size_t scratch_floats(const cf_problem* p);
 cf_err solo_launch(cf_problem* p, const cf_settings* st, const double* warm_uv, bool join_ctx);
+// One cooperative launch in which every CTA (one per SM) carries p's solve.
+cf_err grid_launch(cf_problem* p, const cf_settings* st, const double* warm_uv, bool join_ctx);
 // Launches every problem of `probs` (all on the team engine, one context) in
 // one persistent kernel; each problem's stream is made to wait for it and
 // then copies the control block back and records ev_out.

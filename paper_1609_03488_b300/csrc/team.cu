@@ -26,14 +26,26 @@
 // every thread, since one SM's float64 rate is a small fraction of its
 // float32 rate.
 // Every loop is bounded by counters (max_iters, the CG caps, the queues); the
-// kernel has no spin-waits.
+// batch kernel has no spin-waits.
+//
+// The grid team (CF_ENGINE_GRID) is the same solve with every CTA of a
+// cooperative launch (one per SM) as one team: barriers are a grid-wide
+// arrive/wait on a global counter and generation word, and the CTAs add
+// their partial sums from global memory.  The cooperative launch makes the
+// runtime check that every CTA is resident, so every barrier completes; each
+// wait is still bounded (kGridSpinLimit polls), after which the CTA raises an
+// abort flag, every later barrier returns at once, the loops end, and the
+// host reports the solve as failed.  It carries one large problem through a
+// whole solve in one launch (no per-kernel launches, no graph control flow).
 #include <cooperative_groups.h>
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 
 #include "devutil.cuh"
+#include "fftconv.cuh"
 #include "solver.cuh"
 
 namespace cgr = cooperative_groups;
@@ -63,11 +75,25 @@ struct __align__(16) Prob {
 };
 static_assert(sizeof(Prob) % 16 == 0, "Prob is copied as 16-byte words");
 
+// Barrier words of a grid team (zeroed before each launch).
+struct GridBar {
+  unsigned int arrive;  // CTAs arrived at the current barrier
+  unsigned int gen;     // barriers completed
+  int abort;            // a wait gave up: every later barrier returns at once
+  int pad;
+};
+
+constexpr unsigned int kGridSpinLimit = 1u << 22;  // polls (~0.2 us apart) before a wait gives up
+
 struct Team {
   int C;     // CTAs in the team (1: this CTA alone)
   int rank;  // this CTA's rank in the team
   int tt;    // thread index in the team
   int TT;    // threads in the team
+  int grid = 0;            // the team is every CTA of a cooperative launch
+  GridBar* gb = nullptr;   // grid team: barrier words
+  float* gpart = nullptr;  // grid team: partial sums, [2][C][32] floats
+  unsigned int spin_limit = kGridSpinLimit;  // grid team: polls before a wait gives up
 };
 
 // Scalar state of a solve.  Thread 0 of every CTA of the team updates it from
@@ -93,8 +119,56 @@ struct __align__(16) Shared {
   int item;            // work-queue slot taken by the team's rank 0
 };
 
+__device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_gpu(unsigned int* p, unsigned int v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Grid-wide barrier of a grid team: every write of any CTA before it is
+// visible to every CTA after it.  Thread 0 arrives on the counter (the last
+// to arrive resets it and releases the next generation) and polls the
+// generation word, at most kGridSpinLimit times.
+__device__ __noinline__ void grid_sync(const Team& tm) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    GridBar* g = tm.gb;
+    if (!*(volatile int*)&g->abort) {
+      const unsigned int gen = ld_acquire_gpu(&g->gen);
+      __threadfence();
+      const unsigned int prev = atomicAdd(&g->arrive, 1u);
+      if (prev == (unsigned)tm.C - 1u) {
+        g->arrive = 0u;
+        __threadfence();
+        st_release_gpu(&g->gen, gen + 1u);
+      } else {
+        unsigned int k = 0;
+        while (ld_acquire_gpu(&g->gen) == gen) {
+          if (++k > tm.spin_limit || *(volatile int*)&g->abort) {
+            atomicExch(&g->abort, 1);
+            break;
+          }
+          __nanosleep(64);
+        }
+      }
+      __threadfence();
+    }
+  }
+  __syncthreads();
+}
+
+// Whether a grid team's barrier gave up (loops end early; the solve fails).
+__device__ __forceinline__ bool team_aborted(const Team& tm) {
+  return tm.grid && *(volatile int*)&tm.gb->abort != 0;
+}
+
 __device__ __forceinline__ void tsync(const Team& tm) {
-  if (tm.C > 1)
+  if (tm.grid)
+    grid_sync(tm);
+  else if (tm.C > 1)
     cgr::this_cluster().sync();
   else
     __syncthreads();
@@ -170,7 +244,16 @@ __device__ void team_sum(const Team& tm, Shared& sh, int& ph, Acc2 (&a)[NV], F&&
       th[j] = hi;  // lane 0's values are the CTA's sums
       tl[j] = lo;
     }
-    if (tm.C > 1) {
+    if (tm.grid) {
+      if (lane == 0) {
+        float* gp = tm.gpart + ((size_t)ph * tm.C + tm.rank) * 32;
+#pragma unroll
+        for (int j = 0; j < NV; ++j) {
+          gp[2 * j] = th[j];
+          gp[2 * j + 1] = tl[j];
+        }
+      }
+    } else if (tm.C > 1) {
       if (lane == 0) {
 #pragma unroll
         for (int j = 0; j < NV; ++j) {
@@ -185,7 +268,32 @@ __device__ void team_sum(const Team& tm, Shared& sh, int& ph, Acc2 (&a)[NV], F&&
       fin(tv);
     }
   }
-  if (tm.C > 1) {
+  if (tm.grid) {
+    // every CTA adds the C partials of each value in the same order: warp j
+    // takes value j, lane l the ranks l, l + 32, ..., then a fixed shuffle
+    // tree; thread 0 finishes with the totals
+    grid_sync(tm);
+    __shared__ double gtot[16];
+    if (wid < NV) {
+      float hi = 0.f, lo = 0.f;
+      const float* gp = tm.gpart + (size_t)ph * tm.C * 32 + 2 * wid;
+      for (int r = lane; r < tm.C; r += 32) df_add(hi, lo, __ldcg(gp + (size_t)r * 32), __ldcg(gp + (size_t)r * 32 + 1));
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+        const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+        df_add(hi, lo, h2, l2);
+      }
+      if (lane == 0) gtot[wid] = (double)hi + (double)lo;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double tv[NV];
+#pragma unroll
+      for (int j = 0; j < NV; ++j) tv[j] = gtot[j];
+      fin(tv);
+    }
+  } else if (tm.C > 1) {
     cgr::cluster_group cl = cgr::this_cluster();
     cl.sync();
     if (wid == 0) {
@@ -503,6 +611,30 @@ __device__ void term_conv(const Team& tm, const Term& t, const float* x, float* 
   }
 }
 
+// The 1-D convolution by overlap-save FFTs (fftconv.cuh): each 256 threads of
+// a CTA take pairs of segments in turn (pair g + groups x rank, + groups x C),
+// with a transform buffer of their own in the CTA's shared memory and a
+// named barrier of their own.  The input was written by other CTAs before a
+// team barrier, so it is read through L2 (no read-only path).
+__device__ __forceinline__ void group_bar(int id) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(256) : "memory");
+}
+
+template <bool SC>
+__device__ __noinline__ void term_fft(const Team& tm, const Term& t, const float* x, float* y, float* dsm) {
+  const int ng = blockDim.x >> 8, g = threadIdx.x >> 8, tl = threadIdx.x & 255;
+  const int Lp = (int)t.Lp;
+  const int64_t V = fftc::kN - Lp + 1;
+  const int64_t npairs = (t.rows + 2 * V - 1) / (2 * V);
+  const int64_t D = Lp - 1 - t.shift;
+  float2* buf = reinterpret_cast<float2*>(dsm) + (size_t)g * fftc::kBufF2;
+  __syncthreads();  // earlier users of the shared buffer are done
+  for (int64_t pr = (int64_t)tm.rank * ng + g; pr < npairs; pr += (int64_t)tm.C * ng)
+    fftc::pair<SC, false, false>(tl, pr, t.rows, t.cols, Lp, D, static_cast<const float2*>(t.a), t.tw, t.alpha,
+                                 x + t.xo, y + t.yo, t.acc != 0, t.sin, t.sout, buf, nullptr, nullptr,
+                                 [g] { group_bar(1 + g); });
+}
+
 // y = the flattened operator applied to x (terms in order).  Compiled once
 // per CTA size (not inlined at each call) so that the term loops get
 // registers of their own; with 64 registers a thread (1024 threads on an SM)
@@ -545,6 +677,12 @@ __device__ __noinline__ void apply(const Team& tm, const Term* terms, int nt, co
         break;
       case T_CONV:
         term_conv(tm, t, x, y, dsm);
+        break;
+      case T_FFT:
+        if (t.sin)
+          term_fft<true>(tm, t, x, y, dsm);
+        else
+          term_fft<false>(tm, t, x, y, dsm);
         break;
     }
   }
@@ -607,7 +745,7 @@ __device__ __noinline__ void cg_run(const Team& tm, Shared& sh, int& ph, float* 
     });
   }
   bool cont = sh.sc.cg_cont != 0;
-  while (cont) {
+  while (cont && !team_aborted(tm)) {
     // p (vector partition, followed by a sum or a barrier) -> t = A p -> q = A^T t
     apply<MaxT, MinB>(tm, P.fwd, P.nfwd, p, t, P.scratch, dsm, P.lanes);
     tsync(tm);
@@ -815,7 +953,7 @@ __device__ void solve_one(const Team& tm, Shared& sh, float* dsm) {
   const float af = (float)al, a1 = (float)(1.0 - al);
   const int64_t z = P.z, nl = P.z + P.l;
 
-  for (int guard = 0; guard < st.max_iters; ++guard) {
+  for (int guard = 0; guard < st.max_iters && !team_aborted(tm); ++guard) {
     // ---- w = u + v; rhs = w_x - A^T w_y
     TV4(v, m) {
       const float4 a = ld4v(P.uy, v), b = ld4v(P.vs, v);
@@ -1048,6 +1186,7 @@ __device__ void solve_one(const Team& tm, Shared& sh, float* dsm) {
     c->refreshes = s.refreshes;
     c->status = s.status;
     c->stop = 1;
+    c->grid_abort = team_aborted(tm) ? 1 : 0;
     if (P.do_setup && !P.tune) c->setup_iters = s.setup_iters;
     c->t_start = (long long)t_start;
     c->t_end = (long long)gtimer();
@@ -1099,6 +1238,25 @@ __global__ void __launch_bounds__(MaxT, MinB) k_team(const Prob* __restrict__ pr
     load_prob(sh, probs + order[nbig + it]);
     solve_one<MaxT, MinB>(tm, sh, dsm);
   }
+}
+
+// Grid team: every CTA of this cooperative launch carries the one problem.
+template <int MaxT, int MinB>
+__global__ void __launch_bounds__(MaxT, MinB) k_team_grid(const Prob* __restrict__ prob, GridBar* gb,
+                                                        float* gpart, unsigned int spin_limit) {
+  extern __shared__ __align__(16) float dsm[];
+  __shared__ Shared sh;
+  Team tm;
+  tm.grid = 1;
+  tm.gb = gb;
+  tm.gpart = gpart;
+  tm.spin_limit = spin_limit;
+  tm.C = (int)gridDim.x;
+  tm.rank = (int)blockIdx.x;
+  tm.TT = (int)(gridDim.x * blockDim.x);
+  tm.tt = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+  load_prob(sh, prob);
+  solve_one<MaxT, MinB>(tm, sh, dsm);
 }
 
 // ------------------------------------------------------------ host: planning
@@ -1154,6 +1312,17 @@ bool flatten(const cf_op* op, bool trans, float alpha, int64_t xo, int64_t yo, b
       out.push_back(t);
       return true;
     case OP_CONV1D:
+      if (op->fft_tw) {  // the leaf is evaluated by overlap-save FFTs
+        t.kind = T_FFT;
+        t.rows = trans ? op->n : op->m;
+        t.cols = trans ? op->m : op->n;
+        t.Lp = op->Lp;
+        t.shift = trans ? op->Lp - 1 : 0;
+        t.a = trans ? op->fft_ha : op->fft_hf;
+        t.tw = op->fft_tw;
+        out.push_back(t);
+        return true;
+      }
       if (op->Lp > kConvMaxLp) {
         *why = "convolution longer than " + std::to_string(kConvMaxLp) + " taps";
         return false;
@@ -1249,6 +1418,9 @@ double term_bytes(const Term& t) {
       // input + output, and the multiply-adds at 16 flops per byte (one SM's
       // FP32 rate over its share of the memory bandwidth)
       return 4.0 * (t.rows + t.cols) + 2.0 * t.Lp * t.rows / 16.0;
+    case T_FFT:
+      // input + output, and ~90 transform flops per output at 16 per byte
+      return 4.0 * (t.rows + t.cols) + 90.0 * t.rows / 16.0;
   }
   return 0.0;
 }
@@ -1317,6 +1489,16 @@ cf_err plan_problem(cf_problem* P) {
   }
   for (const std::vector<Term>* lst : {&pl.fwd, &pl.adj, &pl.adj_m})
     for (const Term& t : *lst) {
+      if (t.kind == T_FFT) {
+        if ((t.sin == nullptr) != (t.sout == nullptr)) {
+          pl.fwd.clear();
+          pl.adj.clear();
+          pl.adj_m.clear();
+          pl.why = "FFT convolution term with one of its two scalings";
+          return CF_OK;
+        }
+        pl.has_fft = true;
+      }
       if (t.kind == T_DENSE_N) smem = std::max<int64_t>(smem, (t.cols + 15) & ~(int64_t)15);
       if (t.kind == T_CONV) smem = std::max<int64_t>(smem, 2 * t.Lp + kConvTile + 2 * kConvR);
       if (t.kind == T_DENSE_T) pl.dense_t_cols = std::max(pl.dense_t_cols, t.rows);
@@ -1350,6 +1532,8 @@ size_t scratch_floats(const cf_problem* P) {
 void release(cf_problem* P) {
   if (P->team_terms) cudaFree(P->team_terms);
   if (P->team_buf) cudaFree(P->team_buf);
+  if (P->grid_buf) cudaFree(P->grid_buf);
+  P->grid_buf = nullptr;
   if (P->team_buf_host) cudaFreeHost(P->team_buf_host);
   P->team_terms = nullptr;
   P->team_buf = nullptr;
@@ -1522,6 +1706,7 @@ void build_table(const std::vector<cf_problem*>& probs, const cf_schedule& s, bo
     fill_prob(P, s, do_setup, tune, &ents[i]);
     (is_big(P, s) ? big : small).push_back((int32_t)i);
     smem = std::max(smem, (size_t)P->plan.smem_floats * sizeof(float));
+    if (P->plan.has_fft) smem = std::max(smem, (size_t)(s.threads / 256) * fftc::kBufF2 * sizeof(float2));
   }
   auto longer = [&](int32_t a, int32_t b) {
     const double wa = probs[a]->plan.pass_bytes, wb = probs[b]->plan.pass_bytes;
@@ -1597,6 +1782,87 @@ cf_err solo_launch(cf_problem* P, const cf_settings* st, const double* warm_uv, 
   P->setup_done = true;
   P->setup_sig = sig_for(P, s);
   P->last_engine = CF_ENGINE_TEAM;
+  P->team_launches = 1;
+  (void)st;
+  return CF_OK;
+}
+
+namespace {
+
+constexpr int kGridThreads = 512;  // threads per CTA of a grid team (two FFT transforms at a time)
+
+// Identifies the grid team's reduction partitions (distinct from every
+// batch schedule's).
+int grid_sig(int C, int lanes) { return 2 + ((1000 + C) * 4096 + kGridThreads) * 64 + lanes; }
+
+}  // namespace
+
+cf_err grid_launch(cf_problem* P, const cf_settings* st, const double* warm_uv, bool join_ctx) {
+  cf_schedule s = sched_of(P->ctx);
+  s.cluster = 1;
+  s.threads = kGridThreads;
+  s.ctas_per_sm = 1;
+  const int C = P->ctx->sm_count;  // one CTA per SM
+  size_t smem = (size_t)P->plan.smem_floats * sizeof(float);
+  if (P->plan.has_fft) smem = std::max(smem, (size_t)(kGridThreads / 256) * fftc::kBufF2 * sizeof(float2));
+  auto kern = k_team_grid<kGridThreads, 1>;
+  if (smem > 48 * 1024) CF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  CF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kGridThreads, smem));
+  if (per_sm < 1) return fail(CF_E_INVALID, "solve: the grid engine's kernel does not fit on an SM");
+  const size_t bytes = table_bytes(1);
+  if (!P->team_buf) {
+    cudaError_t e = cudaMalloc(&P->team_buf, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      P->team_buf = nullptr;
+      return fail(CF_E_OOM, "solve: team launch table allocation failed");
+    }
+    CF_CUDA(cudaMallocHost(&P->team_buf_host, bytes));
+  }
+  const size_t gbytes = 256 + (size_t)2 * C * 32 * sizeof(float);
+  if (!P->grid_buf) {
+    cudaError_t e = cudaMalloc(&P->grid_buf, gbytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      P->grid_buf = nullptr;
+      return fail(CF_E_OOM, "solve: grid barrier allocation failed");
+    }
+  }
+  const int64_t N = P->n + P->m + 1;
+  CF_CUDA(cudaEventRecord(P->ev_in, P->ctx->stream));
+  CF_CUDA(cudaStreamWaitEvent(P->stream, P->ev_in, 0));
+  if (warm_uv) CF_TRY(copy_any(P->warm_dev, warm_uv, 2 * N * sizeof(double), P->stream));
+  const int sig = grid_sig(C, lanes_for(P->plan, s));
+  const bool do_setup = !(P->setup_done && P->setup_sig == sig);
+  // the pinned staging buffer is free: the previous solve of P finished
+  Prob* ph = (Prob*)P->team_buf_host;
+  fill_prob(P, s, do_setup, false, ph);
+  CF_CUDA(cudaMemcpyAsync(P->team_buf, ph, sizeof(Prob), cudaMemcpyHostToDevice, P->stream));
+  CF_CUDA(cudaMemsetAsync(P->grid_buf, 0, sizeof(GridBar), P->stream));
+  P->t_launch = now_ns();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)C);
+  cfg.blockDim = dim3((unsigned)kGridThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = P->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  // CVXB300_GRID_SPIN_LIMIT (tests of the give-up path) lowers the poll limit
+  unsigned int spin = kGridSpinLimit;
+  if (const char* ev = std::getenv("CVXB300_GRID_SPIN_LIMIT")) spin = (unsigned int)std::strtoul(ev, nullptr, 10);
+  CF_CUDA(cudaLaunchKernelEx(&cfg, kern, (const Prob*)P->team_buf, (GridBar*)P->grid_buf,
+                             (float*)((char*)P->grid_buf + 256), spin));
+  CF_CUDA(cudaMemcpyAsync(P->ctl_host, P->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, P->stream));
+  CF_CUDA(cudaEventRecord(P->ev_out, P->stream));
+  if (join_ctx) CF_CUDA(cudaStreamWaitEvent(P->ctx->stream, P->ev_out, 0));
+  P->ran_setup = do_setup;
+  P->setup_done = true;
+  P->setup_sig = sig;
+  P->last_engine = CF_ENGINE_GRID;
   P->team_launches = 1;
   (void)st;
   return CF_OK;
@@ -1704,9 +1970,14 @@ cf_err pick_engine(cf_problem* P, const cf_settings* st, int* engine, bool in_ba
     *engine = CF_ENGINE_GRAPH;
     return CF_OK;
   }
-  if (st->engine == CF_ENGINE_TEAM) {
+  if (st->engine == CF_ENGINE_TEAM || (st->engine == CF_ENGINE_GRID && in_batch)) {
     if (!P->plan.ok) return fail(CF_E_INVALID, "solve: the team engine does not support this problem: " + P->plan.why);
     *engine = CF_ENGINE_TEAM;
+    return CF_OK;
+  }
+  if (st->engine == CF_ENGINE_GRID) {
+    if (!P->plan.ok) return fail(CF_E_INVALID, "solve: the grid engine does not support this problem: " + P->plan.why);
+    *engine = CF_ENGINE_GRID;
     return CF_OK;
   }
   double lim;

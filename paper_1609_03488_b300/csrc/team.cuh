@@ -20,7 +20,7 @@ constexpr int kDenseMaxCols = 16384;// forward dense input staged in shared memo
 constexpr int kDenseTGroups = 16;   // row groups of the adjoint dense product
 constexpr int kCsrStageFloats = 40960; // CSR input staged in shared memory up to this length
 
-enum TermKind : int32_t { T_FILL = 0, T_DIAG = 1, T_CSR = 2, T_DENSE_N = 3, T_DENSE_T = 4, T_CONV = 5 };
+enum TermKind : int32_t { T_FILL = 0, T_DIAG = 1, T_CSR = 2, T_DENSE_N = 3, T_DENSE_T = 4, T_CONV = 5, T_FFT = 6 };
 
 // One leaf application y[yo : yo + rows] (+)= sout * alpha * leaf(sin * x[xo : xo + cols]).
 // `sync`: a team barrier runs first (an earlier term since the last barrier
@@ -35,6 +35,7 @@ struct __align__(16) Term {
   const int32_t* rowptr;  // CSR (for the adjoint: the stored transpose)
   const int32_t* col;
   int64_t lda, Lp, shift; // dense leading dimension; conv padded taps and shift
+  const float2* tw;       // FFT convolution: twiddle tables (a: the spectrum)
   // diagonal scalings around the leaf (equilibration), aligned with the
   // term's slices: x[xo + j] is read as sin[j] x[xo + j], and the term's
   // result for y[yo + i] is multiplied by sout[i]; null means 1
@@ -51,7 +52,8 @@ struct Plan {
   double pass_bytes = 0;    // bytes (and flop-equivalents) of one forward pass
   double avg_row_nnz = 0;   // CSR leaves of the forward pass
   int64_t dense_t_cols = 0; // widest adjoint dense output (row-group partials)
-  int64_t smem_floats = 0;  // dynamic shared memory the terms need
+  int64_t smem_floats = 0;  // dynamic shared memory the terms need (FFT terms aside)
+  bool has_fft = false;     // FFT convolution terms: one transform buffer per 256 threads
 };
 
 }  // namespace team

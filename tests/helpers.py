@@ -54,3 +54,41 @@ def fp64_residuals(prob, x, y, s):
 def objective_rel_err(p, p_star):
     """|p - p*| / (1 + |p*|)."""
     return abs(p - p_star) / (1.0 + abs(p_star))
+
+
+def fp32_fft_trajectory(prob, k_max, **solve_kw):
+    """The oracle's trajectory with every 1-D convolution of the iterations
+    evaluated by a float32 FFT (scipy's single-precision transform, not this
+    library's), the equilibration kept exact: how far float32 FFT rounding
+    alone moves the iterates.  Returns (exact, perturbed) oracle results."""
+    import scipy.fft as sfft
+
+    from oracle import equil, linop, scs
+    kw = dict(max_iters=k_max, check_interval=10 ** 6, linsys="cg", cg_fixed_steps=3, trajectory=k_max)
+    kw.update(solve_kw)
+    eq_kw = kw.pop("equilibrate", None)
+    eq = (equil.equilibrate(scs.Operator(prob["A"]), prob["cone"], prob["b"], prob["c"], **eq_kw)
+          if eq_kw else None)
+    exact = scs.solve(prob["A"], prob["b"], prob["c"], prob["cone"], equil=eq, **kw)
+    plain = linop.apply
+
+    def fft32(op, x, adjoint=False):
+        if op["kind"] != "conv1d":
+            return plain(op, x, adjoint)
+        k = np.asarray(op["kernel"], dtype=np.float32)
+        v = np.asarray(x, dtype=np.float32)
+        L = k.size
+        if not adjoint:
+            m = v.size + L - 1
+            nf = sfft.next_fast_len(m)
+            return sfft.irfft(sfft.rfft(v, nf) * sfft.rfft(k, nf), nf)[:m].astype(np.float64)
+        n = v.size - L + 1
+        nf = sfft.next_fast_len(v.size)
+        return sfft.irfft(sfft.rfft(v, nf) * np.conj(sfft.rfft(k, nf)), nf)[:n].astype(np.float64)
+
+    linop.apply = fft32
+    try:
+        pert = scs.solve(prob["A"], prob["b"], prob["c"], prob["cone"], equil=eq, **kw)
+    finally:
+        linop.apply = plain
+    return exact, pert

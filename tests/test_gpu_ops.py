@@ -269,3 +269,14 @@ def test_device_pointers(B, ctx):
     torch.cuda.synchronize()
     ref = D.astype(float) @ x.cpu().numpy().astype(float)
     assert_fp32_matvec(y.cpu().numpy(), ref, np.abs(D) @ np.abs(x.cpu().numpy()), 48, "device ptrs")
+
+
+def test_measured_fma_rates_are_plausible(B, ctx):
+    """cf_measure_fma_rate, the measured denominator of the ALU rooflines:
+    float32 within [0.5, 1.05] of SMs x 128 lanes x 2 flop x the maximum SM
+    clock (2032 MHz on B300), float64 positive and well below float32."""
+    fp32 = ctx.fma_rate(False)
+    fp64 = ctx.fma_rate(True)
+    nominal = ctx.sm_count * 128 * 2 * 2032e6
+    assert 0.5 * nominal <= fp32 <= 1.05 * nominal, (fp32, nominal)
+    assert 0 < fp64 < 0.5 * fp32, (fp64, fp32)

@@ -24,7 +24,7 @@ from tests.helpers import fp64_residuals, objective_rel_err, rel
 
 pytestmark = pytest.mark.gpu
 EPS = 1e-4
-ENGINES = ["graph", "team"]
+ENGINES = ["graph", "team", "grid"]
 
 
 @pytest.fixture(scope="module")
@@ -258,7 +258,7 @@ def test_invalid_inputs(B, ctx):
         B.Problem(ctx, op, prob["b"], prob["c"], {"z": 0, "l": 50, "q": [0, 55]})
     P = B.Problem(ctx, op, prob["b"], prob["c"], prob["cone"])
     for bad in (dict(alpha=2.5), dict(eps=0.0), dict(max_iters=0), dict(check_interval=0), dict(engine=7),
-                dict(engine=2, host_loop=1)):
+                dict(engine=2, host_loop=1), dict(engine=3, host_loop=1)):
         with pytest.raises(B.CfError) as e:
             B.solve(P, B.settings(**bad))
         assert e.value.code == B.CF_E_INVALID
@@ -368,3 +368,23 @@ def test_serving_rejects_oversized_and_times_out(B, ctx):
         srv.wait(t, P, timeout_ns=0)
     assert e.value.code == B.CF_E_STATE
     srv.close()
+
+
+def test_grid_engine_gives_up_cleanly_when_a_barrier_wait_runs_out(B, ctx, monkeypatch):
+    """Every grid-wide barrier wait of the grid engine is bounded.  With the
+    poll limit lowered to zero (a launch-time override) the first wait gives
+    up: the kernel raises its abort flag, every CTA leaves its loops, and the
+    solve returns CF_E_CUDA; the context and the problem stay usable and the
+    next solve (normal limit) recomputes the setup and is correct."""
+    prob = synth.deconv(n_x=20000, L=100, seed=5)
+    P = B.cone_problem_create(ctx, prob)
+    monkeypatch.setenv("CVXB300_GRID_SPIN_LIMIT", "0")
+    with pytest.raises(B.CfError) as e:
+        B.solve(P, B.settings(engine="grid", max_iters=50))
+    assert e.value.code == B.CF_E_CUDA and "gave up" in str(e.value)
+    monkeypatch.delenv("CVXB300_GRID_SPIN_LIMIT")
+    info_g, x_g, *_ = B.solve(P, B.settings(engine="grid", max_iters=200, check_interval=10 ** 6, cg_fixed_iters=3))
+    info_r, x_r, *_ = B.solve(B.cone_problem_create(ctx, prob),
+                              B.settings(engine="grid", max_iters=200, check_interval=10 ** 6, cg_fixed_iters=3))
+    assert info_g["iters"] == info_r["iters"] == 200
+    np.testing.assert_array_equal(x_g, x_r)
