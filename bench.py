@@ -71,8 +71,16 @@ OPTIMUM_FILE = os.path.join(ROOT, "tests", "golden", "deconv_large_optimum.json"
 # pass that the equilibrated solver runs.
 CONV_NCU = {"traffic_bytes": 4029184, "src_sha256_16": "f372736cf1cfc748"}
 FFT_NCU = {"traffic_bytes": None, "src_sha256_16": None}
-FFT_N = 4096
 FFT_AUTO_LP = (256, 2048)   # padded tap counts for which the library's auto method takes the FFT
+FFT_2048_MAX_LP = 1024      # the library takes 2048-point transforms up to this many padded taps when
+                            # 4096-point ones would give fewer pairs than twice the SMs
+
+
+def fft_size(Lp, n_out, sm_count):
+    """The transform size the library picks for a convolution leaf."""
+    v4096 = 4096 - Lp + 1
+    pairs4096 = -(-n_out // (2 * v4096))
+    return 2048 if (Lp <= FFT_2048_MAX_LP and pairs4096 < 2 * sm_count) else 4096
 FP32_LANES_PER_SM = 128
 L2_FLUSH_BYTES = 256 << 20
 PROFILE = False   # set by --profile
@@ -719,11 +727,12 @@ def deconv_roofline(B, ctx, torch, stream, prob, W, P, conv_method, eq, small, r
     direct_adj = 2.0 * L * nx
     Lp = (L + 15) // 16 * 16
     fft = conv_method == "fft" or (conv_method == "auto" and FFT_AUTO_LP[0] <= Lp <= FFT_AUTO_LP[1])
+    fft_n = fft_size(Lp, nx + L - 1, ctx.sm_count) if fft else None
     if fft:
-        # overlap-save: per pair of segments one complex FFT_N-point transform
+        # overlap-save: per pair of segments one complex N-point transform
         # each way (5 N log2 N flops, the usual count) and the spectrum product
-        v = FFT_N - Lp + 1
-        per_pair = 2 * 5 * FFT_N * np.log2(FFT_N) + 6 * FFT_N
+        v = fft_n - Lp + 1
+        per_pair = 2 * 5 * fft_n * np.log2(fft_n) + 6 * fft_n
         flops_fwd = per_pair * np.ceil((nx + L - 1) / (2 * v))
         flops_adj = per_pair * np.ceil(nx / (2 * v))
     else:
@@ -750,7 +759,7 @@ def deconv_roofline(B, ctx, torch, stream, prob, W, P, conv_method, eq, small, r
             "fp64_fma_TFLOPs_measured": fp64,
             "per_launch_ms": {"forward": 1e3 * t_fwd, "adjoint": 1e3 * t_adj},
             "flops_per_launch": {"forward": flops_fwd, "adjoint": flops_adj},
-            "flops_definition": ("FFT method: pairs x (2 x 5 N log2 N + 6 N), N = 4096" if fft
+            "flops_definition": (f"FFT method: pairs x (2 x 5 N log2 N + 6 N), N = {fft_n}" if fft
                                  else "direct sum: 2 L per output"),
             "algorithmic_bytes_per_launch": {"forward": by_fwd, "adjoint": by_adj},
             "hbm_frac_of_launch": (by_fwd + by_adj) / (t_fwd + t_adj) / 1e9 / hbm_peak(),

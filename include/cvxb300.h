@@ -247,6 +247,14 @@ cf_err cf_op_zero(cf_ctx* ctx, int64_t m, int64_t n, cf_op** out);
 cf_err operator_compose(cf_ctx* ctx, cf_compose_kind kind, cf_op* const* parts, int32_t k,
                         double alpha, cf_op** out);
 
+/* Kronecker product A (x) B (Section 3.1 lists it among the structured
+ * operators; the paper's image example uses it for separable kernels):
+ * (mA mB) x (nA nB), row-major vec: (A (x) B) vec(X) = vec(A X B^T), applied
+ * as two GEMMs without forming the product.  The same operator as
+ * operator_compose(CF_KRON, {A, B}); both parts dense FP32 leaves
+ * (CF_E_INVALID otherwise).  The result references A and B. */
+cf_err cf_op_kron(cf_ctx* ctx, cf_op* A, cf_op* B, cf_op** out);
+
 /* Drop the caller's reference. NULL is ignored. */
 void cf_op_destroy(cf_op* op);
 

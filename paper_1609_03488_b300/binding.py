@@ -97,6 +97,7 @@ _sig = {
     "cf_op_diag": (C.c_int, [P, C.c_int64, P, PP]),
     "cf_op_zero": (C.c_int, [P, C.c_int64, C.c_int64, PP]),
     "operator_compose": (C.c_int, [P, C.c_int, PP, C.c_int32, C.c_double, PP]),
+    "cf_op_kron": (C.c_int, [P, P, P, PP]),
     "cf_op_destroy": (None, [P]),
     "cf_op_shape": (C.c_int, [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "cf_op_apply": (C.c_int, [P, C.c_int32, P, P]),
@@ -350,6 +351,11 @@ def operator_compose(ctx, kind, parts, alpha=1.0):
     arr = (C.c_void_p * len(parts))(*[p.h.value for p in parts])
     h = _new("operator_compose", ctx.h, COMPOSE[kind], arr, len(parts), float(alpha))
     return Operator(ctx, h)
+
+
+def cf_op_kron(ctx, A, Bop):
+    """cf_op_kron: A (x) B of two dense FP32 operators."""
+    return Operator(ctx, _new("cf_op_kron", ctx.h, A.h, Bop.h), keep=(A, Bop))
 
 
 def build_operator(ctx, node):

@@ -105,6 +105,7 @@ struct cf_op {
   // conv1d by overlap-save FFTs (when chosen): the twiddle table and the
   // spectra of the forward and adjoint taps (see k_fftconv.cu)
   float2 *fft_tw = nullptr, *fft_hf = nullptr, *fft_ha = nullptr;
+  int fft_n = 0;  // transform size of the FFT method (4096 or 2048)
   // conv2d
   int64_t h = 0, w = 0, kh = 0, kw = 0;
   float *k2_fwd = nullptr, *k2_adj = nullptr;
@@ -140,8 +141,27 @@ size_t op_tree_bytes(const cf_op* op);
 // direct_conv: 1-D convolution leaves use the direct sum even where the leaf
 // is evaluated by FFTs (entrywise float32 accuracy instead of a per-segment
 // 2-norm bound).
+// skip_parts: when the operator is a vstack (possibly inside the
+// equilibration product), parts k with skip_parts[k] != 0 are left out: no
+// outputs written forward, no contribution adjoint.
 void op_apply(const cf_op* op, bool trans, float alpha, const float* x, float* y, bool acc,
-              float* ws, cudaStream_t s, bool direct_conv = false);
+              float* ws, cudaStream_t s, bool direct_conv = false, const uint8_t* skip_parts = nullptr);
+
+// Row blocks of a vstack operator that are one diagonal leaf on a column
+// slice (the other leaves of the block zero): rows [r0, r0 + len) of A hold
+// alpha d_j at column c0 + j (d == nullptr: the identity).  Such a block adds
+// the diagonal alpha^2 d^2 to A^T A, and its rows of A z are alpha d z[cols],
+// so the solver folds it out of its CG passes.
+constexpr int kMaxFold = 4;
+struct DiagBlock {
+  int64_t r0, c0, len;
+  float alpha;
+  const float* d;
+};
+// Fills `blocks` (at most kMaxFold) and `skip` (one flag per vstack part) for
+// the solver's operator A (the core of an equilibration product, if any);
+// false when nothing can be folded or nothing would remain.
+bool fold_diag_blocks(const cf_op* A, std::vector<DiagBlock>* blocks, std::vector<uint8_t>* skip);
 void op_retain(cf_op* op);
 
 // ---- elementwise segments: y = sout * sum_k alpha_k d_k sin_k x_k (+ y if
@@ -188,17 +208,19 @@ void launch_diag(cudaStream_t s, int64_t n, const float* d, float alpha, const f
 void launch_conv1d(cudaStream_t s, int64_t n_out, int64_t n_in, int64_t Lp, int64_t shift,
                    const float* wrev, float alpha, const float* x, float* y, bool acc,
                    const float* sin = nullptr, const float* sout = nullptr);
-// The same operation as launch_conv1d by overlap-save FFTs of kFftConvN
-// points (Lp <= kFftConvMaxLp); H = the spectrum of the taps in the kernel's
-// order, scaled by 1 / kFftConvN; tw = the kernel's twiddle tables
-// (kFftConvTw values; k_fftconv.cu gives both layouts).
-constexpr int kFftConvN = 4096;
+// The same operation as launch_conv1d by overlap-save FFTs of fft_n points
+// (4096, or 2048 when Lp <= kFftConv2048MaxLp and the larger transform would
+// leave SMs idle; Lp <= kFftConvMaxLp); H = the spectrum of the taps in the
+// kernel's order, scaled by 1 / fft_n (fft_n values); tw = the kernel's
+// twiddle tables (fft_n + fft_n / 16 values; fftconv.cuh gives both layouts).
+constexpr int kFftConvN = 4096;            // largest transform
 constexpr int kFftConvMaxLp = 2048;
-constexpr int kFftConvAutoMinLp = 256;  // CF_CONV_AUTO uses the FFT from here on
+constexpr int kFftConv2048MaxLp = 1024;    // the 2048-point transform keeps >= half its outputs
+constexpr int kFftConvAutoMinLp = 256;     // CF_CONV_AUTO uses the FFT from here on
 constexpr int kFftConvTw = kFftConvN + 256;
 cf_err conv1d_fft_prepare(int device);  // once per device before the first launch (not during capture)
-void launch_conv1d_fft(cudaStream_t s, int64_t n_out, int64_t n_in, int64_t Lp, int64_t shift, const float2* H,
-                       const float2* tw, float alpha, const float* x, float* y, bool acc,
+void launch_conv1d_fft(cudaStream_t s, int fft_n, int64_t n_out, int64_t n_in, int64_t Lp, int64_t shift,
+                       const float2* H, const float2* tw, float alpha, const float* x, float* y, bool acc,
                        const float* sin = nullptr, const float* sout = nullptr);
 void launch_conv2d(cudaStream_t s, int64_t Ho, int64_t Wo, int64_t Hi, int64_t Wi, int64_t kh,
                    int64_t kw, int64_t sh, int64_t sw, const float* kern, float alpha,

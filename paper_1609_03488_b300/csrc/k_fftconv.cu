@@ -7,15 +7,16 @@
 // with D = Lp - 1 - shift (in = 0 outside [0, n_in)), i.e. a linear
 // convolution of z[m] = in[m - D] with h[v] = wrev[Lp - 1 - v]:
 // out[i] = (h * z)[i + Lp - 1].  Overlap-save: for a segment
-// seg[t] = z[i0 + t], t < N (N = 4096), the circular convolution with h
+// seg[t] = z[i0 + t], t < N (N = 4096 or 2048), the circular convolution with h
 // (zero-padded to N) equals the linear one for t >= Lp - 1, giving outputs
 // i0 .. i0 + V - 1 (V = N - Lp + 1).  Two consecutive segments travel as the
 // real and imaginary parts of one complex FFT: h is real, so the inverse
 // transform returns the two real convolutions in the two parts.
 //
-// One CTA of 256 threads transforms one pair in shared memory:
-//   forward: decimation in frequency, three radix-16 stages (natural order in,
-//            base-16 digit-reversed order out);
+// One CTA of N/16 threads transforms one pair in shared memory:
+//   forward: decimation in frequency, radix-16, radix-16 and radix-16 (N =
+//            4096) or radix-8 (N = 2048) stages (natural order in,
+//            digit-reversed order out);
 //   product: with H (the DFT of h, precomputed in FP64 on the host, scaled
 //            by 1/N, permuted to the digit-reversed order);
 //   inverse: decimation in time, the three stages transposed (digit-reversed
@@ -24,10 +25,10 @@
 // global memory and the last inverse stage writes the outputs; the innermost
 // stage, the product and its inverse run in registers; four shared-memory
 // round trips remain.  Twiddles come from tables rounded from FP64 and laid
-// out so that a warp's loads are contiguous: stage 0's W4096^(t q) at
-// tw[q 256 + t], stage 1's W256^(j q) at tw[4096 + q 16 + j]; the spectrum is
-// stored the same way, H[q 256 + t] for the value thread t multiplies into its
-// q-th output.
+// out so that a warp's loads are contiguous (fftconv.cuh).  The 2048-point
+// transform (128 threads a pair) is taken when the 4096-point one would give
+// fewer pairs than twice the SMs: 2.95x the CTAs for 1.37x the flops at 1000
+// taps, so that several CTAs share each SM and hide each other's latency.
 #include <mutex>
 
 #include "fftconv.cuh"
@@ -35,18 +36,16 @@
 namespace cf {
 namespace {
 
-using fftc::kN;
-using fftc::kT;
-
-template <bool SC>
-__global__ void __launch_bounds__(kT, 2)
+template <int N, bool SC>
+__global__ void __launch_bounds__(N / 16, N == 4096 ? 2 : 4)
 k_conv1d_fft(int64_t n_out, int64_t n_in, int Lp, int64_t D, const float2* __restrict__ H,
              const float2* __restrict__ tw, float alpha, const float* __restrict__ x, float* __restrict__ y,
              bool acc, const float* __restrict__ sin, const float* __restrict__ sout) {
-  __shared__ __align__(16) float2 buf[fftc::kBufF2];
+  constexpr int T = N / 16;
+  __shared__ __align__(16) float2 buf[fftc::buf_f2<N>()];
   extern __shared__ float tail[];  // acc: y, SC: sout, over this pair's outputs
   const int t = threadIdx.x;
-  const int V = kN - Lp + 1;
+  const int V = N - Lp + 1;
   const int64_t i0 = (int64_t)blockIdx.x * 2 * V;  // first output of the pair
   // what the epilogue reads besides the transform is copied in now, while the
   // transform runs
@@ -54,14 +53,39 @@ k_conv1d_fft(int64_t n_out, int64_t n_in, int Lp, int64_t D, const float2* __res
   float* ys = tail;
   float* ss = tail + (acc ? 2 * V : 0);
   if (acc || SC) {
-    for (int j = t; j < nout; j += kT) {
+    for (int j = t; j < nout; j += T) {
       if (acc) fftc::cp_async4(ys + j, y + i0 + j);
       if (SC) fftc::cp_async4(ss + j, sout + i0 + j);
     }
     fftc::cp_async_commit();
   }
-  fftc::pair<SC, true, true>(t, blockIdx.x, n_out, n_in, Lp, D, H, tw, alpha, x, y, acc, sin, sout, buf, ys, ss,
-                             [] { __syncthreads(); }, acc || SC);
+  fftc::pair<N, SC, true, true>(t, blockIdx.x, n_out, n_in, Lp, D, H, tw, alpha, x, y, acc, sin, sout, buf, ys,
+                                ss, [] { __syncthreads(); }, acc || SC);
+}
+
+template <int N>
+cudaError_t raise_limit() {
+  const int lim = 2 * 2 * (N - 16 + 1) * (int)sizeof(float);
+  cudaError_t e = cudaFuncSetAttribute(k_conv1d_fft<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_conv1d_fft<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  return e;
+}
+
+template <int N>
+void launch_n(cudaStream_t s, int64_t n_out, int64_t n_in, int64_t Lp, int64_t shift, const float2* H,
+              const float2* tw, float alpha, const float* x, float* y, bool acc, const float* sin,
+              const float* sout) {
+  const int64_t V = N - Lp + 1;
+  const int64_t pairs = (n_out + 2 * V - 1) / (2 * V);
+  const int64_t D = Lp - 1 - shift;
+  const bool sc = sin || sout;
+  const size_t dyn = (size_t)((acc ? 2 * V : 0) + (sc ? 2 * V : 0)) * sizeof(float);
+  if (sc)
+    k_conv1d_fft<N, true><<<(unsigned)pairs, N / 16, dyn, s>>>(n_out, n_in, (int)Lp, D, H, tw, alpha, x, y, acc,
+                                                                 sin, sout);
+  else
+    k_conv1d_fft<N, false><<<(unsigned)pairs, N / 16, dyn, s>>>(n_out, n_in, (int)Lp, D, H, tw, alpha, x, y,
+                                                                  acc, nullptr, nullptr);
 }
 
 }  // namespace
@@ -75,31 +99,22 @@ cf_err conv1d_fft_prepare(int device) {
   static cudaError_t err[kMaxDevices];
   if (device < 0 || device >= kMaxDevices) return fail(CF_E_INVALID, "conv1d FFT: device index out of range");
   std::call_once(once[device], [device] {
-    const int lim = 2 * 2 * (kN - 16 + 1) * (int)sizeof(float);
-    err[device] = cudaFuncSetAttribute(k_conv1d_fft<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-    if (err[device] == cudaSuccess)
-      err[device] = cudaFuncSetAttribute(k_conv1d_fft<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    err[device] = raise_limit<4096>();
+    if (err[device] == cudaSuccess) err[device] = raise_limit<2048>();
   });
   if (err[device] != cudaSuccess)
     return fail(CF_E_CUDA, std::string("conv1d FFT: shared memory limit: ") + cudaGetErrorString(err[device]));
   return CF_OK;
 }
 
-void launch_conv1d_fft(cudaStream_t s, int64_t n_out, int64_t n_in, int64_t Lp, int64_t shift, const float2* H,
-                       const float2* tw, float alpha, const float* x, float* y, bool acc, const float* sin,
-                       const float* sout) {
+void launch_conv1d_fft(cudaStream_t s, int fft_n, int64_t n_out, int64_t n_in, int64_t Lp, int64_t shift,
+                       const float2* H, const float2* tw, float alpha, const float* x, float* y, bool acc,
+                       const float* sin, const float* sout) {
   if (n_out <= 0) return;
-  const int64_t V = kN - Lp + 1;
-  const int64_t pairs = (n_out + 2 * V - 1) / (2 * V);
-  const int64_t D = Lp - 1 - shift;
-  const bool sc = sin || sout;
-  const size_t dyn = (size_t)((acc ? 2 * V : 0) + (sc ? 2 * V : 0)) * sizeof(float);
-  if (sc)
-    k_conv1d_fft<true><<<(unsigned)pairs, kT, dyn, s>>>(n_out, n_in, (int)Lp, D, H, tw, alpha, x, y, acc, sin,
-                                                        sout);
+  if (fft_n == 2048)
+    launch_n<2048>(s, n_out, n_in, Lp, shift, H, tw, alpha, x, y, acc, sin, sout);
   else
-    k_conv1d_fft<false><<<(unsigned)pairs, kT, dyn, s>>>(n_out, n_in, (int)Lp, D, H, tw, alpha, x, y, acc,
-                                                         nullptr, nullptr);
+    launch_n<4096>(s, n_out, n_in, Lp, shift, H, tw, alpha, x, y, acc, sin, sout);
 }
 
 }  // namespace cf

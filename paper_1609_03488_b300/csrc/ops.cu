@@ -138,7 +138,7 @@ struct Scales {
 };
 
 void op_apply_rec(const cf_op* op, bool trans, float alpha, const float* x, float* y, bool acc,
-                  float* ws, cudaStream_t s, EwQueue& q, Scales sc);
+                  float* ws, cudaStream_t s, EwQueue& q, Scales sc, const uint8_t* skip = nullptr);
 
 // Whether every leaf below takes input / output scalings.
 bool scalable(const cf_op* op) {
@@ -160,24 +160,97 @@ bool scalable(const cf_op* op) {
 // diag(D) A diag(E) whose leaves all take scalings is applied as A with the
 // two diagonals folded into A's leaf kernels (no separate passes).
 void op_apply(const cf_op* op, bool trans, float alpha, const float* x, float* y, bool acc,
-              float* ws, cudaStream_t s, bool direct_conv) {
+              float* ws, cudaStream_t s, bool direct_conv, const uint8_t* skip_parts) {
   EwQueue q(s);
   q.direct_conv = direct_conv;
   if (op->kind == OP_PRODUCT && op->parts.size() == 3 && op->parts[0]->kind == OP_DIAG &&
       op->parts[2]->kind == OP_DIAG && op->parts[0]->d && op->parts[2]->d && scalable(op->parts[1])) {
     const float* D = op->parts[0]->d;
     const float* E = op->parts[2]->d;
-    op_apply_rec(op->parts[1], trans, alpha, x, y, acc, ws, s, q, trans ? Scales{D, E} : Scales{E, D});
+    op_apply_rec(op->parts[1], trans, alpha, x, y, acc, ws, s, q, trans ? Scales{D, E} : Scales{E, D}, skip_parts);
   } else {
-    op_apply_rec(op, trans, alpha, x, y, acc, ws, s, q, Scales{});
+    op_apply_rec(op, trans, alpha, x, y, acc, ws, s, q, Scales{}, skip_parts);
   }
   q.flush();
 }
 
 namespace {
 
+// A diagonal leaf (possibly under scale nodes): its product of scales and d.
+bool diag_leaf(const cf_op* op, float* alpha, const float** d) {
+  float a = 1.f;
+  while (op->kind == OP_SCALE) {
+    a *= (float)op->alpha;
+    op = op->parts[0];
+  }
+  if (op->kind != OP_DIAG) return false;
+  *alpha = a;
+  *d = op->d;
+  return true;
+}
+
+}  // namespace
+
+bool fold_diag_blocks(const cf_op* A, std::vector<DiagBlock>* blocks, std::vector<uint8_t>* skip) {
+  blocks->clear();
+  skip->clear();
+  const cf_op* core = A;
+  if (A->kind == OP_PRODUCT && A->parts.size() == 3 && A->parts[0]->kind == OP_DIAG &&
+      A->parts[2]->kind == OP_DIAG && A->parts[0]->d && A->parts[2]->d) {
+    if (!scalable(A->parts[1])) return false;  // op_apply would not fold the scalings
+    core = A->parts[1];
+  }
+  if (core->kind != OP_VSTACK) return false;
+  skip->assign(core->parts.size(), 0);
+  int64_t r0 = 0;
+  size_t kept = 0;
+  for (size_t k = 0; k < core->parts.size(); ++k) {
+    const cf_op* p = core->parts[k];
+    float alpha = 1.f;
+    const float* d = nullptr;
+    int64_t c0 = -1;
+    if (diag_leaf(p, &alpha, &d)) {
+      c0 = 0;
+    } else if (p->kind == OP_HSTACK) {
+      int64_t off = 0;
+      int ndiag = 0;
+      bool other = false;
+      for (const cf_op* c : p->parts) {
+        float a2;
+        const float* d2;
+        if (c->kind == OP_ZERO) {
+        } else if (diag_leaf(c, &a2, &d2)) {
+          ++ndiag;
+          alpha = a2;
+          d = d2;
+          c0 = off;
+        } else {
+          other = true;
+        }
+        off += c->n;
+      }
+      if (other || ndiag != 1) c0 = -1;
+    }
+    if (c0 >= 0 && blocks->size() < (size_t)kMaxFold) {
+      blocks->push_back(DiagBlock{r0, c0, p->m, alpha, d});
+      (*skip)[k] = 1;
+    } else {
+      ++kept;
+    }
+    r0 += p->m;
+  }
+  if (blocks->empty() || kept == 0) {
+    blocks->clear();
+    skip->clear();
+    return false;
+  }
+  return true;
+}
+
+namespace {
+
 void op_apply_rec(const cf_op* op, bool trans, float alpha, const float* x, float* y, bool acc,
-                  float* ws, cudaStream_t s, EwQueue& q, Scales sc) {
+                  float* ws, cudaStream_t s, EwQueue& q, Scales sc, const uint8_t* skip) {
   const int64_t out_dim = trans ? op->n : op->m;
   // Elementwise leaves are queued; any other leaf first launches the queue,
   // so operations keep their order wherever they could interact.
@@ -210,10 +283,10 @@ void op_apply_rec(const cf_op* op, bool trans, float alpha, const float* x, floa
       const int64_t nx = op->n, ny = op->m;
       if (op->fft_tw && !q.direct_conv) {
         if (!trans)
-          launch_conv1d_fft(s, ny, nx, op->Lp, 0, op->fft_hf, op->fft_tw, alpha, x, y, acc, sc.in, sc.out);
+          launch_conv1d_fft(s, op->fft_n, ny, nx, op->Lp, 0, op->fft_hf, op->fft_tw, alpha, x, y, acc, sc.in, sc.out);
         else
-          launch_conv1d_fft(s, nx, ny, op->Lp, op->Lp - 1, op->fft_ha, op->fft_tw, alpha, x, y, acc, sc.in,
-                            sc.out);
+          launch_conv1d_fft(s, op->fft_n, nx, ny, op->Lp, op->Lp - 1, op->fft_ha, op->fft_tw, alpha, x, y, acc,
+                            sc.in, sc.out);
       } else if (!trans) {
         launch_conv1d(s, ny, nx, op->Lp, 0, op->w_fwd, alpha, x, y, acc, sc.in, sc.out);
       } else {
@@ -238,18 +311,23 @@ void op_apply_rec(const cf_op* op, bool trans, float alpha, const float* x, floa
       return;
     case OP_VSTACK:
     case OP_HSTACK: {
-      // "stacked" along the output dimension: vstack forward, hstack adjoint
+      // "stacked" along the output dimension: vstack forward, hstack adjoint;
+      // skipped parts (a vstack's folded diagonal blocks) are left out
       const bool split_out = (op->kind == OP_VSTACK) != trans;
       int64_t off = 0;
       bool first = true;
-      for (const cf_op* p : op->parts) {
+      for (size_t k = 0; k < op->parts.size(); ++k) {
+        const cf_op* p = op->parts[k];
+        const bool skipped = skip && op->kind == OP_VSTACK && skip[k];
         if (split_out) {
-          op_apply_rec(p, trans, alpha, x, y + off, acc, ws, s, q, sc.shift(0, off));
+          if (!skipped) op_apply_rec(p, trans, alpha, x, y + off, acc, ws, s, q, sc.shift(0, off));
           off += trans ? p->n : p->m;
         } else {
-          op_apply_rec(p, trans, alpha, x + off, y, first ? acc : true, ws, s, q, sc.shift(off, 0));
+          if (!skipped) {
+            op_apply_rec(p, trans, alpha, x + off, y, first ? acc : true, ws, s, q, sc.shift(off, 0));
+            first = false;
+          }
           off += trans ? p->m : p->n;
-          first = false;
         }
       }
       return;
@@ -490,36 +568,40 @@ void fft_host(std::vector<std::complex<double>>& a) {
       }
 }
 
-// Spectrum of h[v] = wrev[Lp - 1 - v] (zero-padded to kFftConvN) in the FFT
-// kernel's order, scaled by 1 / kFftConvN: after the forward transform, the
-// value at position p = 16 t + q (q0 256 + q1 16 + q2 in base 16) is
-// H[q0 + 16 q1 + 256 q2], and thread t reads its q-th factor at q 256 + t.
-std::vector<float2> fft_taps(const std::vector<float>& wrev) {
+// Spectrum of h[v] = wrev[Lp - 1 - v] (zero-padded to N) in the FFT kernel's
+// order, scaled by 1 / N: after the forward stages the value at position
+// p = 16 t + q holds frequency (p >> lg) + 16 ((p >> ls) & 15) + 256 (p & (S-1))
+// (G = N/16 = 2^lg, S = G/16 = 2^ls), and thread t reads its q-th factor at
+// q (N/16) + t.
+std::vector<float2> fft_taps(const std::vector<float>& wrev, int N) {
   const int64_t Lp = (int64_t)wrev.size();
-  std::vector<std::complex<double>> h(kFftConvN, 0.0);
+  const int T = N / 16, lg = N == 4096 ? 8 : 7, ls = lg - 4, S = 1 << ls;
+  std::vector<std::complex<double>> h(N, 0.0);
   for (int64_t v = 0; v < Lp; ++v) h[v] = wrev[Lp - 1 - v];
   fft_host(h);
-  std::vector<float2> out(kFftConvN);
-  for (int p = 0; p < kFftConvN; ++p) {
-    const int k = (p >> 8) + ((p >> 4) & 15) * 16 + (p & 15) * 256;
-    const std::complex<double> v = h[k] / (double)kFftConvN;
-    out[(p & 15) * 256 + (p >> 4)] = make_float2((float)v.real(), (float)v.imag());
+  std::vector<float2> out(N);
+  for (int p = 0; p < N; ++p) {
+    const int k = (p >> lg) + ((p >> ls) & 15) * 16 + (p & (S - 1)) * 256;
+    const std::complex<double> v = h[k] / (double)N;
+    out[(p & 15) * T + (p >> 4)] = make_float2((float)v.real(), (float)v.imag());
   }
   return out;
 }
 
-// The FFT kernel's twiddles: W4096^(t q) at q 256 + t (t < 256, q < 16), then
-// W256^(j q) at 4096 + q 16 + j (j, q < 16), W_N = exp(-2 pi i / N).
-std::vector<float2> fft_twiddles() {
-  std::vector<float2> tw(kFftConvTw);
+// The FFT kernel's twiddles: W_N^(t q) at q T + t (t < T = N/16, q < 16),
+// then W_G^(j q) at N + q S + j (j < S, q < 16; G = N/16, S = G/16),
+// W_M = exp(-2 pi i / M).
+std::vector<float2> fft_twiddles(int N) {
+  const int T = N / 16, G = N / 16, S = G / 16;
+  std::vector<float2> tw(N + G);
   auto w = [](int64_t e, int64_t n) {
     const double th = -2.0 * M_PI * (double)(e % n) / (double)n;
     return make_float2((float)std::cos(th), (float)std::sin(th));
   };
   for (int q = 0; q < 16; ++q)
-    for (int t = 0; t < 256; ++t) tw[q * 256 + t] = w((int64_t)t * q, 4096);
+    for (int t = 0; t < T; ++t) tw[q * T + t] = w((int64_t)t * q, N);
   for (int q = 0; q < 16; ++q)
-    for (int j = 0; j < 16; ++j) tw[4096 + q * 16 + j] = w((int64_t)j * q, 256);
+    for (int j = 0; j < S; ++j) tw[N + q * S + j] = w((int64_t)j * q, G);
   return tw;
 }
 
@@ -560,13 +642,18 @@ cf_err cf_op_conv1d_method(cf_ctx* ctx, int64_t n, const float* kernel, int64_t 
     CF_CUDA(cudaMemcpy(op->w_adj, wa.data(), op->Lp * 4, cudaMemcpyHostToDevice));
     if (use_fft) {
       CF_TRY(conv1d_fft_prepare(ctx->device));
-      const std::vector<float2> tw = fft_twiddles(), hf = fft_taps(wf), ha = fft_taps(wa);
-      CF_TRY(dev_alloc(&op->fft_tw, kFftConvTw, &op->device_bytes));
-      CF_TRY(dev_alloc(&op->fft_hf, kFftConvN, &op->device_bytes));
-      CF_TRY(dev_alloc(&op->fft_ha, kFftConvN, &op->device_bytes));
-      CF_CUDA(cudaMemcpy(op->fft_tw, tw.data(), kFftConvTw * sizeof(float2), cudaMemcpyHostToDevice));
-      CF_CUDA(cudaMemcpy(op->fft_hf, hf.data(), kFftConvN * sizeof(float2), cudaMemcpyHostToDevice));
-      CF_CUDA(cudaMemcpy(op->fft_ha, ha.data(), kFftConvN * sizeof(float2), cudaMemcpyHostToDevice));
+      // 2048-point transforms when the 4096-point ones would give fewer pairs
+      // (CTAs) than twice the SMs and the kernel leaves them >= half their outputs
+      const int64_t pairs4096 = (n + L - 1 + 2 * (4096 - Lp_ + 1) - 1) / (2 * (4096 - Lp_ + 1));
+      const int N = (Lp_ <= kFftConv2048MaxLp && pairs4096 < 2 * (int64_t)ctx->sm_count) ? 2048 : 4096;
+      op->fft_n = N;
+      const std::vector<float2> tw = fft_twiddles(N), hf = fft_taps(wf, N), ha = fft_taps(wa, N);
+      CF_TRY(dev_alloc(&op->fft_tw, tw.size(), &op->device_bytes));
+      CF_TRY(dev_alloc(&op->fft_hf, N, &op->device_bytes));
+      CF_TRY(dev_alloc(&op->fft_ha, N, &op->device_bytes));
+      CF_CUDA(cudaMemcpy(op->fft_tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice));
+      CF_CUDA(cudaMemcpy(op->fft_hf, hf.data(), N * sizeof(float2), cudaMemcpyHostToDevice));
+      CF_CUDA(cudaMemcpy(op->fft_ha, ha.data(), N * sizeof(float2), cudaMemcpyHostToDevice));
     }
     return CF_OK;
   };
@@ -692,6 +779,12 @@ cf_err operator_compose(cf_ctx* ctx, cf_compose_kind kind, cf_op* const* parts, 
   }
   *out = op;
   return CF_OK;
+}
+
+cf_err cf_op_kron(cf_ctx* ctx, cf_op* A, cf_op* B, cf_op** out) {
+  if (!A || !B) return fail(CF_E_INVALID, "cf_op_kron: NULL part");
+  cf_op* parts[2] = {A, B};
+  return operator_compose(ctx, CF_KRON, parts, 2, 1.0, out);
 }
 
 void cf_op_destroy(cf_op* op) {

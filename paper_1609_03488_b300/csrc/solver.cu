@@ -172,17 +172,112 @@ __global__ void k_init(Ctl* c, int64_t n, int64_t m, float* ux, float* uy, float
   }
 }
 
-// w_y = u_y + v_s, rhs = u_x (then rhs -= A^T w_y by the operator walk)
+// ---- folded diagonal row blocks
+// Block of row r, or -1.
+__device__ __forceinline__ int fold_row(const Fold& f, int64_t r) {
+  for (int b = 0; b < f.nb; ++b)
+    if (r >= f.r0[b] && r < f.r0[b] + f.len[b]) return b;
+  return -1;
+}
+// Whether any folded block touches columns (or rows) [lo, lo + 4).
+__device__ __forceinline__ bool fold_cols_touch(const Fold& f, int64_t lo) {
+  for (int b = 0; b < f.nb; ++b)
+    if (lo < f.c0[b] + f.len[b] && f.c0[b] < lo + 4) return true;
+  return false;
+}
+__device__ __forceinline__ bool fold_rows_touch(const Fold& f, int64_t lo) {
+  for (int b = 0; b < f.nb; ++b)
+    if (lo < f.r0[b] + f.len[b] && f.r0[b] < lo + 4) return true;
+  return false;
+}
+__device__ __forceinline__ bool fold_rows_cover(const Fold& f, int64_t lo) {
+  for (int b = 0; b < f.nb; ++b)
+    if (lo >= f.r0[b] && lo + 4 <= f.r0[b] + f.len[b]) return true;
+  return false;
+}
+// The one block whose rows (cols: its columns) hold all of [lo, lo + 4), with
+// its row-to-column offset a multiple of 4 (16-byte loads on both sides), and
+// no other block touching them; -1 otherwise.
+template <bool COLS>
+__device__ __forceinline__ int fold_vec_block(const Fold& f, int64_t lo) {
+  int hit = -1;
+  for (int b = 0; b < f.nb; ++b) {
+    const int64_t a = COLS ? f.c0[b] : f.r0[b];
+    if (lo < a + f.len[b] && a < lo + 4) {
+      if (hit >= 0 || lo < a || lo + 4 > a + f.len[b] || ((f.c0[b] - f.r0[b]) & 3)) return -1;
+      hit = b;
+    }
+  }
+  return hit;
+}
+
+// Diagonal of each folded block's rows, s_r = D_r alpha d_j E_(c0 + j)
+// (j = r - r0; D, E the equilibration, 1 without), and per column the sum of
+// s^2 over the blocks covering it.
+struct FoldSrc {
+  float alpha[kMaxFold];
+  const float* d[kMaxFold];
+};
+__global__ void k_fold_prep(Fold f, FoldSrc src, int64_t m, int64_t n, const float* __restrict__ D,
+                            const float* __restrict__ E, float* __restrict__ s, float* __restrict__ gd) {
+  auto val = [&](int b, int64_t j) {
+    const int64_t r = f.r0[b] + j, c = f.c0[b] + j;
+    float v = src.alpha[b] * (src.d[b] ? src.d[b][j] : 1.f);
+    if (D) v *= D[r];
+    if (E) v *= E[c];
+    return v;
+  };
+  GRID_STRIDE(r, m) {
+    const int b = fold_row(f, r);
+    s[r] = b >= 0 ? val(b, r - f.r0[b]) : 0.f;
+  }
+  GRID_STRIDE(c, n) {
+    float g = 0.f;
+    for (int b = 0; b < f.nb; ++b)
+      if (c >= f.c0[b] && c < f.c0[b] + f.len[b]) {
+        const float v = val(b, c - f.c0[b]);
+        g = fmaf(v, v, g);
+      }
+    gd[c] = g;
+  }
+}
+
+// w_y = u_y + v_s, rhs = u_x (then rhs -= A^T w_y by the operator walk); the
+// folded blocks' part of A^T w_y is subtracted here: rhs_c -= s_r w_y,r for
+// the rows r of the blocks covering column c.
 __global__ void k_rhs(Ctl* c, int64_t n, int64_t m, const float* __restrict__ ux,
                       const float* __restrict__ uy, const float* __restrict__ vs,
-                      float* __restrict__ wy, float* __restrict__ rhs) {
+                      float* __restrict__ wy, float* __restrict__ rhs, Fold f) {
   VEC4_LOOP(v, m >> 2) {
     const float4 a = ld4(uy, v), b = ld4(vs, v);
     st4(wy, v, make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w));
   }
   TAIL_LOOP(i, m) wy[i] = uy[i] + vs[i];
-  VEC4_LOOP(v, n >> 2) st4(rhs, v, ld4(ux, v));
-  TAIL_LOOP(i, n) rhs[i] = ux[i];
+  auto folded = [&](int64_t col, float x) {
+    for (int b = 0; b < f.nb; ++b)
+      if (col >= f.c0[b] && col < f.c0[b] + f.len[b]) {
+        const int64_t r = f.r0[b] + (col - f.c0[b]);
+        x = fmaf(-f.s[r], uy[r] + vs[r], x);
+      }
+    return x;
+  };
+  VEC4_LOOP(v, n >> 2) {
+    float4 x = ld4(ux, v);
+    if (f.nb && fold_cols_touch(f, 4 * v)) {
+      const int b = fold_vec_block<true>(f, 4 * v);
+      if (b >= 0) {
+        const int64_t rv = v + ((f.r0[b] - f.c0[b]) >> 2);
+        const float4 s4 = ld4(f.s, rv), a4 = ld4(uy, rv), b4 = ld4(vs, rv);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) el(x, k) = fmaf(-elc(s4, k), elc(a4, k) + elc(b4, k), el(x, k));
+      } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) el(x, k) = folded(4 * v + k, el(x, k));
+      }
+    }
+    st4(rhs, v, x);
+  }
+  TAIL_LOOP(i, n) rhs[i] = f.nb ? folded(i, ux[i]) : ux[i];
   if (blockIdx.x == 0 && threadIdx.x == 0) c->w_tau = c->tau + c->kappa;
 }
 
@@ -198,41 +293,51 @@ __global__ void k_rhs(Ctl* c, int64_t n, int64_t m, const float* __restrict__ ux
 
 // r = rhs - G z; p = r; stopping threshold.  fresh != 0: gz holds A^T A z
 // just computed, and G z = gz + lam z is formed (and kept) here.
+//
+// gd (folded diagonal blocks, may be null): the Gram's diagonal part beyond
+// lam; then q is started at (lam + gd) p, onto which the next Gram pass adds
+// the remaining blocks' A^T A p.
 __global__ void k_cg_init(Ctl* c, int64_t n, const float* __restrict__ rhs,
                           const float* __restrict__ z, float* __restrict__ gz,
                           float* __restrict__ r, float* __restrict__ p, double* part, int mode,
-                          int fresh, cudaGraphConditionalHandle h, int in_graph) {
+                          int fresh, cudaGraphConditionalHandle h, int in_graph,
+                          const float* __restrict__ gd, float* __restrict__ q) {
   const float lam = (float)c->lam;
   Acc2 a0, a1;
   VEC4_LOOP(v, n >> 2) {
     float4 g = ld4(gz, v);
     const float4 rh = ld4(rhs, v);
+    const float4 dg = gd ? ld4(gd, v) : make_float4(0.f, 0.f, 0.f, 0.f);
     if (fresh) {
       const float4 zz = ld4(z, v);
 #pragma unroll
-      for (int k = 0; k < 4; ++k) el(g, k) = fmaf(lam, elc(zz, k), el(g, k));
+      for (int k = 0; k < 4; ++k) el(g, k) = fmaf(lam + elc(dg, k), elc(zz, k), el(g, k));
       st4(gz, v, g);
     }
-    float4 rr;
+    float4 rr, qq;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       el(rr, k) = elc(rh, k) - elc(g, k);
+      el(qq, k) = (lam + elc(dg, k)) * el(rr, k);
       a0.add_prod(elc(rr, k), elc(rr, k));
       a1.add_prod(elc(rh, k), elc(rh, k));
     }
     st4(r, v, rr);
     st4(p, v, rr);
+    if (gd) st4(q, v, qq);
   }
   TAIL_LOOP(i, n) {
     float g = gz[i];
+    const float dg = gd ? gd[i] : 0.f;
     if (fresh) {
-      g = fmaf(lam, z[i], g);
+      g = fmaf(lam + dg, z[i], g);
       gz[i] = g;
     }
     const float rh = rhs[i];
     float ri = rh - g;
     r[i] = ri;
     p[i] = ri;
+    if (gd) q[i] = (lam + dg) * ri;
     a0.add_prod(ri, ri);
     a1.add_prod(rh, rh);
   }
@@ -262,9 +367,10 @@ __global__ void k_cg_init(Ctl* c, int64_t n, const float* __restrict__ rhs,
   }
 }
 
-// q += lam p (q held A^T A p); alpha = rr / p^T q
+// q += lam p (q held A^T A p); alpha = rr / p^T q.  folded: q already holds
+// (lam + gd) p + A^T A p over the remaining blocks, and is only read.
 __global__ void k_cg_dot(Ctl* c, int64_t n, const float* __restrict__ p, float* __restrict__ q,
-                         double* part) {
+                         double* part, int folded) {
   const float lam = (float)c->lam;
   Acc2 a0;
   VEC4_LOOP(w, n >> 2) {
@@ -272,15 +378,15 @@ __global__ void k_cg_dot(Ctl* c, int64_t n, const float* __restrict__ p, float* 
     float4 qq = ld4(q, w);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      el(qq, k) = el(qq, k) + lam * elc(pp, k);
+      if (!folded) el(qq, k) = el(qq, k) + lam * elc(pp, k);
       a0.add_prod(elc(pp, k), elc(qq, k));
     }
-    st4(q, w, qq);
+    if (!folded) st4(q, w, qq);
   }
   TAIL_LOOP(i, n) {
     const float pi = p[i];
-    float qi = q[i] + lam * pi;
-    q[i] = qi;
+    float qi = folded ? q[i] : q[i] + lam * pi;
+    if (!folded) q[i] = qi;
     a0.add_prod(pi, qi);
   }
   double v[1] = {a0.value()};
@@ -295,7 +401,7 @@ __global__ void k_cg_dot(Ctl* c, int64_t n, const float* __restrict__ p, float* 
 __global__ void k_cg_update(Ctl* c, int64_t n, int64_t m, float* __restrict__ z, float* __restrict__ r,
                             const float* __restrict__ p, const float* __restrict__ q,
                             float* __restrict__ gz, float* __restrict__ az,
-                            const float* __restrict__ t, double* part, int mode) {
+                            const float* __restrict__ t, double* part, int mode, Fold f) {
   const float a = (float)c->alpha_cg;
   Acc2 a0;
   VEC4_LOOP(v, n >> 2) {
@@ -322,7 +428,9 @@ __global__ void k_cg_update(Ctl* c, int64_t n, int64_t m, float* __restrict__ z,
   }
   double v[1] = {a0.value()};
   if (az) {
+    // rows of folded blocks: A z there is s z, formed where it is used
     VEC4_LOOP(w, m >> 2) {
+      if (f.nb && fold_rows_cover(f, 4 * w)) continue;
       const float4 tt = ld4(t, w);
       float4 aa = ld4(az, w);
 #pragma unroll
@@ -353,17 +461,28 @@ __global__ void k_cg_update(Ctl* c, int64_t n, int64_t m, float* __restrict__ z,
 // p = r + beta p; decide whether the CG loop runs again.  The guard counter
 // is advanced here by one thread, so the loop ends after at most `cap` steps
 // whatever the reductions produced.
+// gd (folded blocks): also start the next Gram pass's q at (lam + gd) p.
 __global__ void k_cg_p(Ctl* c, int64_t n, const float* __restrict__ r, float* __restrict__ p,
-                       int mode, cudaGraphConditionalHandle h, int in_graph) {
+                       int mode, cudaGraphConditionalHandle h, int in_graph, const float* __restrict__ gd,
+                       float* __restrict__ q) {
   const float b = (float)c->beta_cg;
+  const float lam = (float)c->lam;
   VEC4_LOOP(v, n >> 2) {
     const float4 rr = ld4(r, v);
     float4 pp = ld4(p, v);
 #pragma unroll
     for (int k = 0; k < 4; ++k) el(pp, k) = fmaf(b, el(pp, k), elc(rr, k));
     st4(p, v, pp);
+    if (gd) {
+      const float4 dg = ld4(gd, v);
+      st4(q, v, make_float4((lam + dg.x) * pp.x, (lam + dg.y) * pp.y, (lam + dg.z) * pp.z, (lam + dg.w) * pp.w));
+    }
   }
-  TAIL_LOOP(i, n) p[i] = fmaf(b, p[i], r[i]);
+  TAIL_LOOP(i, n) {
+    const float pi = fmaf(b, p[i], r[i]);
+    p[i] = pi;
+    if (gd) q[i] = (lam + gd[i]) * pi;
+  }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     const int g = ++c->cg_guard;
     int cap = mode == CG_SETUP ? c->st.setup_cg_max : (c->st.cg_fixed > 0 ? c->st.cg_fixed : c->st.cg_max);
@@ -381,12 +500,30 @@ __global__ void k_gz_shift(const Ctl* c, int64_t n, const float* __restrict__ z,
 
 // ------------------------------------------------------------ subspace step
 // z_y = w_y + A z_x (A z_x carried in az); u~_tau = (w_tau + c^T z_x + b^T z_y) / (1 + h^T g)
+// (rows of folded blocks: A z_x there is s z_x[c0 + j])
 __global__ void k_utau(Ctl* c, int64_t n, int64_t m, const float* __restrict__ zx,
                        const float* __restrict__ az, float* __restrict__ zy, const float* __restrict__ wy,
-                       const float* __restrict__ bf, const float* __restrict__ cf, double* part) {
+                       const float* __restrict__ bf, const float* __restrict__ cf, double* part, Fold f) {
   Acc2 a0;
+  auto azr = [&](int64_t r, float carried) {
+    const int b = fold_row(f, r);
+    return b < 0 ? carried : f.s[r] * zx[f.c0[b] + (r - f.r0[b])];
+  };
   VEC4_LOOP(w, m >> 2) {
-    const float4 aa = ld4(az, w), ww = ld4(wy, w), bb = ld4(bf, w);
+    const float4 ww = ld4(wy, w), bb = ld4(bf, w);
+    float4 aa;
+    const bool touch = f.nb && fold_rows_touch(f, 4 * w);
+    const int vb = touch ? fold_vec_block<false>(f, 4 * w) : -1;
+    if (vb >= 0) {  // four rows of one block: s z_x[c0 + j], 16-byte loads
+      const float4 s4 = ld4(f.s, w), z4 = ld4(zx, w + ((f.c0[vb] - f.r0[vb]) >> 2));
+      aa = make_float4(s4.x * z4.x, s4.y * z4.y, s4.z * z4.z, s4.w * z4.w);
+    } else {
+      aa = ld4(az, w);
+      if (touch) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) el(aa, k) = azr(4 * w + k, el(aa, k));
+      }
+    }
     float4 zz;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -396,7 +533,7 @@ __global__ void k_utau(Ctl* c, int64_t n, int64_t m, const float* __restrict__ z
     st4(zy, w, zz);
   }
   TAIL_LOOP(i, m) {
-    float zi = az[i] + wy[i];
+    float zi = (f.nb ? azr(i, az[i]) : az[i]) + wy[i];
     zy[i] = zi;
     a0.add_prod(bf[i], zi);
   }
@@ -802,7 +939,9 @@ int count_kernels(cudaGraph_t g) {
   return k;
 }
 
-// Buffers of one CG run on (lam I + A^T A) z = rhs.
+// Buffers of one CG run on (lam I + A^T A) z = rhs.  With folded diagonal
+// blocks (fold.nb > 0), the Gram pass applies A's other blocks (skip) and the
+// blocks' diagonal (fold.gd) enters through q's start value.
 struct CgBufs {
   Ctl* ctl;
   const cf_op* A;
@@ -810,6 +949,8 @@ struct CgBufs {
   float *z, *rhs, *r, *p, *q, *t, *ws;
   float *gz, *az;  // G z and A z carried along (az may be null)
   double* part;
+  Fold fold = {};
+  const uint8_t* skip = nullptr;
 };
 
 // Loop-decision handles of the graph being captured; in_graph == 0 when the
@@ -819,34 +960,42 @@ struct Conds {
   int in_graph = 1;
 };
 
-// Gram pass out = A^T A x (the CG kernels add lam x).
-void gram(const CgBufs& b, const float* x, float* out, cudaStream_t s) {
-  op_apply(b.A, false, 1.f, x, b.t, false, b.ws, s);
-  op_apply(b.A, true, 1.f, b.t, out, false, b.ws, s);
+// Gram pass out = A^T A x (the CG kernels add lam x).  Folded: the other
+// blocks only; acc: added onto out (the CG step's q starts at (lam + gd) p).
+void gram(const CgBufs& b, const float* x, float* out, bool acc, cudaStream_t s) {
+  op_apply(b.A, false, 1.f, x, b.t, false, b.ws, s, false, b.skip);
+  op_apply(b.A, true, 1.f, b.t, out, acc, b.ws, s, false, b.skip);
 }
 
 // CG start at z with gz = G z already known (fresh = 0) or computed here
 // from scratch (fresh = 1).
 void emit_cg_start(const CgBufs& b, int mode, int fresh, const Conds& cd, cudaStream_t s) {
-  if (fresh) gram(b, b.z, b.gz, s);
+  if (fresh) gram(b, b.z, b.gz, false, s);
   k_cg_init<<<red_grid(b.n), kThreads, 0, s>>>(b.ctl, b.n, b.rhs, b.z, b.gz, b.r, b.p, b.part, mode, fresh,
-                                               cd.cg, cd.in_graph);
+                                               cd.cg, cd.in_graph, b.fold.gd, b.q);
 }
 
 // One CG step (body of the CG WHILE node).
 void emit_cg_step(const CgBufs& b, int mode, const Conds& cd, cudaStream_t s) {
-  gram(b, b.p, b.q, s);
-  k_cg_dot<<<red_grid(b.n), kThreads, 0, s>>>(b.ctl, b.n, b.p, b.q, b.part);
+  const bool folded = b.fold.nb > 0;
+  gram(b, b.p, b.q, folded, s);
+  k_cg_dot<<<red_grid(b.n), kThreads, 0, s>>>(b.ctl, b.n, b.p, b.q, b.part, folded ? 1 : 0);
   k_cg_update<<<red_grid(b.n), kThreads, 0, s>>>(b.ctl, b.n, b.m, b.z, b.r, b.p, b.q, b.gz, b.az, b.t,
-                                                 b.part, mode);
-  k_cg_p<<<grid_for(b.n), kThreads, 0, s>>>(b.ctl, b.n, b.r, b.p, mode, cd.cg, cd.in_graph);
+                                                 b.part, mode, b.fold);
+  k_cg_p<<<grid_for(b.n), kThreads, 0, s>>>(b.ctl, b.n, b.r, b.p, mode, cd.cg, cd.in_graph, b.fold.gd, b.q);
 }
 
 // CG buffers on z; the ADMM iterations' CG steps apply the inner operator
-// when one is set (the setup's always apply A).
+// when one is set (the setup's always apply A).  The folded blocks belong to
+// A, so they apply whenever A does.
 CgBufs cg_bufs(cf_problem* P, float* z, bool iter = false) {
   const cf_op* A = iter && P->inner ? P->inner : P->A;
-  return CgBufs{P->ctl, A, P->n, P->m, z, P->rhs, P->r, P->p, P->qv, P->t, P->ws, P->gz, P->az, P->part};
+  CgBufs b{P->ctl, A, P->n, P->m, z, P->rhs, P->r, P->p, P->qv, P->t, P->ws, P->gz, P->az, P->part};
+  if (A == P->A && P->fold.nb > 0) {
+    b.fold = P->fold;
+    b.skip = P->fold_skip.data();
+  }
+  return b;
 }
 
 // ---- the pieces of the setup and of one ADMM iteration
@@ -872,16 +1021,17 @@ void emit_init(cf_problem* P, cudaStream_t s) {
 // w = u + v; rhs = w_x - A^T w_y; CG start at the previous z_x
 void emit_pre_cg(cf_problem* P, const Conds& cd, cudaStream_t s) {
   const int64_t n = P->n, m = P->m;
-  k_rhs<<<grid_for(std::max(n, m)), kThreads, 0, s>>>(P->ctl, n, m, P->ux, P->uy, P->vs, P->wy, P->rhs);
-  op_apply(P->A, true, -1.f, P->wy, P->rhs, true, P->ws, s);
-  emit_cg_start(cg_bufs(P, P->zx), CG_ITER, 0, cd, s);
+  k_rhs<<<grid_for(std::max(n, m)), kThreads, 0, s>>>(P->ctl, n, m, P->ux, P->uy, P->vs, P->wy, P->rhs,
+                                                       P->fold);
+  op_apply(P->A, true, -1.f, P->wy, P->rhs, true, P->ws, s, false, P->fold.nb ? P->fold_skip.data() : nullptr);
+  emit_cg_start(cg_bufs(P, P->zx, true), CG_ITER, 0, cd, s);
 }
 
 // subspace step, projection, dual update
 void emit_post_cg(cf_problem* P, const Conds& cd, cudaStream_t s) {
   const int64_t n = P->n, m = P->m;
   k_utau<<<red_grid(std::max(n, m)), kThreads, 0, s>>>(P->ctl, n, m, P->zx, P->az, P->zy, P->wy, P->bf, P->cf,
-                                                       P->part);
+                                                       P->part, P->fold);
   if (P->nchunk > 0)
     k_soc_norm<<<(unsigned)P->nchunk, kThreads, 0, s>>>(P->ctl, P->chunk_seg, P->chunk_r0, P->chunk_r1,
                                                         P->seg_head, P->seg_c0, P->seg_nc, P->zy, P->gy,
@@ -1077,8 +1227,8 @@ size_t problem_state_bytes(const cf_problem* P) {
   auto d = [](size_t k) { return align_up(k * sizeof(double), 256); };
   size_t wsf = solver_ws_floats(P);
   size_t b = 0;
-  b += 9 * f(n);            // ux zx rhs r p q gx cn gz
-  b += 8 * f(m);            // uy vs wy t zy gy cm az
+  b += 10 * f(n);           // ux zx rhs r p q gx cn gz, fold_gd
+  b += 9 * f(m);            // uy vs wy t zy gy cm az, fold_s
   b += f(wsf);
   b += f(std::max<size_t>(team::scratch_floats(P), 1));
   b += d((size_t)kMaxRedBlocks * kRedSlots);
@@ -1109,6 +1259,7 @@ cf_err ensure_state(cf_problem* P) {
   P->uy = takef(m); P->vs = takef(m); P->wy = takef(m); P->t = takef(m);
   P->zy = takef(m); P->gy = takef(m); P->cm = takef(m);
   P->gz = takef(n); P->az = takef(m);
+  P->fold_gd = takef(n); P->fold_s = takef(m);
   P->ws = takef(solver_ws_floats(P));
   P->team_scratch = takef(std::max<size_t>(team::scratch_floats(P), 1));
   P->part = taked((size_t)kMaxRedBlocks * kRedSlots);
@@ -1121,6 +1272,33 @@ cf_err ensure_state(cf_problem* P) {
   P->out_dev = taked(n + 2 * m);
   P->ctl = (Ctl*)cur;
   CF_CUDA(cudaMemsetAsync(P->ctl, 0, sizeof(Ctl), P->stream));
+  // diagonal row blocks folded out of the graph engine's CG passes (not with
+  // an inner operator: its CG steps carry A z from the inner copy); t is
+  // zeroed so that the rows the folded passes never write stay zero
+  CF_CUDA(cudaMemsetAsync(P->t, 0, m * sizeof(float), P->stream));
+  P->fold = Fold{};
+  P->fold_skip.clear();
+  std::vector<DiagBlock> blocks;
+  if (!P->inner && fold_diag_blocks(P->A, &blocks, &P->fold_skip)) {
+    Fold f;
+    FoldSrc src{};
+    f.nb = (int)blocks.size();
+    for (int b = 0; b < f.nb; ++b) {
+      f.r0[b] = blocks[b].r0;
+      f.c0[b] = blocks[b].c0;
+      f.len[b] = blocks[b].len;
+      src.alpha[b] = blocks[b].alpha;
+      src.d[b] = blocks[b].d;
+    }
+    f.s = P->fold_s;
+    f.gd = P->fold_gd;
+    k_fold_prep<<<grid_for(std::max(n, m)), kThreads, 0, P->stream>>>(f, src, (int64_t)m, (int64_t)n, P->eq_d,
+                                                                       P->eq_e, P->fold_s, P->fold_gd);
+    CF_CUDA(cudaGetLastError());
+    P->fold = f;
+  } else {
+    P->fold_skip.clear();
+  }
   CF_CUDA(cudaMemsetAsync(P->seg_cnt, 0, sizeof(double) * std::max<int64_t>(P->nseg, 1), P->stream));
   CF_CUDA(cudaMemsetAsync(P->warm_dev, 0, 2 * N * sizeof(double), P->stream));
   CF_CUDA(cudaStreamSynchronize(P->stream));
@@ -1148,6 +1326,9 @@ void release_state(cf_problem* P) {
   if (P->arena) cudaFree(P->arena);
   P->arena = nullptr;
   P->team_scratch = nullptr;
+  P->fold = Fold{};
+  P->fold_skip.clear();
+  P->fold_s = P->fold_gd = nullptr;
   P->setup_done = false;
 }
 

@@ -38,6 +38,17 @@ struct KernelCounts {
   int top = 0, body = 0, cg = 0, check = 0, refresh = 0;
 };
 
+// Diagonal row blocks folded out of the graph engine's CG passes (see
+// fold_diag_blocks): block b covers rows [r0[b], r0[b] + len[b]) and columns
+// [c0[b], c0[b] + len[b]); s holds the (equilibrated) diagonal on its rows,
+// gd the sum of s^2 over the blocks covering each column.  nb == 0: none.
+struct Fold {
+  int nb = 0;
+  int64_t r0[kMaxFold] = {}, c0[kMaxFold] = {}, len[kMaxFold] = {};
+  const float* s = nullptr;
+  const float* gd = nullptr;
+};
+
 }  // namespace cf
 
 struct cf_problem {
@@ -98,6 +109,11 @@ struct cf_problem {
   // operator kept in inner_orig
   cf_op* inner = nullptr;
   cf_op* inner_orig = nullptr;
+  // graph engine: diagonal row blocks of A folded out of the CG passes
+  // (planned with the state; s and gd live in the state arena)
+  cf::Fold fold;
+  std::vector<uint8_t> fold_skip;
+  float *fold_s = nullptr, *fold_gd = nullptr;
 };
 
 namespace cf {

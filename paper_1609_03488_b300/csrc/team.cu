@@ -30,8 +30,8 @@
 //
 // The grid team (CF_ENGINE_GRID) is the same solve with every CTA of a
 // cooperative launch (one per SM) as one team: barriers are a grid-wide
-// arrive/wait on a global counter and generation word, and the CTAs add
-// their partial sums from global memory.  The cooperative launch makes the
+// arrive/wait on a global arrival counter, and the CTAs add their partial
+// sums from global memory.  The cooperative launch makes the
 // runtime check that every CTA is resident, so every barrier completes; each
 // wait is still bounded (kGridSpinLimit polls), after which the CTA raises an
 // abort flag, every later barrier returns at once, the loops end, and the
@@ -77,13 +77,12 @@ static_assert(sizeof(Prob) % 16 == 0, "Prob is copied as 16-byte words");
 
 // Barrier words of a grid team (zeroed before each launch).
 struct GridBar {
-  unsigned int arrive;  // CTAs arrived at the current barrier
-  unsigned int gen;     // barriers completed
-  int abort;            // a wait gave up: every later barrier returns at once
+  unsigned long long count;  // arrivals since the launch: barrier b completes at C (b + 1)
+  int abort;                 // a wait gave up: every later barrier returns at once
   int pad;
 };
 
-constexpr unsigned int kGridSpinLimit = 1u << 22;  // polls (~0.2 us apart) before a wait gives up
+constexpr unsigned int kGridSpinLimit = 1u << 22;  // polls (~0.5 us apart) before a wait gives up
 
 struct Team {
   int C;     // CTAs in the team (1: this CTA alone)
@@ -119,42 +118,34 @@ struct __align__(16) Shared {
   int item;            // work-queue slot taken by the team's rank 0
 };
 
-__device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int* p) {
-  unsigned int v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+__device__ __forceinline__ unsigned long long ld_acquire_gpu(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
-}
-__device__ __forceinline__ void st_release_gpu(unsigned int* p, unsigned int v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 // Grid-wide barrier of a grid team: every write of any CTA before it is
-// visible to every CTA after it.  Thread 0 arrives on the counter (the last
-// to arrive resets it and releases the next generation) and polls the
-// generation word, at most kGridSpinLimit times.
+// visible to every CTA after it.  Thread 0 of each CTA publishes the CTA's
+// writes (the CTA barrier, then a fence) and adds one to the arrival count;
+// the barrier its arrival belongs to completes when the count reaches the
+// next multiple of C, which it polls with acquire loads, at most spin_limit
+// times.  One atomic and the polls: no reset, no second word.
 __device__ __noinline__ void grid_sync(const Team& tm) {
   __syncthreads();
   if (threadIdx.x == 0) {
     GridBar* g = tm.gb;
     if (!*(volatile int*)&g->abort) {
-      const unsigned int gen = ld_acquire_gpu(&g->gen);
       __threadfence();
-      const unsigned int prev = atomicAdd(&g->arrive, 1u);
-      if (prev == (unsigned)tm.C - 1u) {
-        g->arrive = 0u;
-        __threadfence();
-        st_release_gpu(&g->gen, gen + 1u);
-      } else {
-        unsigned int k = 0;
-        while (ld_acquire_gpu(&g->gen) == gen) {
-          if (++k > tm.spin_limit || *(volatile int*)&g->abort) {
-            atomicExch(&g->abort, 1);
-            break;
-          }
-          __nanosleep(64);
+      const unsigned long long C = (unsigned long long)tm.C;
+      const unsigned long long target = (atomicAdd(&g->count, 1ull) / C + 1ull) * C;
+      unsigned int k = 0;
+      while (ld_acquire_gpu(&g->count) < target) {
+        if (++k > tm.spin_limit || ((k & 255u) == 0u && *(volatile int*)&g->abort)) {
+          atomicExch(&g->abort, 1);
+          break;
         }
+        if (k > 32u) __nanosleep(32);
       }
-      __threadfence();
     }
   }
   __syncthreads();
@@ -611,28 +602,29 @@ __device__ void term_conv(const Team& tm, const Term& t, const float* x, float* 
   }
 }
 
-// The 1-D convolution by overlap-save FFTs (fftconv.cuh): each 256 threads of
-// a CTA take pairs of segments in turn (pair g + groups x rank, + groups x C),
-// with a transform buffer of their own in the CTA's shared memory and a
+// The 1-D convolution by overlap-save FFTs (fftconv.cuh): each N/16 threads
+// of a CTA take pairs of segments in turn (pair g + groups x rank, + groups x
+// C), with a transform buffer of their own in the CTA's shared memory and a
 // named barrier of their own.  The input was written by other CTAs before a
 // team barrier, so it is read through L2 (no read-only path).
-__device__ __forceinline__ void group_bar(int id) {
-  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(256) : "memory");
+__device__ __forceinline__ void group_bar(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
-template <bool SC>
+template <int N, bool SC>
 __device__ __noinline__ void term_fft(const Team& tm, const Term& t, const float* x, float* y, float* dsm) {
-  const int ng = blockDim.x >> 8, g = threadIdx.x >> 8, tl = threadIdx.x & 255;
+  constexpr int T = N / 16;
+  const int ng = blockDim.x / T, g = threadIdx.x / T, tl = threadIdx.x % T;
   const int Lp = (int)t.Lp;
-  const int64_t V = fftc::kN - Lp + 1;
+  const int64_t V = N - Lp + 1;
   const int64_t npairs = (t.rows + 2 * V - 1) / (2 * V);
   const int64_t D = Lp - 1 - t.shift;
-  float2* buf = reinterpret_cast<float2*>(dsm) + (size_t)g * fftc::kBufF2;
+  float2* buf = reinterpret_cast<float2*>(dsm) + (size_t)g * fftc::buf_f2<N>();
   __syncthreads();  // earlier users of the shared buffer are done
   for (int64_t pr = (int64_t)tm.rank * ng + g; pr < npairs; pr += (int64_t)tm.C * ng)
-    fftc::pair<SC, false, false>(tl, pr, t.rows, t.cols, Lp, D, static_cast<const float2*>(t.a), t.tw, t.alpha,
-                                 x + t.xo, y + t.yo, t.acc != 0, t.sin, t.sout, buf, nullptr, nullptr,
-                                 [g] { group_bar(1 + g); });
+    fftc::pair<N, SC, false, false>(tl, pr, t.rows, t.cols, Lp, D, static_cast<const float2*>(t.a), t.tw, t.alpha,
+                                    x + t.xo, y + t.yo, t.acc != 0, t.sin, t.sout, buf, nullptr, nullptr,
+                                    [g] { group_bar(1 + g, T); });
 }
 
 // y = the flattened operator applied to x (terms in order).  Compiled once
@@ -679,10 +671,17 @@ __device__ __noinline__ void apply(const Team& tm, const Term* terms, int nt, co
         term_conv(tm, t, x, y, dsm);
         break;
       case T_FFT:
-        if (t.sin)
-          term_fft<true>(tm, t, x, y, dsm);
-        else
-          term_fft<false>(tm, t, x, y, dsm);
+        if (t.fftn == 2048) {
+          if (t.sin)
+            term_fft<2048, true>(tm, t, x, y, dsm);
+          else
+            term_fft<2048, false>(tm, t, x, y, dsm);
+        } else {
+          if (t.sin)
+            term_fft<4096, true>(tm, t, x, y, dsm);
+          else
+            term_fft<4096, false>(tm, t, x, y, dsm);
+        }
         break;
     }
   }
@@ -1320,6 +1319,7 @@ bool flatten(const cf_op* op, bool trans, float alpha, int64_t xo, int64_t yo, b
         t.shift = trans ? op->Lp - 1 : 0;
         t.a = trans ? op->fft_ha : op->fft_hf;
         t.tw = op->fft_tw;
+        t.fftn = op->fft_n;
         out.push_back(t);
         return true;
       }
@@ -1706,7 +1706,7 @@ void build_table(const std::vector<cf_problem*>& probs, const cf_schedule& s, bo
     fill_prob(P, s, do_setup, tune, &ents[i]);
     (is_big(P, s) ? big : small).push_back((int32_t)i);
     smem = std::max(smem, (size_t)P->plan.smem_floats * sizeof(float));
-    if (P->plan.has_fft) smem = std::max(smem, (size_t)(s.threads / 256) * fftc::kBufF2 * sizeof(float2));
+    if (P->plan.has_fft) smem = std::max(smem, (size_t)s.threads * 17 * sizeof(float2));  // (N + N/16) float2 per N/16 threads
   }
   auto longer = [&](int32_t a, int32_t b) {
     const double wa = probs[a]->plan.pass_bytes, wb = probs[b]->plan.pass_bytes;
@@ -1804,7 +1804,7 @@ cf_err grid_launch(cf_problem* P, const cf_settings* st, const double* warm_uv, 
   s.ctas_per_sm = 1;
   const int C = P->ctx->sm_count;  // one CTA per SM
   size_t smem = (size_t)P->plan.smem_floats * sizeof(float);
-  if (P->plan.has_fft) smem = std::max(smem, (size_t)(kGridThreads / 256) * fftc::kBufF2 * sizeof(float2));
+  if (P->plan.has_fft) smem = std::max(smem, (size_t)kGridThreads * 17 * sizeof(float2));
   auto kern = k_team_grid<kGridThreads, 1>;
   if (smem > 48 * 1024) CF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;

@@ -29,7 +29,7 @@ struct __align__(16) Term {
   int32_t kind, acc, sync, prec;
   int64_t xo, yo, rows, cols;
   float alpha;
-  int32_t pad0;
+  int32_t fftn;           // FFT convolution: transform size (4096 or 2048)
   const void* a;          // dense / CSR values, reversed conv taps, diagonal (may be null)
   const float* scale;     // per-row scales of an FP8 dense leaf
   const int32_t* rowptr;  // CSR (for the adjoint: the stored transpose)

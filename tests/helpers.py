@@ -56,11 +56,13 @@ def objective_rel_err(p, p_star):
     return abs(p - p_star) / (1.0 + abs(p_star))
 
 
-def fp32_fft_trajectory(prob, k_max, **solve_kw):
+def fp32_conv_trajectory(prob, k_max, method="fft", **solve_kw):
     """The oracle's trajectory with every 1-D convolution of the iterations
-    evaluated by a float32 FFT (scipy's single-precision transform, not this
-    library's), the equilibration kept exact: how far float32 FFT rounding
-    alone moves the iterates.  Returns (exact, perturbed) oracle results."""
+    evaluated in float32 -- by scipy's single-precision FFT (method "fft") or
+    by a sequential float32 direct sum over the taps ("direct"), neither of
+    them this library's -- the equilibration kept exact: how far float32
+    rounding of the operator alone moves the iterates.  Returns (exact,
+    perturbed) oracle results."""
     import scipy.fft as sfft
 
     from oracle import equil, linop, scs
@@ -72,21 +74,32 @@ def fp32_fft_trajectory(prob, k_max, **solve_kw):
     exact = scs.solve(prob["A"], prob["b"], prob["c"], prob["cone"], equil=eq, **kw)
     plain = linop.apply
 
-    def fft32(op, x, adjoint=False):
+    def conv32(op, x, adjoint=False):
         if op["kind"] != "conv1d":
             return plain(op, x, adjoint)
         k = np.asarray(op["kernel"], dtype=np.float32)
         v = np.asarray(x, dtype=np.float32)
         L = k.size
+        if method == "fft":
+            if not adjoint:
+                m = v.size + L - 1
+                nf = sfft.next_fast_len(m)
+                return sfft.irfft(sfft.rfft(v, nf) * sfft.rfft(k, nf), nf)[:m].astype(np.float64)
+            n = v.size - L + 1
+            nf = sfft.next_fast_len(v.size)
+            return sfft.irfft(sfft.rfft(v, nf) * np.conj(sfft.rfft(k, nf)), nf)[:n].astype(np.float64)
         if not adjoint:
-            m = v.size + L - 1
-            nf = sfft.next_fast_len(m)
-            return sfft.irfft(sfft.rfft(v, nf) * sfft.rfft(k, nf), nf)[:m].astype(np.float64)
+            out = np.zeros(v.size + L - 1, dtype=np.float32)
+            for j in range(L):
+                out[j:j + v.size] += k[j] * v
+            return out.astype(np.float64)
         n = v.size - L + 1
-        nf = sfft.next_fast_len(v.size)
-        return sfft.irfft(sfft.rfft(v, nf) * np.conj(sfft.rfft(k, nf)), nf)[:n].astype(np.float64)
+        out = np.zeros(n, dtype=np.float32)
+        for j in range(L):
+            out += k[j] * v[j:j + n]
+        return out.astype(np.float64)
 
-    linop.apply = fft32
+    linop.apply = conv32
     try:
         pert = scs.solve(prob["A"], prob["b"], prob["c"], prob["cone"], equil=eq, **kw)
     finally:

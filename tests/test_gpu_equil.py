@@ -18,7 +18,7 @@ import scipy.optimize as so
 
 from oracle import cones, equil, linop, scs
 from paper_1609_03488_b300 import synth
-from tests.helpers import fp32_fft_trajectory, fp64_residuals, objective_rel_err, rel
+from tests.helpers import fp32_conv_trajectory, fp64_residuals, objective_rel_err, rel
 
 pytestmark = pytest.mark.gpu
 ENGINES = ["graph", "team", "grid"]
@@ -75,18 +75,20 @@ def test_scalings_match_oracle(B, ctx, family):
         assert np.all(D[lo:hi] == D[lo])
 
 
-_FFT_BAR = {}
+_CONV_BAR = {}
 
 
-def _fft_bar(family, prob):
-    """Per-iterate bar of an FFT-evaluated family: the larger of 1e-5 and
-    twice how far float32 FFT rounding alone (scipy's single-precision FFT in
-    the FP64 oracle) moves that iterate (tests/test_fft_rounding.py)."""
-    if family not in _FFT_BAR:
-        exact, pert = fp32_fft_trajectory(prob, 20, equilibrate=EQ)
-        _FFT_BAR[family] = [max(1e-5, 2 * rel(pert["traj_u"][k], exact["traj_u"][k]),
-                                2 * rel(pert["traj_v"][k], exact["traj_v"][k])) for k in range(20)]
-    return _FFT_BAR[family]
+def _conv_bar(family, prob):
+    """Per-iterate bar of a wide-kernel family: the larger of 1e-5 and twice
+    how far float32 rounding of the convolution alone (scipy's
+    single-precision FFT, or a float32 direct sum, in the FP64 oracle) moves
+    that iterate (tests/test_conv_rounding.py)."""
+    if family not in _CONV_BAR:
+        method = "direct" if "direct" in family else "fft"
+        exact, pert = fp32_conv_trajectory(prob, 20, method, equilibrate=EQ)
+        _CONV_BAR[family] = [max(1e-5, 2 * rel(pert["traj_u"][k], exact["traj_u"][k]),
+                                 2 * rel(pert["traj_v"][k], exact["traj_v"][k])) for k in range(20)]
+    return _CONV_BAR[family]
 
 
 @pytest.mark.parametrize("engine", ENGINES)
@@ -95,7 +97,7 @@ def test_equilibrated_trajectory_matches_oracle(B, ctx, family, engine):
     prob = FAMILIES[family]()
     ref = scs.problem_solve(prob, max_iters=20, check_interval=10 ** 6, linsys="cg", cg_fixed_steps=3,
                             trajectory=20, equilibrate=EQ)
-    bar = _fft_bar(family, prob) if family.startswith("deconv_fft") else [1e-5] * 20
+    bar = _conv_bar(family, prob) if family.startswith(("deconv_fft", "deconv_direct")) else [1e-5] * 20
     P = _eq_problem(B, ctx, prob)
     N = prob["A"]["n"] + prob["A"]["m"] + 1
     for k in (1, 5, 20):

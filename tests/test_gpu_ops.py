@@ -91,10 +91,15 @@ def _check_fft(B, ctx, k, n, method="fft", seed=0, what=""):
     return op, x, y
 
 
-# one output, a single pair, ragged tails around the 2V-output pairs
-# (V = 4097 - Lp), the largest kernel (2048 taps, V = 2049), tiny kernels
+# one output, a single pair, ragged tails around the 2V-output pairs (V =
+# N + 1 - Lp: 4096-point transforms for kernels over 1024 padded taps or
+# outputs enough to fill the GPU, else 2048-point), the largest kernel (2048
+# taps, V = 2049), the largest 2048-point kernel (1024 taps, V = 1025) and the
+# next, tiny kernels, and 2e6 outputs on 4096-point transforms
 @pytest.mark.parametrize("n,L", [(1, 1000), (5, 16), (1000, 100), (3000, 1000), (6177, 1000), (6178, 1000),
-                                 (20000, 2048), (70001, 1000), (4099, 257), (100, 3)])
+                                 (20000, 2048), (70001, 1000), (4099, 257), (100, 3),
+                                 (1083, 1000), (1084, 1000), (2082, 1000), (5000, 1024), (5000, 1025),
+                                 (2_000_000, 1000)])
 def test_conv1d_fft(B, ctx, n, L):
     rng = np.random.default_rng(7 * n + L)
     k = rng.standard_normal(L).astype(np.float32)
@@ -235,6 +240,15 @@ def test_kron(B, ctx):
     tree = synth.kron(synth.dense(A), synth.dense(Bm))
     # two chained float32 products: k = 4 + 5 terms bounds each output
     _check(B, ctx, tree, 4 * 5 + 9, 7 * 6 + 13, what="kron")
+    # the named entry point is the same operator, bit for bit
+    op1 = B.build_operator(ctx, tree)
+    op2 = B.cf_op_kron(ctx, B.cf_op_dense(ctx, A), B.cf_op_dense(ctx, Bm))
+    x = rng.standard_normal(20).astype(np.float32)
+    y = rng.standard_normal(42).astype(np.float32)
+    np.testing.assert_array_equal(op1.apply(x), op2.apply(x))
+    np.testing.assert_array_equal(op1.apply(y, adjoint=True), op2.apply(y, adjoint=True))
+    with pytest.raises(B.CfError):
+        B.cf_op_kron(ctx, B.cf_op_dense(ctx, A), B.cf_op_diag(ctx, 4))
 
 
 def test_random_composition_tree(B, ctx):
