@@ -232,6 +232,9 @@ size_t gemv_t_ws_floats(int64_t m, int64_t n, int64_t lda);
 void launch_gemv_t(cudaStream_t s, cf_prec p, int64_t m, int64_t n, int64_t lda, const void* A,
                    const float* rs, float alpha, const float* x, float* y, bool acc, float* ws,
                    const float* sin = nullptr, const float* sout = nullptr);
+// Resident-grid sizes of the CSR kernels, queried once per process before the
+// first launch (at operator creation, not during stream capture).
+void csr_prepare();
 void launch_csr(cudaStream_t s, cf_prec p, int64_t m, int64_t nnz, const int32_t* rowptr, const int32_t* col,
                 const void* val, float alpha, const float* x, float* y, bool acc,
                 const float* sin = nullptr, const float* sout = nullptr);

@@ -277,25 +277,38 @@ void launch_conv2d(cudaStream_t s, int64_t Ho, int64_t Wo, int64_t Hi, int64_t W
 
 // ------------------------------------------------------------ dense GEMV
 
-// y[i] = alpha * s_i * sum_j A[i, j] x[j]: a warp handles RW rows, so each
-// slice of x it loads is reused RW times; the RW operand loads are issued
-// before any of them is used.
+// y[i] = alpha * s_i * sum_j A[i, j] x[j]: a CTA handles RW consecutive
+// rows and all its threads sweep the columns together, each thread taking
+// the V columns of one 16-byte load, so that the CTA reads THREADS x 16
+// contiguous bytes of each of its rows at once (long DRAM bursts) and each
+// slice of x a thread loads serves RW rows.  The per-thread sums of a row
+// are added by a warp tree and then across warps in warp order.
 // SC: x is read as sin * x and the rows are multiplied by sout.
-template <typename T, int RW, bool SC>
-__global__ void __launch_bounds__(256)
+constexpr int kGemvNRows = 8;
+
+template <typename T, int THREADS, bool SC>
+__global__ void __launch_bounds__(THREADS)
 k_gemv_n(int64_t m, int64_t n, int64_t lda, const T* __restrict__ A, const float* __restrict__ rs,
          float alpha, const float* __restrict__ x, float* __restrict__ y, bool acc,
          const float* __restrict__ sin, const float* __restrict__ sout) {
   constexpr int V = Vec<T>::N;
-  const int lane = threadIdx.x & 31;
-  const int64_t row0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * RW;
-  if (row0 >= m) return;
+  constexpr int RW = kGemvNRows;
+  constexpr int NW = THREADS / 32;
+  __shared__ float red[NW][RW];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t row0 = (int64_t)blockIdx.x * RW;
   const bool xal = ((reinterpret_cast<uintptr_t>(x) & 15) == 0) &&
                    (!SC || ((reinterpret_cast<uintptr_t>(sin) & 15) == 0));
+  const T* arow[RW];
+#pragma unroll
+  for (int r = 0; r < RW; ++r) arow[r] = A + (row0 + r < m ? row0 + r : m - 1) * lda;  // rows past m: not stored
   float accv[RW];
 #pragma unroll
   for (int r = 0; r < RW; ++r) accv[r] = 0.f;
-  for (int64_t c = (int64_t)lane * V; c < n; c += 32 * V) {
+  for (int64_t c = (int64_t)threadIdx.x * V; c < n; c += (int64_t)THREADS * V) {
+    uint4 u[RW];
+#pragma unroll
+    for (int r = 0; r < RW; ++r) u[r] = __ldg(reinterpret_cast<const uint4*>(arow[r] + c));
     float xv[V];
     if (xal && c + V <= n) {
 #pragma unroll
@@ -312,12 +325,6 @@ k_gemv_n(int64_t m, int64_t n, int64_t lda, const T* __restrict__ A, const float
       for (int q = 0; q < V; ++q)
         xv[q] = (c + q < n) ? (SC ? __ldg(sin + c + q) * __ldg(x + c + q) : __ldg(x + c + q)) : 0.f;
     }
-    uint4 u[RW];
-#pragma unroll
-    for (int r = 0; r < RW; ++r) {
-      const int64_t row = row0 + r < m ? row0 + r : m - 1;   // clamp: rows past m are not stored
-      u[r] = __ldg(reinterpret_cast<const uint4*>(A + row * lda + c));
-    }
 #pragma unroll
     for (int r = 0; r < RW; ++r) {
       float av[V];
@@ -331,8 +338,16 @@ k_gemv_n(int64_t m, int64_t n, int64_t lda, const T* __restrict__ A, const float
     float v = accv[r];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    int64_t row = row0 + r;
-    if (lane == 0 && row < m) {
+    if (lane == 0) red[wid][r] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < RW) {
+    const int r = threadIdx.x;
+    const int64_t row = row0 + r;
+    if (row < m) {
+      float v = 0.f;
+#pragma unroll
+      for (int w = 0; w < NW; ++w) v += red[w][r];
       float out = (SC ? alpha * sout[row] : alpha) * (rs ? rs[row] * v : v);
       y[row] = acc ? y[row] + out : out;
     }
@@ -342,12 +357,13 @@ k_gemv_n(int64_t m, int64_t n, int64_t lda, const T* __restrict__ A, const float
 template <typename T>
 static void gemv_n_typed(cudaStream_t s, int64_t m, int64_t n, int64_t lda, const void* A, const float* rs,
                          float alpha, const float* x, float* y, bool acc, const float* sin, const float* sout) {
-  constexpr int RW = 4;
-  const unsigned grid = (unsigned)((m + 8 * RW - 1) / (8 * RW));
+  // 2048 columns a sweep for the 1- and 2-byte types, 1024 for float32
+  constexpr int TH = sizeof(T) == 1 ? 128 : 256;
+  const unsigned grid = (unsigned)((m + kGemvNRows - 1) / kGemvNRows);
   if (sin || sout)
-    k_gemv_n<T, RW, true><<<grid, 256, 0, s>>>(m, n, lda, (const T*)A, rs, alpha, x, y, acc, sin, sout);
+    k_gemv_n<T, TH, true><<<grid, TH, 0, s>>>(m, n, lda, (const T*)A, rs, alpha, x, y, acc, sin, sout);
   else
-    k_gemv_n<T, RW, false><<<grid, 256, 0, s>>>(m, n, lda, (const T*)A, rs, alpha, x, y, acc, nullptr, nullptr);
+    k_gemv_n<T, TH, false><<<grid, TH, 0, s>>>(m, n, lda, (const T*)A, rs, alpha, x, y, acc, nullptr, nullptr);
 }
 
 void launch_gemv_n(cudaStream_t s, cf_prec p, int64_t m, int64_t n, int64_t lda, const void* A,
@@ -364,73 +380,120 @@ void launch_gemv_n(cudaStream_t s, cf_prec p, int64_t m, int64_t n, int64_t lda,
 
 // x^T-side: part[rb, j] = sum_{i in row block rb} A[i, j] (s_i y_i); each
 // thread owns the V columns of one 16-byte load, so every row is read once
-// with coalesced loads; a CTA covers kGemvTCols columns whatever the storage
-// type (256 / 128 / 64 threads for FP32 / BF16 / FP8), and the row blocks are
-// sized for about 8 CTAs per SM.  A second kernel sums the row blocks in a
-// fixed order.
+// with coalesced loads.  A CTA of 256 threads covers kGemvTCols columns
+// whatever the storage type: 256 / 128 / 64 threads span the columns for
+// FP32 / BF16 / FP8, and the narrower types split the block's rows over
+// RG = 1 / 2 / 4 row groups (rows r0 + g, r0 + g + RG, ...) whose sums are
+// added in group order through shared memory.  A thread has kGemvTUnroll
+// rows' loads in flight; the row blocks are sized for about 8 CTAs per SM.
+// A second kernel sums the row blocks in a fixed order.
 constexpr int kGemvTCols = 1024;
 constexpr int kGemvTMaxRows = 512;
 constexpr int kGemvTUnroll = 8;
+constexpr int kGemvTThreads = 256;
 
 template <typename T>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kGemvTThreads)
 k_gemv_t_part(int64_t m, int64_t n, int64_t lda, int64_t rows_per_block, const T* __restrict__ A,
               const float* __restrict__ rs, const float* __restrict__ yv, float* __restrict__ part,
               const float* __restrict__ sin) {
   constexpr int V = Vec<T>::N;
+  constexpr int CT = kGemvTCols / V;      // threads across the columns
+  constexpr int RG = kGemvTThreads / CT;  // row groups
   __shared__ float sy[kGemvTMaxRows];
+  __shared__ float red[RG > 1 ? RG - 1 : 1][RG > 1 ? kGemvTCols : 1];
   const int64_t r0 = (int64_t)blockIdx.y * rows_per_block;
   const int64_t r1 = (r0 + rows_per_block < m) ? r0 + rows_per_block : m;
   for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x)
     sy[i - r0] = (rs ? rs[i] * yv[i] : yv[i]) * (sin ? sin[i] : 1.f);
   __syncthreads();
-  const int64_t c0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * V;
-  if (c0 >= n) return;
+  const int ct = threadIdx.x % CT, g = threadIdx.x / CT;
+  const int64_t c0 = ((int64_t)blockIdx.x * CT + ct) * V;
+  const bool live = c0 < n;
   float accv[V];
 #pragma unroll
   for (int q = 0; q < V; ++q) accv[q] = 0.f;
-  int64_t i = r0;
-  for (; i + kGemvTUnroll <= r1; i += kGemvTUnroll) {
-    uint4 u[kGemvTUnroll];
+  if (live) {
+    int64_t i = r0 + g;
+    for (; i + (int64_t)(kGemvTUnroll - 1) * RG < r1; i += (int64_t)kGemvTUnroll * RG) {
+      uint4 u[kGemvTUnroll];
 #pragma unroll
-    for (int k = 0; k < kGemvTUnroll; ++k) u[k] = __ldg(reinterpret_cast<const uint4*>(A + (i + k) * lda + c0));
+      for (int k = 0; k < kGemvTUnroll; ++k)
+        u[k] = __ldg(reinterpret_cast<const uint4*>(A + (i + (int64_t)k * RG) * lda + c0));
 #pragma unroll
-    for (int k = 0; k < kGemvTUnroll; ++k) {
+      for (int k = 0; k < kGemvTUnroll; ++k) {
+        float av[V];
+        Vec<T>::unpack(u[k], av);
+        const float sv = sy[i + (int64_t)k * RG - r0];
+#pragma unroll
+        for (int q = 0; q < V; ++q) accv[q] = fmaf(av[q], sv, accv[q]);
+      }
+    }
+    for (; i < r1; i += RG) {
+      uint4 u = __ldg(reinterpret_cast<const uint4*>(A + i * lda + c0));
       float av[V];
-      Vec<T>::unpack(u[k], av);
-      const float sv = sy[i + k - r0];
+      Vec<T>::unpack(u, av);
+      const float sv = sy[i - r0];
 #pragma unroll
       for (int q = 0; q < V; ++q) accv[q] = fmaf(av[q], sv, accv[q]);
     }
   }
-  for (; i < r1; ++i) {
-    uint4 u = __ldg(reinterpret_cast<const uint4*>(A + i * lda + c0));
-    float av[V];
-    Vec<T>::unpack(u, av);
-    const float sv = sy[i - r0];
+  if (RG > 1) {
+    if (g > 0) {
 #pragma unroll
-    for (int q = 0; q < V; ++q) accv[q] = fmaf(av[q], sv, accv[q]);
+      for (int q = 0; q < V; ++q) red[g - 1][ct * V + q] = accv[q];
+    }
+    __syncthreads();
+    if (g > 0) return;
+#pragma unroll
+    for (int h = 0; h < RG - 1; ++h)
+#pragma unroll
+      for (int q = 0; q < V; ++q) accv[q] += red[h][ct * V + q];
   }
+  if (!live) return;
   float* dst = part + (int64_t)blockIdx.y * lda + c0;
 #pragma unroll
   for (int q = 0; q < V; q += 4)
     *reinterpret_cast<float4*>(dst + q) = make_float4(accv[q], accv[q + 1], accv[q + 2], accv[q + 3]);
 }
 
-__global__ void k_gemv_t_reduce(int64_t n, int64_t lda, int nrb, const float* __restrict__ part,
-                                float alpha, float* __restrict__ x, bool acc, const float* __restrict__ sout) {
-  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
-       j += (int64_t)gridDim.x * blockDim.x) {
+// x[j] = alpha sout_j sum_rb part[rb, j]: a CTA takes 32 columns; its 8 warps
+// sum interleaved row blocks (coalesced over the columns) and warp 0 adds
+// the 8 results in warp order, so the sum's order is fixed.
+constexpr int kGemvTRedRows = 8;
+
+__global__ void __launch_bounds__(32 * kGemvTRedRows)
+k_gemv_t_reduce(int64_t n, int64_t lda, int nrb, const float* __restrict__ part, float alpha,
+                float* __restrict__ x, bool acc, const float* __restrict__ sout) {
+  constexpr int R = kGemvTRedRows;
+  __shared__ float sh[R][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int64_t j = (int64_t)blockIdx.x * 32 + tx;
+  float s4[4] = {0.f, 0.f, 0.f, 0.f};
+  if (j < n) {
+    int b = ty;
+    for (; b + 3 * R < nrb; b += 4 * R) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) s4[k] += __ldcg(part + (int64_t)(b + k * R) * lda + j);
+    }
+    for (; b < nrb; b += R) s4[0] += __ldcg(part + (int64_t)b * lda + j);
+  }
+  sh[ty][tx] = (s4[0] + s4[1]) + (s4[2] + s4[3]);
+  __syncthreads();
+  if (ty == 0 && j < n) {
     float sum = 0.f;
-    for (int b = 0; b < nrb; ++b) sum += part[(int64_t)b * lda + j];
-    float v = (sout ? alpha * sout[j] : alpha) * sum;
+#pragma unroll
+    for (int k = 0; k < R; ++k) sum += sh[k][tx];
+    const float v = (sout ? alpha * sout[j] : alpha) * sum;
     x[j] = acc ? x[j] + v : v;
   }
 }
 
-static int gemv_t_row_blocks(int64_t m, int64_t n) {
+// Row blocks for `per_sm` CTAs per SM (the CTAs that fit: 8 / 6 / 4 for
+// FP32 / BF16 / FP8 by registers), rounded down so the grid is one wave.
+static int gemv_t_row_blocks(int64_t m, int64_t n, int per_sm = 8) {
   const int64_t col_tiles = (n + kGemvTCols - 1) / kGemvTCols;
-  const int64_t want = (8 * 148 + col_tiles - 1) / col_tiles;   // about 8 CTAs per SM
+  const int64_t want = std::max<int64_t>(1, (int64_t)per_sm * 148 / col_tiles);
   const int64_t min_rb = (m + kGemvTMaxRows - 1) / kGemvTMaxRows;  // shared-memory cap
   const int64_t max_rb = std::max<int64_t>(1, m / 32);
   const int64_t rb = std::min(want, max_rb);
@@ -449,10 +512,9 @@ void launch_gemv_t(cudaStream_t s, cf_prec p, int64_t m, int64_t n, int64_t lda,
     if (!acc) launch_fill(s, n, 0.f, y);
     return;
   }
-  const int rb = gemv_t_row_blocks(m, n);
+  const int rb = gemv_t_row_blocks(m, n, p == CF_FP32 ? 8 : (p == CF_BF16 ? 6 : 4));  // <= the workspace's
   const int64_t rows_per_block = (m + rb - 1) / rb;
-  const int V = p == CF_FP32 ? 4 : (p == CF_BF16 ? 8 : 16);
-  const int threads = kGemvTCols / V;
+  const int threads = kGemvTThreads;
   dim3 grid((unsigned)((n + kGemvTCols - 1) / kGemvTCols), (unsigned)rb);
   if (p == CF_FP32)
     k_gemv_t_part<float><<<grid, threads, 0, s>>>(m, n, lda, rows_per_block, (const float*)A, rs, x, ws, sin);
@@ -462,7 +524,7 @@ void launch_gemv_t(cudaStream_t s, cf_prec p, int64_t m, int64_t n, int64_t lda,
   else
     k_gemv_t_part<__nv_fp8_e4m3><<<grid, threads, 0, s>>>(m, n, lda, rows_per_block, (const __nv_fp8_e4m3*)A, rs, x,
                                                           ws, sin);
-  k_gemv_t_reduce<<<grid_for(n, 1), kThreads, 0, s>>>(n, lda, rb, ws, alpha, y, acc, sout);
+  k_gemv_t_reduce<<<(unsigned)((n + 31) / 32), 32 * kGemvTRedRows, 0, s>>>(n, lda, rb, ws, alpha, y, acc, sout);
 }
 
 // ------------------------------------------------------------ quantisation
@@ -510,64 +572,145 @@ void launch_quantize(cudaStream_t s, cf_prec p, int64_t m, int64_t n, int64_t ld
 }
 
 // ------------------------------------------------------------ CSR SpMV
-// One warp per row; lanes stride over the row's entries, four strides at a
-// time so that each lane has four independent index -> x gathers in flight.
+// Warps are persistent (the grid is what fits on the GPU at once) and walk
+// rows row, row + W, ... (W warps in the grid).  A row's first 32 U entries
+// are held as U (index, value) pairs a lane; while the warp gathers x for
+// the current row and sums it, the index and value loads of its next row and
+// the row-pointer loads of the row after are already in flight, so a row
+// costs about one memory latency instead of three (row pointers -> entries
+// -> x).  Entries past 32 U in a row (rows far above the average) are taken
+// by a plain strided loop.  U = 16 for matrices that average more than 256
+// entries a row, else 8.
 template <bool BF16>
 __device__ __forceinline__ float csr_val(const void* __restrict__ val, int32_t k) {
   return BF16 ? __bfloat162float(__ldg(((const __nv_bfloat16*)val) + k)) : __ldg(((const float*)val) + k);
 }
 
+template <bool BF16, int U>
+__device__ __forceinline__ void csr_fetch(const int32_t* __restrict__ col, const void* __restrict__ val, int32_t b,
+                                          int32_t e, int lane, int32_t (&c)[U], float (&v)[U]) {
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int32_t k = b + lane + 32 * u;
+    c[u] = k < e ? __ldg(col + k) : -1;
+    v[u] = k < e ? csr_val<BF16>(val, k) : 0.f;
+  }
+}
+
 // SC: input / output scalings (sin, sout) are applied.
-template <bool BF16, bool SC>
+template <bool BF16, bool SC, int U>
 __global__ void __launch_bounds__(256)
 k_csr(int64_t m, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
       const void* __restrict__ val, float alpha, const float* __restrict__ x,
       float* __restrict__ y, bool acc, const float* __restrict__ sin, const float* __restrict__ sout) {
   const int lane = threadIdx.x & 31;
-  const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int64_t W = (int64_t)gridDim.x * (blockDim.x >> 5);
+  int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (row >= m) return;
-  const int32_t b = __ldg(rowptr + row), e = __ldg(rowptr + row + 1);
-  float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-  int32_t k = b + lane;
-  for (; k + 96 < e; k += 128) {
-    const int32_t c0 = __ldg(col + k), c1 = __ldg(col + k + 32), c2 = __ldg(col + k + 64), c3 = __ldg(col + k + 96);
-    const float v0 = csr_val<BF16>(val, k), v1 = csr_val<BF16>(val, k + 32);
-    const float v2 = csr_val<BF16>(val, k + 64), v3 = csr_val<BF16>(val, k + 96);
-    s0 = fmaf(v0, SC ? __ldg(sin + c0) * __ldg(x + c0) : __ldg(x + c0), s0);
-    s1 = fmaf(v1, SC ? __ldg(sin + c1) * __ldg(x + c1) : __ldg(x + c1), s1);
-    s2 = fmaf(v2, SC ? __ldg(sin + c2) * __ldg(x + c2) : __ldg(x + c2), s2);
-    s3 = fmaf(v3, SC ? __ldg(sin + c3) * __ldg(x + c3) : __ldg(x + c3), s3);
-  }
-  for (; k < e; k += 32) {
-    const int32_t c = __ldg(col + k);
-    s0 = fmaf(csr_val<BF16>(val, k), SC ? __ldg(sin + c) * __ldg(x + c) : __ldg(x + c), s0);
-  }
-  float sum = (s0 + s1) + (s2 + s3);
+  auto xin = [&](int32_t j) { return SC ? __ldg(sin + j) * __ldg(x + j) : __ldg(x + j); };
+  int32_t b = __ldg(rowptr + row), e = __ldg(rowptr + row + 1);
+  int32_t c[U];
+  float v[U];
+  csr_fetch<BF16, U>(col, val, b, e, lane, c, v);
+  int32_t b1 = 0, e1 = 0;
+  if (row + W < m) { b1 = __ldg(rowptr + row + W); e1 = __ldg(rowptr + row + W + 1); }
+  while (true) {
+    float xg[U];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
-  if (lane == 0) {
-    float out = (SC ? alpha * __ldg(sout + row) : alpha) * sum;
-    y[row] = acc ? y[row] + out : out;
+    for (int u = 0; u < U; ++u) xg[u] = c[u] >= 0 ? xin(c[u]) : 0.f;
+    const int64_t next = row + W;
+    int32_t cn[U];
+    float vn[U];
+    int32_t b2 = 0, e2 = 0;
+    if (next < m) {
+      csr_fetch<BF16, U>(col, val, b1, e1, lane, cn, vn);
+      if (next + W < m) { b2 = __ldg(rowptr + next + W); e2 = __ldg(rowptr + next + W + 1); }
+    }
+    float s[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) s[u] = v[u] * xg[u];
+    for (int32_t k = b + lane + 32 * U; k < e; k += 32) {
+      const int32_t j = __ldg(col + k);
+      s[0] = fmaf(csr_val<BF16>(val, k), xin(j), s[0]);
+    }
+#pragma unroll
+    for (int w = U / 2; w > 0; w >>= 1)
+#pragma unroll
+      for (int u = 0; u < w; ++u) s[u] += s[u + w];
+    float sum = s[0];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
+    if (lane == 0) {
+      float out = (SC ? alpha * __ldg(sout + row) : alpha) * sum;
+      y[row] = acc ? y[row] + out : out;
+    }
+    if (next >= m) break;
+    row = next;
+    b = b1;
+    e = e1;
+    b1 = b2;
+    e1 = e2;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      c[u] = cn[u];
+      v[u] = vn[u];
+    }
   }
+}
+
+// The persistent grid: CTAs that fit at once (occupancy x SMs), no more
+// than the rows need.  Cached per kernel instance.
+template <bool BF16, bool SC, int U>
+static unsigned csr_grid(int64_t m) {
+  static const int resident = [] {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_csr<BF16, SC, U>, 256, 0);
+    return std::max(1, sms * std::max(per_sm, 1));
+  }();
+  return (unsigned)std::min<int64_t>((m + 7) / 8, resident);
+}
+
+template <bool BF16, bool SC, int U>
+static void csr_launch_one(cudaStream_t s, int64_t m, const int32_t* rowptr, const int32_t* col, const void* val,
+                           float alpha, const float* x, float* y, bool acc, const float* sin, const float* sout) {
+  k_csr<BF16, SC, U><<<csr_grid<BF16, SC, U>(m), 256, 0, s>>>(m, rowptr, col, val, alpha, x, y, acc, sin, sout);
+}
+
+template <int U>
+static void csr_launch_u(cudaStream_t s, cf_prec p, int64_t m, const int32_t* rowptr, const int32_t* col,
+                         const void* val, float alpha, const float* x, float* y, bool acc, const float* sin,
+                         const float* sout) {
+  // both scalings or none (op_apply folds a product only when both diagonals are stored)
+  if (sin || sout) {
+    if (p == CF_BF16)
+      csr_launch_one<true, true, U>(s, m, rowptr, col, val, alpha, x, y, acc, sin, sout);
+    else
+      csr_launch_one<false, true, U>(s, m, rowptr, col, val, alpha, x, y, acc, sin, sout);
+  } else if (p == CF_BF16) {
+    csr_launch_one<true, false, U>(s, m, rowptr, col, val, alpha, x, y, acc, nullptr, nullptr);
+  } else {
+    csr_launch_one<false, false, U>(s, m, rowptr, col, val, alpha, x, y, acc, nullptr, nullptr);
+  }
+}
+
+void csr_prepare() {
+  const int64_t big = INT32_MAX;
+  (void)csr_grid<false, false, 8>(big); (void)csr_grid<true, false, 8>(big);
+  (void)csr_grid<false, true, 8>(big); (void)csr_grid<true, true, 8>(big);
+  (void)csr_grid<false, false, 16>(big); (void)csr_grid<true, false, 16>(big);
+  (void)csr_grid<false, true, 16>(big); (void)csr_grid<true, true, 16>(big);
 }
 
 void launch_csr(cudaStream_t s, cf_prec p, int64_t m, int64_t nnz, const int32_t* rowptr, const int32_t* col,
                 const void* val, float alpha, const float* x, float* y, bool acc, const float* sin,
                 const float* sout) {
   if (m <= 0) return;
-  (void)nnz;
-  unsigned grid = (unsigned)((m + 7) / 8);
-  // both scalings or none (op_apply folds a product only when both diagonals are stored)
-  if (sin || sout) {
-    if (p == CF_BF16)
-      k_csr<true, true><<<grid, 256, 0, s>>>(m, rowptr, col, val, alpha, x, y, acc, sin, sout);
-    else
-      k_csr<false, true><<<grid, 256, 0, s>>>(m, rowptr, col, val, alpha, x, y, acc, sin, sout);
-  } else if (p == CF_BF16) {
-    k_csr<true, false><<<grid, 256, 0, s>>>(m, rowptr, col, val, alpha, x, y, acc, nullptr, nullptr);
-  } else {
-    k_csr<false, false><<<grid, 256, 0, s>>>(m, rowptr, col, val, alpha, x, y, acc, nullptr, nullptr);
-  }
+  if (nnz > 256 * m)
+    csr_launch_u<16>(s, p, m, rowptr, col, val, alpha, x, y, acc, sin, sout);
+  else
+    csr_launch_u<8>(s, p, m, rowptr, col, val, alpha, x, y, acc, sin, sout);
 }
 
 // ------------------------------------------------------------ small GEMM

@@ -470,6 +470,7 @@ cf_err cf_op_csr(cf_ctx* ctx, int64_t m, int64_t n, int64_t nnz, const int32_t* 
     return fail(CF_E_INVALID, "cf_op_csr: storage must be CF_FP32 or CF_BF16");
   if (nnz > INT32_MAX) return fail(CF_E_INVALID, "cf_op_csr: nnz exceeds int32");
   DevGuard g(ctx->device);
+  csr_prepare();
   // Host copies: validate, then build the transpose (CSR of A^T) by a
   // counting sort over columns, keeping row order inside each column.
   std::vector<int32_t> rp(m + 1), cl(nnz), trp(n + 1, 0), tcl(nnz);

@@ -112,6 +112,31 @@ __device__ bool grid_sum(double (&v)[NV], double* part, unsigned int* counter) {
   for (int64_t i = ((n) & ~(int64_t)3) + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; \
        i < (n); i += (int64_t)gridDim.x * blockDim.x)
 
+// The same walk in batches of U consecutive strides: the loads of U groups
+// (load(v) returns them) go out before the first is used (use(v, data)), so
+// a thread has U groups in flight.  The groups are used in the order of the
+// plain walk, so per-thread sums come out bit for bit the same.  The grids of
+// the kernels that end in a grid-wide sum hold only 16 warps per SM (their
+// per-CTA ticket costs more than extra elements per thread do); this is
+// where their memory-level parallelism comes from.
+constexpr int kVecBatch = 4;
+
+template <int U, class Load, class Use>
+__device__ __forceinline__ void vec4_batched(int64_t n4, Load&& load, Use&& use) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t v0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v0 < n4; v0 += U * stride) {
+    decltype(load(v0)) d[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (v0 + u * stride < n4) d[u] = load(v0 + u * stride);
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (v0 + u * stride < n4) use(v0 + u * stride, d[u]);
+  }
+}
+
+__device__ __forceinline__ float4 zero4() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+
 // ------------------------------------------------------------ problem data
 // b, c (float64, already on the device) -> float32 copies, per-CTA float64
 // sums of b_i^2 and c_i^2 (summed on the host in CTA order), and a flag set
@@ -179,36 +204,54 @@ __device__ __forceinline__ int fold_row(const Fold& f, int64_t r) {
     if (r >= f.r0[b] && r < f.r0[b] + f.len[b]) return b;
   return -1;
 }
+// The helpers below walk the blocks with static indices (unrolled over
+// kMaxFold), so the Fold parameter is read in place, never copied to the
+// stack.
+// Column of the folded block entry in row r (c0 + r - r0), or -1.
+__device__ __forceinline__ int64_t fold_row_col(const Fold& f, int64_t r) {
+  int64_t c = -1;
+#pragma unroll
+  for (int b = 0; b < kMaxFold; ++b)
+    if (b < f.nb && c < 0 && r >= f.r0[b] && r < f.r0[b] + f.len[b]) c = f.c0[b] + (r - f.r0[b]);
+  return c;
+}
 // Whether any folded block touches columns (or rows) [lo, lo + 4).
 __device__ __forceinline__ bool fold_cols_touch(const Fold& f, int64_t lo) {
-  for (int b = 0; b < f.nb; ++b)
-    if (lo < f.c0[b] + f.len[b] && f.c0[b] < lo + 4) return true;
-  return false;
+  bool t = false;
+#pragma unroll
+  for (int b = 0; b < kMaxFold; ++b) t |= b < f.nb && lo < f.c0[b] + f.len[b] && f.c0[b] < lo + 4;
+  return t;
 }
 __device__ __forceinline__ bool fold_rows_touch(const Fold& f, int64_t lo) {
-  for (int b = 0; b < f.nb; ++b)
-    if (lo < f.r0[b] + f.len[b] && f.r0[b] < lo + 4) return true;
-  return false;
+  bool t = false;
+#pragma unroll
+  for (int b = 0; b < kMaxFold; ++b) t |= b < f.nb && lo < f.r0[b] + f.len[b] && f.r0[b] < lo + 4;
+  return t;
 }
 __device__ __forceinline__ bool fold_rows_cover(const Fold& f, int64_t lo) {
-  for (int b = 0; b < f.nb; ++b)
-    if (lo >= f.r0[b] && lo + 4 <= f.r0[b] + f.len[b]) return true;
-  return false;
+  bool t = false;
+#pragma unroll
+  for (int b = 0; b < kMaxFold; ++b) t |= b < f.nb && lo >= f.r0[b] && lo + 4 <= f.r0[b] + f.len[b];
+  return t;
 }
-// The one block whose rows (cols: its columns) hold all of [lo, lo + 4), with
-// its row-to-column offset a multiple of 4 (16-byte loads on both sides), and
-// no other block touching them; -1 otherwise.
+// Whether one block's rows (COLS: its columns) hold all of [lo, lo + 4),
+// with its column-minus-row offset a multiple of 4 (16-byte loads on both
+// sides), and no other block touching them; the offset c0 - r0 in *delta.
 template <bool COLS>
-__device__ __forceinline__ int fold_vec_block(const Fold& f, int64_t lo) {
-  int hit = -1;
-  for (int b = 0; b < f.nb; ++b) {
+__device__ __forceinline__ bool fold_vec_delta(const Fold& f, int64_t lo, int64_t* delta) {
+  int hits = 0;
+  bool ok = true;
+#pragma unroll
+  for (int b = 0; b < kMaxFold; ++b) {
+    if (b >= f.nb) break;
     const int64_t a = COLS ? f.c0[b] : f.r0[b];
     if (lo < a + f.len[b] && a < lo + 4) {
-      if (hit >= 0 || lo < a || lo + 4 > a + f.len[b] || ((f.c0[b] - f.r0[b]) & 3)) return -1;
-      hit = b;
+      ++hits;
+      ok = ok && lo >= a && lo + 4 <= a + f.len[b] && ((f.c0[b] - f.r0[b]) & 3) == 0;
+      *delta = f.c0[b] - f.r0[b];
     }
   }
-  return hit;
+  return hits == 1 && ok;
 }
 
 // Diagonal of each folded block's rows, s_r = D_r alpha d_j E_(c0 + j)
@@ -254,8 +297,9 @@ __global__ void k_rhs(Ctl* c, int64_t n, int64_t m, const float* __restrict__ ux
   }
   TAIL_LOOP(i, m) wy[i] = uy[i] + vs[i];
   auto folded = [&](int64_t col, float x) {
-    for (int b = 0; b < f.nb; ++b)
-      if (col >= f.c0[b] && col < f.c0[b] + f.len[b]) {
+#pragma unroll
+    for (int b = 0; b < kMaxFold; ++b)
+      if (b < f.nb && col >= f.c0[b] && col < f.c0[b] + f.len[b]) {
         const int64_t r = f.r0[b] + (col - f.c0[b]);
         x = fmaf(-f.s[r], uy[r] + vs[r], x);
       }
@@ -264,9 +308,9 @@ __global__ void k_rhs(Ctl* c, int64_t n, int64_t m, const float* __restrict__ ux
   VEC4_LOOP(v, n >> 2) {
     float4 x = ld4(ux, v);
     if (f.nb && fold_cols_touch(f, 4 * v)) {
-      const int b = fold_vec_block<true>(f, 4 * v);
-      if (b >= 0) {
-        const int64_t rv = v + ((f.r0[b] - f.c0[b]) >> 2);
+      int64_t delta = 0;
+      if (fold_vec_delta<true>(f, 4 * v, &delta)) {
+        const int64_t rv = v - delta / 4;
         const float4 s4 = ld4(f.s, rv), a4 = ld4(uy, rv), b4 = ld4(vs, rv);
 #pragma unroll
         for (int k = 0; k < 4; ++k) el(x, k) = fmaf(-elc(s4, k), elc(a4, k) + elc(b4, k), el(x, k));
@@ -304,28 +348,37 @@ __global__ void k_cg_init(Ctl* c, int64_t n, const float* __restrict__ rhs,
                           const float* __restrict__ gd, float* __restrict__ q) {
   const float lam = (float)c->lam;
   Acc2 a0, a1;
-  VEC4_LOOP(v, n >> 2) {
-    float4 g = ld4(gz, v);
-    const float4 rh = ld4(rhs, v);
-    const float4 dg = gd ? ld4(gd, v) : make_float4(0.f, 0.f, 0.f, 0.f);
-    if (fresh) {
-      const float4 zz = ld4(z, v);
+  struct In { float4 g, rh, dg, zz; };
+  vec4_batched<kVecBatch>(
+      n >> 2,
+      [&](int64_t v) {
+        In d;
+        d.g = ld4(gz, v);
+        d.rh = ld4(rhs, v);
+        d.dg = gd ? ld4(gd, v) : zero4();
+        d.zz = fresh ? ld4(z, v) : zero4();
+        return d;
+      },
+      [&](int64_t v, In& d) {
+        float4 g = d.g;
+        const float4 rh = d.rh, dg = d.dg;
+        if (fresh) {
 #pragma unroll
-      for (int k = 0; k < 4; ++k) el(g, k) = fmaf(lam + elc(dg, k), elc(zz, k), el(g, k));
-      st4(gz, v, g);
-    }
-    float4 rr, qq;
+          for (int k = 0; k < 4; ++k) el(g, k) = fmaf(lam + elc(dg, k), elc(d.zz, k), el(g, k));
+          st4(gz, v, g);
+        }
+        float4 rr, qq;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      el(rr, k) = elc(rh, k) - elc(g, k);
-      el(qq, k) = (lam + elc(dg, k)) * el(rr, k);
-      a0.add_prod(elc(rr, k), elc(rr, k));
-      a1.add_prod(elc(rh, k), elc(rh, k));
-    }
-    st4(r, v, rr);
-    st4(p, v, rr);
-    if (gd) st4(q, v, qq);
-  }
+        for (int k = 0; k < 4; ++k) {
+          el(rr, k) = elc(rh, k) - elc(g, k);
+          el(qq, k) = (lam + elc(dg, k)) * el(rr, k);
+          a0.add_prod(elc(rr, k), elc(rr, k));
+          a1.add_prod(elc(rh, k), elc(rh, k));
+        }
+        st4(r, v, rr);
+        st4(p, v, rr);
+        if (gd) st4(q, v, qq);
+      });
   TAIL_LOOP(i, n) {
     float g = gz[i];
     const float dg = gd ? gd[i] : 0.f;
@@ -373,16 +426,18 @@ __global__ void k_cg_dot(Ctl* c, int64_t n, const float* __restrict__ p, float* 
                          double* part, int folded) {
   const float lam = (float)c->lam;
   Acc2 a0;
-  VEC4_LOOP(w, n >> 2) {
-    const float4 pp = ld4(p, w);
-    float4 qq = ld4(q, w);
+  struct In { float4 pp, qq; };
+  vec4_batched<kVecBatch>(
+      n >> 2, [&](int64_t w) { return In{ld4(p, w), ld4(q, w)}; },
+      [&](int64_t w, In& d) {
+        float4 qq = d.qq;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      if (!folded) el(qq, k) = el(qq, k) + lam * elc(pp, k);
-      a0.add_prod(elc(pp, k), elc(qq, k));
-    }
-    if (!folded) st4(q, w, qq);
-  }
+        for (int k = 0; k < 4; ++k) {
+          if (!folded) el(qq, k) = el(qq, k) + lam * elc(d.pp, k);
+          a0.add_prod(elc(d.pp, k), elc(qq, k));
+        }
+        if (!folded) st4(q, w, qq);
+      });
   TAIL_LOOP(i, n) {
     const float pi = p[i];
     float qi = folded ? q[i] : q[i] + lam * pi;
@@ -404,20 +459,21 @@ __global__ void k_cg_update(Ctl* c, int64_t n, int64_t m, float* __restrict__ z,
                             const float* __restrict__ t, double* part, int mode, Fold f) {
   const float a = (float)c->alpha_cg;
   Acc2 a0;
-  VEC4_LOOP(v, n >> 2) {
-    const float4 qq = ld4(q, v), pp = ld4(p, v);
-    float4 zz = ld4(z, v), gg = ld4(gz, v), rr = ld4(r, v);
+  struct In { float4 qq, pp, zz, gg, rr; };
+  vec4_batched<kVecBatch>(
+      n >> 2, [&](int64_t v) { return In{ld4(q, v), ld4(p, v), ld4(z, v), ld4(gz, v), ld4(r, v)}; },
+      [&](int64_t v, In& d) {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      el(zz, k) = fmaf(a, elc(pp, k), el(zz, k));
-      el(gg, k) = fmaf(a, elc(qq, k), el(gg, k));
-      el(rr, k) = fmaf(-a, elc(qq, k), el(rr, k));
-      a0.add_prod(elc(rr, k), elc(rr, k));
-    }
-    st4(z, v, zz);
-    st4(gz, v, gg);
-    st4(r, v, rr);
-  }
+        for (int k = 0; k < 4; ++k) {
+          el(d.zz, k) = fmaf(a, elc(d.pp, k), el(d.zz, k));
+          el(d.gg, k) = fmaf(a, elc(d.qq, k), el(d.gg, k));
+          el(d.rr, k) = fmaf(-a, elc(d.qq, k), el(d.rr, k));
+          a0.add_prod(elc(d.rr, k), elc(d.rr, k));
+        }
+        st4(z, v, d.zz);
+        st4(gz, v, d.gg);
+        st4(r, v, d.rr);
+      });
   TAIL_LOOP(i, n) {
     const float qi = q[i];
     z[i] = fmaf(a, p[i], z[i]);
@@ -429,14 +485,24 @@ __global__ void k_cg_update(Ctl* c, int64_t n, int64_t m, float* __restrict__ z,
   double v[1] = {a0.value()};
   if (az) {
     // rows of folded blocks: A z there is s z, formed where it is used
-    VEC4_LOOP(w, m >> 2) {
-      if (f.nb && fold_rows_cover(f, 4 * w)) continue;
-      const float4 tt = ld4(t, w);
-      float4 aa = ld4(az, w);
+    struct InA { float4 tt, aa; bool skip; };
+    vec4_batched<kVecBatch>(
+        m >> 2,
+        [&](int64_t w) {
+          InA d;
+          d.skip = f.nb && fold_rows_cover(f, 4 * w);
+          if (!d.skip) {
+            d.tt = ld4(t, w);
+            d.aa = ld4(az, w);
+          }
+          return d;
+        },
+        [&](int64_t w, InA& d) {
+          if (d.skip) return;
 #pragma unroll
-      for (int k = 0; k < 4; ++k) el(aa, k) = fmaf(a, elc(tt, k), el(aa, k));
-      st4(az, w, aa);
-    }
+          for (int k = 0; k < 4; ++k) el(d.aa, k) = fmaf(a, elc(d.tt, k), el(d.aa, k));
+          st4(az, w, d.aa);
+        });
     TAIL_LOOP(i, m) az[i] = fmaf(a, t[i], az[i]);
   }
   if (grid_sum<1>(v, part, &c->red_count) && threadIdx.x == 0) {
@@ -506,42 +572,51 @@ __global__ void k_utau(Ctl* c, int64_t n, int64_t m, const float* __restrict__ z
                        const float* __restrict__ bf, const float* __restrict__ cf, double* part, Fold f) {
   Acc2 a0;
   auto azr = [&](int64_t r, float carried) {
-    const int b = fold_row(f, r);
-    return b < 0 ? carried : f.s[r] * zx[f.c0[b] + (r - f.r0[b])];
+    const int64_t col = fold_row_col(f, r);
+    return col < 0 ? carried : f.s[r] * zx[col];
   };
-  VEC4_LOOP(w, m >> 2) {
-    const float4 ww = ld4(wy, w), bb = ld4(bf, w);
-    float4 aa;
-    const bool touch = f.nb && fold_rows_touch(f, 4 * w);
-    const int vb = touch ? fold_vec_block<false>(f, 4 * w) : -1;
-    if (vb >= 0) {  // four rows of one block: s z_x[c0 + j], 16-byte loads
-      const float4 s4 = ld4(f.s, w), z4 = ld4(zx, w + ((f.c0[vb] - f.r0[vb]) >> 2));
-      aa = make_float4(s4.x * z4.x, s4.y * z4.y, s4.z * z4.z, s4.w * z4.w);
-    } else {
-      aa = ld4(az, w);
-      if (touch) {
+  struct In { float4 ww, bb, aa; };
+  vec4_batched<kVecBatch>(
+      m >> 2,
+      [&](int64_t w) {
+        In d;
+        d.ww = ld4(wy, w);
+        d.bb = ld4(bf, w);
+        const bool touch = f.nb && fold_rows_touch(f, 4 * w);
+        int64_t delta = 0;
+        if (touch && fold_vec_delta<false>(f, 4 * w, &delta)) {  // four rows of one block: s z_x[c0 + j]
+          const float4 s4 = ld4(f.s, w), z4 = ld4(zx, w + delta / 4);
+          d.aa = make_float4(s4.x * z4.x, s4.y * z4.y, s4.z * z4.z, s4.w * z4.w);
+        } else {
+          d.aa = ld4(az, w);
+          if (touch) {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) el(aa, k) = azr(4 * w + k, el(aa, k));
-      }
-    }
-    float4 zz;
+            for (int k = 0; k < 4; ++k) el(d.aa, k) = azr(4 * w + k, el(d.aa, k));
+          }
+        }
+        return d;
+      },
+      [&](int64_t w, In& d) {
+        float4 zz;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      el(zz, k) = elc(aa, k) + elc(ww, k);
-      a0.add_prod(elc(bb, k), elc(zz, k));
-    }
-    st4(zy, w, zz);
-  }
+        for (int k = 0; k < 4; ++k) {
+          el(zz, k) = elc(d.aa, k) + elc(d.ww, k);
+          a0.add_prod(elc(d.bb, k), elc(zz, k));
+        }
+        st4(zy, w, zz);
+      });
   TAIL_LOOP(i, m) {
     float zi = (f.nb ? azr(i, az[i]) : az[i]) + wy[i];
     zy[i] = zi;
     a0.add_prod(bf[i], zi);
   }
-  VEC4_LOOP(w, n >> 2) {
-    const float4 cc = ld4(cf, w), xx = ld4(zx, w);
+  struct InX { float4 cc, xx; };
+  vec4_batched<kVecBatch>(
+      n >> 2, [&](int64_t w) { return InX{ld4(cf, w), ld4(zx, w)}; },
+      [&](int64_t, InX& d) {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) a0.add_prod(elc(cc, k), elc(xx, k));
-  }
+        for (int k = 0; k < 4; ++k) a0.add_prod(elc(d.cc, k), elc(d.xx, k));
+      });
   TAIL_LOOP(i, n) a0.add_prod(cf[i], zx[i]);
   double v[1] = {a0.value()};
   if (grid_sum<1>(v, part, &c->red_count) && threadIdx.x == 0)
