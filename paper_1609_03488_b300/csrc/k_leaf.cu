@@ -281,12 +281,15 @@ void launch_conv2d(cudaStream_t s, int64_t Ho, int64_t Wo, int64_t Hi, int64_t W
 // rows and all its threads sweep the columns together, each thread taking
 // the V columns of one 16-byte load, so that the CTA reads THREADS x 16
 // contiguous bytes of each of its rows at once (long DRAM bursts) and each
-// slice of x a thread loads serves RW rows.  The per-thread sums of a row
-// are added by a warp tree and then across warps in warp order.
+// slice of x a thread loads serves RW rows.  PF: the next sweep's operand
+// loads are issued before the current sweep's arithmetic (FP8, whose
+// unpacking makes a sweep long enough to hide them behind).  The per-thread
+// sums of a row are added by a warp tree and then across warps in warp
+// order.
 // SC: x is read as sin * x and the rows are multiplied by sout.
 constexpr int kGemvNRows = 8;
 
-template <typename T, int THREADS, bool SC>
+template <typename T, int THREADS, bool PF, bool SC>
 __global__ void __launch_bounds__(THREADS)
 k_gemv_n(int64_t m, int64_t n, int64_t lda, const T* __restrict__ A, const float* __restrict__ rs,
          float alpha, const float* __restrict__ x, float* __restrict__ y, bool acc,
@@ -305,10 +308,17 @@ k_gemv_n(int64_t m, int64_t n, int64_t lda, const T* __restrict__ A, const float
   float accv[RW];
 #pragma unroll
   for (int r = 0; r < RW; ++r) accv[r] = 0.f;
-  for (int64_t c = (int64_t)threadIdx.x * V; c < n; c += (int64_t)THREADS * V) {
-    uint4 u[RW];
+  int64_t c = (int64_t)threadIdx.x * V;
+  uint4 u[RW];
+  if (PF && c < n) {
 #pragma unroll
     for (int r = 0; r < RW; ++r) u[r] = __ldg(reinterpret_cast<const uint4*>(arow[r] + c));
+  }
+  for (; c < n; c += (int64_t)THREADS * V) {
+    if (!PF) {
+#pragma unroll
+      for (int r = 0; r < RW; ++r) u[r] = __ldg(reinterpret_cast<const uint4*>(arow[r] + c));
+    }
     float xv[V];
     if (xal && c + V <= n) {
 #pragma unroll
@@ -325,12 +335,23 @@ k_gemv_n(int64_t m, int64_t n, int64_t lda, const T* __restrict__ A, const float
       for (int q = 0; q < V; ++q)
         xv[q] = (c + q < n) ? (SC ? __ldg(sin + c + q) * __ldg(x + c + q) : __ldg(x + c + q)) : 0.f;
     }
+    uint4 un[RW];
+    if (PF) {
+      const int64_t cn = c + (int64_t)THREADS * V;
+#pragma unroll
+      for (int r = 0; r < RW; ++r)
+        un[r] = cn < n ? __ldg(reinterpret_cast<const uint4*>(arow[r] + cn)) : make_uint4(0u, 0u, 0u, 0u);
+    }
 #pragma unroll
     for (int r = 0; r < RW; ++r) {
       float av[V];
       Vec<T>::unpack(u[r], av);
 #pragma unroll
       for (int q = 0; q < V; ++q) accv[r] = fmaf(av[q], xv[q], accv[r]);
+    }
+    if (PF) {
+#pragma unroll
+      for (int r = 0; r < RW; ++r) u[r] = un[r];
     }
   }
 #pragma unroll
@@ -359,11 +380,13 @@ static void gemv_n_typed(cudaStream_t s, int64_t m, int64_t n, int64_t lda, cons
                          float alpha, const float* x, float* y, bool acc, const float* sin, const float* sout) {
   // 2048 columns a sweep for the 1- and 2-byte types, 1024 for float32
   constexpr int TH = sizeof(T) == 1 ? 128 : 256;
+  constexpr bool PF = sizeof(T) == 1;
   const unsigned grid = (unsigned)((m + kGemvNRows - 1) / kGemvNRows);
   if (sin || sout)
-    k_gemv_n<T, TH, true><<<grid, TH, 0, s>>>(m, n, lda, (const T*)A, rs, alpha, x, y, acc, sin, sout);
+    k_gemv_n<T, TH, PF, true><<<grid, TH, 0, s>>>(m, n, lda, (const T*)A, rs, alpha, x, y, acc, sin, sout);
   else
-    k_gemv_n<T, TH, false><<<grid, TH, 0, s>>>(m, n, lda, (const T*)A, rs, alpha, x, y, acc, nullptr, nullptr);
+    k_gemv_n<T, TH, PF, false><<<grid, TH, 0, s>>>(m, n, lda, (const T*)A, rs, alpha, x, y, acc, nullptr,
+                                                   nullptr);
 }
 
 void launch_gemv_n(cudaStream_t s, cf_prec p, int64_t m, int64_t n, int64_t lda, const void* A,
@@ -380,17 +403,20 @@ void launch_gemv_n(cudaStream_t s, cf_prec p, int64_t m, int64_t n, int64_t lda,
 
 // x^T-side: part[rb, j] = sum_{i in row block rb} A[i, j] (s_i y_i); each
 // thread owns the V columns of one 16-byte load, so every row is read once
-// with coalesced loads.  A CTA of 256 threads covers kGemvTCols columns
-// whatever the storage type: 256 / 128 / 64 threads span the columns for
-// FP32 / BF16 / FP8, and the narrower types split the block's rows over
-// RG = 1 / 2 / 4 row groups (rows r0 + g, r0 + g + RG, ...) whose sums are
-// added in group order through shared memory.  A thread has kGemvTUnroll
-// rows' loads in flight; the row blocks are sized for about 8 CTAs per SM.
-// A second kernel sums the row blocks in a fixed order.
+// with coalesced loads.  A CTA covers kGemvTCols columns whatever the storage
+// type: 256 / 128 / 64 threads span them for FP32 / BF16 / FP8, and FP8 runs
+// RG = 4 such row groups per CTA (rows r0 + g, r0 + g + 4, ...; 256 threads)
+// whose sums are added in group order through shared memory.  A thread has
+// kGemvTUnroll rows' loads in flight.  The row blocks are sized for one wave
+// of 8 CTAs per SM (4 for FP8), the shapes measured fastest at 20000 x
+// 10000.  A second kernel sums the row blocks in a fixed order.
 constexpr int kGemvTCols = 1024;
 constexpr int kGemvTMaxRows = 512;
 constexpr int kGemvTUnroll = 8;
-constexpr int kGemvTThreads = 256;
+constexpr int kGemvTThreads = 256;  // the largest CTA
+
+template <typename T>
+constexpr int gemv_t_groups() { return sizeof(T) == 1 ? 4 : 1; }
 
 template <typename T>
 __global__ void __launch_bounds__(kGemvTThreads)
@@ -398,8 +424,8 @@ k_gemv_t_part(int64_t m, int64_t n, int64_t lda, int64_t rows_per_block, const T
               const float* __restrict__ rs, const float* __restrict__ yv, float* __restrict__ part,
               const float* __restrict__ sin) {
   constexpr int V = Vec<T>::N;
-  constexpr int CT = kGemvTCols / V;      // threads across the columns
-  constexpr int RG = kGemvTThreads / CT;  // row groups
+  constexpr int CT = kGemvTCols / V;  // threads across the columns
+  constexpr int RG = gemv_t_groups<T>();
   __shared__ float sy[kGemvTMaxRows];
   __shared__ float red[RG > 1 ? RG - 1 : 1][RG > 1 ? kGemvTCols : 1];
   const int64_t r0 = (int64_t)blockIdx.y * rows_per_block;
@@ -489,8 +515,7 @@ k_gemv_t_reduce(int64_t n, int64_t lda, int nrb, const float* __restrict__ part,
   }
 }
 
-// Row blocks for `per_sm` CTAs per SM (the CTAs that fit: 8 / 6 / 4 for
-// FP32 / BF16 / FP8 by registers), rounded down so the grid is one wave.
+// Row blocks for `per_sm` CTAs per SM, rounded down so the grid is one wave.
 static int gemv_t_row_blocks(int64_t m, int64_t n, int per_sm = 8) {
   const int64_t col_tiles = (n + kGemvTCols - 1) / kGemvTCols;
   const int64_t want = std::max<int64_t>(1, (int64_t)per_sm * 148 / col_tiles);
@@ -512,9 +537,9 @@ void launch_gemv_t(cudaStream_t s, cf_prec p, int64_t m, int64_t n, int64_t lda,
     if (!acc) launch_fill(s, n, 0.f, y);
     return;
   }
-  const int rb = gemv_t_row_blocks(m, n, p == CF_FP32 ? 8 : (p == CF_BF16 ? 6 : 4));  // <= the workspace's
+  const int rb = gemv_t_row_blocks(m, n, p == CF_FP8_E4M3 ? 4 : 8);  // <= the workspace's (8)
   const int64_t rows_per_block = (m + rb - 1) / rb;
-  const int threads = kGemvTThreads;
+  const int threads = p == CF_FP32 ? 256 : (p == CF_BF16 ? 128 : 64 * gemv_t_groups<__nv_fp8_e4m3>());
   dim3 grid((unsigned)((n + kGemvTCols - 1) / kGemvTCols), (unsigned)rb);
   if (p == CF_FP32)
     k_gemv_t_part<float><<<grid, threads, 0, s>>>(m, n, lda, rows_per_block, (const float*)A, rs, x, ws, sin);

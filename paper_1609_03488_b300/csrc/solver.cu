@@ -773,17 +773,38 @@ __global__ void k_apply(Ctl* c, int64_t n, int64_t m, int64_t z, int64_t l, int 
   const float head_val = (float)ah;
   const float scl = mode == 2 ? (float)(ah / nrm) : 0.f;
   const int64_t r0 = chunk_r0[ch], r1 = chunk_r1[ch];
-  for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
-    float pi = y_pre(a, a1, ut, zy[i], gy[i], uy[i], vs[i]);
-    float ui;
-    if (mode == 0)
-      ui = pi;
-    else if (mode == 1)
-      ui = 0.f;
-    else
-      ui = (i == head) ? head_val : __fmul_rn(scl, pi);
+  auto proj = [&](int64_t i, float pi) {
+    if (mode == 0) return pi;
+    if (mode == 1) return 0.f;
+    return (i == head) ? head_val : __fmul_rn(scl, pi);
+  };
+  auto row = [&](int64_t i) {
+    const float pi = y_pre(a, a1, ut, zy[i], gy[i], uy[i], vs[i]);
+    const float ui = proj(i, pi);
     uy[i] = ui;
     vs[i] = __fsub_rn(ui, pi);
+  };
+  // 16-byte accesses over the chunk's 4-aligned interior, single rows at its edges
+  const int64_t q0 = (r0 + 3) & ~(int64_t)3, q1 = r1 & ~(int64_t)3;
+  if (q0 >= q1) {
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) row(i);
+    return;
+  }
+  for (int64_t i = r0 + threadIdx.x; i < q0; i += blockDim.x) row(i);
+  for (int64_t i = q1 + threadIdx.x; i < r1; i += blockDim.x) row(i);
+#pragma unroll 2
+  for (int64_t v = (q0 >> 2) + threadIdx.x; v < (q1 >> 2); v += blockDim.x) {
+    const float4 z4 = ld4(zy, v), g4 = ld4(gy, v);
+    float4 u4 = ld4(uy, v), s4 = ld4(vs, v);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float pi = y_pre(a, a1, ut, elc(z4, k), elc(g4, k), elc(u4, k), elc(s4, k));
+      const float ui = proj(4 * v + k, pi);
+      el(u4, k) = ui;
+      el(s4, k) = __fsub_rn(ui, pi);
+    }
+    st4(uy, v, u4);
+    st4(vs, v, s4);
   }
 }
 
@@ -825,19 +846,22 @@ __global__ void k_resid(Ctl* c, int64_t n, int64_t m, const float* __restrict__ 
     s5.add_prod(cfi, uxi);
   };
   const float4 one4 = make_float4(1.f, 1.f, 1.f, 1.f);
-  VEC4_LOOP(v, m >> 2) {
-    const float4 w = dinv ? ld4(dinv, v) : one4;
-    const float4 a = ld4(cm, v), b = ld4(vs, v), c4 = ld4(bf, v), u = ld4(uy, v);
+  struct InY { float4 w, a, b, c4, u; };
+  vec4_batched<kVecBatch>(
+      m >> 2,
+      [&](int64_t v) { return InY{dinv ? ld4(dinv, v) : one4, ld4(cm, v), ld4(vs, v), ld4(bf, v), ld4(uy, v)}; },
+      [&](int64_t, InY& d) {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) row_y(elc(w, k), elc(a, k), elc(b, k), elc(c4, k), elc(u, k));
-  }
+        for (int k = 0; k < 4; ++k) row_y(elc(d.w, k), elc(d.a, k), elc(d.b, k), elc(d.c4, k), elc(d.u, k));
+      });
   TAIL_LOOP(i, m) row_y(dinv ? dinv[i] : 1.f, cm[i], vs[i], bf[i], uy[i]);
-  VEC4_LOOP(v, n >> 2) {
-    const float4 w = einv ? ld4(einv, v) : one4;
-    const float4 a = ld4(cn, v), c4 = ld4(cf, v), u = ld4(ux, v);
+  struct InX { float4 w, a, c4, u; };
+  vec4_batched<kVecBatch>(
+      n >> 2, [&](int64_t v) { return InX{einv ? ld4(einv, v) : one4, ld4(cn, v), ld4(cf, v), ld4(ux, v)}; },
+      [&](int64_t, InX& d) {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) row_x(elc(w, k), elc(a, k), elc(c4, k), elc(u, k));
-  }
+        for (int k = 0; k < 4; ++k) row_x(elc(d.w, k), elc(d.a, k), elc(d.c4, k), elc(d.u, k));
+      });
   TAIL_LOOP(i, n) row_x(einv ? einv[i] : 1.f, cn[i], cf[i], ux[i]);
   double v[6] = {s0.value(), s1.value(), s2.value(), s3.value(), s4.value(), s5.value()};
   if (grid_sum<6>(v, part, &c->red_count) && threadIdx.x == 0) {
