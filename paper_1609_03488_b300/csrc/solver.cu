@@ -143,9 +143,10 @@ __device__ __forceinline__ float4 ld4cg(const float* p, int64_t v) {
   return __ldcg(reinterpret_cast<const float4*>(p) + v);
 }
 
-// Programmatic dependent launch.  k_cg_update, k_cg_p, k_soc_norm and k_apply
-// are launched with programmatic stream serialisation: such a dependent may
-// start while its predecessor still runs, issues the loads of data the
+// Programmatic dependent launch.  k_cg_update (after k_cg_dot) and k_cg_p
+// (after k_cg_update) are launched with programmatic stream serialisation:
+// such a dependent may start while its predecessor still runs, issues the
+// loads of data the
 // predecessor does not write, then waits (pdl_wait: until the predecessor
 // has completed and its writes are visible) before it reads anything the
 // predecessor writes or writes anything itself.  A predecessor lets its
@@ -637,7 +638,6 @@ __global__ void k_gz_shift(const Ctl* c, int64_t n, const float* __restrict__ z,
 __global__ void k_utau(Ctl* c, int64_t n, int64_t m, const float* __restrict__ zx,
                        const float* __restrict__ az, float* __restrict__ zy, const float* __restrict__ wy,
                        const float* __restrict__ bf, const float* __restrict__ cf, double* part, Fold f) {
-  pdl_release();  // launched after a graph node, so everything before it is complete
   Acc2 a0;
   auto azr = [&](int64_t r, float carried) {
     const int64_t col = fold_row_col(f, r);
@@ -705,6 +705,7 @@ __global__ void k_soc_norm(const Ctl* c, const int32_t* __restrict__ chunk_seg,
   const int32_t sg = chunk_seg[ch];
   const int64_t head = seg_head[sg];
   const int64_t r0 = chunk_r0[ch], r1 = chunk_r1[ch];
+  const float a = (float)c->st.alpha, a1 = (float)(1.0 - c->st.alpha), ut = (float)c->ut_tau;
   Acc2 a0;
   auto row = [&](int64_t i, float pi) {
     if (i == head)
@@ -715,33 +716,15 @@ __global__ void k_soc_norm(const Ctl* c, const int32_t* __restrict__ chunk_seg,
   // 16-byte loads over the chunk's 4-aligned interior, single rows at its edges
   const int64_t q0 = (r0 + 3) & ~(int64_t)3, q1 = r1 & ~(int64_t)3;
   const int64_t e0 = q0 < q1 ? q0 : r1;
-  // g_y, u_y, v_s of the first interior group are not written by the
-  // predecessor (k_utau): they are loaded before the wait; z_y and
-  // u~_tau after it
-  const int64_t vf = (q0 >> 2) + threadIdx.x;
-  const bool pre = q0 < q1 && vf < (q1 >> 2);
-  float4 g4f = zero4(), u4f = zero4(), s4f = zero4();
-  if (pre) {
-    g4f = ld4(gy, vf);
-    u4f = ld4(uy, vf);
-    s4f = ld4(vs, vf);
-  }
-  pdl_wait();
-  pdl_release();
-  const float a = (float)c->st.alpha, a1 = (float)(1.0 - c->st.alpha);
-  const float ut = (float)__ldcg(&c->ut_tau);
-  for (int64_t i = r0 + threadIdx.x; i < e0; i += blockDim.x)
-    row(i, y_pre(a, a1, ut, __ldcg(zy + i), gy[i], uy[i], vs[i]));
+  for (int64_t i = r0 + threadIdx.x; i < e0; i += blockDim.x) row(i, y_pre(a, a1, ut, zy[i], gy[i], uy[i], vs[i]));
   if (q0 < q1) {
 #pragma unroll 2
-    for (int64_t v = vf; v < (q1 >> 2); v += blockDim.x) {
-      const float4 z4 = ld4cg(zy, v);
-      const float4 g4 = v == vf ? g4f : ld4(gy, v), u4 = v == vf ? u4f : ld4(uy, v), s4 = v == vf ? s4f : ld4(vs, v);
+    for (int64_t v = (q0 >> 2) + threadIdx.x; v < (q1 >> 2); v += blockDim.x) {
+      const float4 z4 = ld4(zy, v), g4 = ld4(gy, v), u4 = ld4(uy, v), s4 = ld4(vs, v);
 #pragma unroll
       for (int k = 0; k < 4; ++k) row(4 * v + k, y_pre(a, a1, ut, elc(z4, k), elc(g4, k), elc(u4, k), elc(s4, k)));
     }
-    for (int64_t i = q1 + threadIdx.x; i < r1; i += blockDim.x)
-      row(i, y_pre(a, a1, ut, __ldcg(zy + i), gy[i], uy[i], vs[i]));
+    for (int64_t i = q1 + threadIdx.x; i < r1; i += blockDim.x) row(i, y_pre(a, a1, ut, zy[i], gy[i], uy[i], vs[i]));
   }
   double v[1] = {a0.value()};
   block_sum<1>(v);
@@ -779,38 +762,16 @@ __global__ void k_apply(Ctl* c, int64_t n, int64_t m, int64_t z, int64_t l, int 
                         const int64_t* __restrict__ chunk_r1, const int64_t* __restrict__ seg_head,
                         const double* __restrict__ seg_nrm, const double* __restrict__ seg_p0,
                         cudaGraphConditionalHandle h_check, cudaGraphConditionalHandle h_refresh,
-                        cudaGraphConditionalHandle h_outer, int in_graph, int prefetch) {
-  // prefetch: the predecessor (k_soc_norm) writes none of the vectors read
-  // here, so each thread's first groups are loaded before the wait; without
-  // it (no cone chunks: the predecessor is k_utau, which writes z_y) the wait
-  // comes first
-  if (!prefetch) pdl_wait();
+                        cudaGraphConditionalHandle h_outer, int in_graph) {
+  const double al = c->st.alpha;
+  const float a = (float)al, a1 = (float)(1.0 - al), ut = (float)c->ut_tau;
   if ((int)blockIdx.x < nlin) {
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t stride = (int64_t)nlin * blockDim.x;
-    const int64_t nl = z + l;
-    float4 xz = zero4(), xg = zero4(), xu = zero4(), yz = zero4(), yg = zero4(), yu = zero4(), ys = zero4();
-    if (prefetch) {
-      if (tid < (n >> 2)) {
-        xz = ld4(zx, tid);
-        xg = ld4(gx, tid);
-        xu = ld4(ux, tid);
-      }
-      if (tid < (nl >> 2)) {
-        yz = ld4cg(zy, tid);
-        yg = ld4(gy, tid);
-        yu = ld4(uy, tid);
-        ys = ld4(vs, tid);
-      }
-      pdl_wait();
-    }
-    const double al = c->st.alpha;
-    const float a = (float)al, a1 = (float)(1.0 - al), ut = (float)__ldcg(&c->ut_tau);
     // x (free): u_x = alpha (z_x - u~_tau g_x) + (1 - alpha) u_x
     for (int64_t v = tid; v < (n >> 2); v += stride) {
-      const bool f = prefetch && v == tid;
-      const float4 zz = f ? xz : ld4(zx, v), gg = f ? xg : ld4(gx, v);
-      float4 uu = f ? xu : ld4(ux, v);
+      const float4 zz = ld4(zx, v), gg = ld4(gx, v);
+      float4 uu = ld4(ux, v);
 #pragma unroll
       for (int k = 0; k < 4; ++k)
         el(uu, k) = __fadd_rn(__fmul_rn(a, __fsub_rn(elc(zz, k), __fmul_rn(ut, elc(gg, k)))),
@@ -820,10 +781,10 @@ __global__ void k_apply(Ctl* c, int64_t n, int64_t m, int64_t z, int64_t l, int 
     for (int64_t i = (n & ~(int64_t)3) + tid; i < n; i += stride)
       ux[i] = __fadd_rn(__fmul_rn(a, __fsub_rn(zx[i], __fmul_rn(ut, gx[i]))), __fmul_rn(a1, ux[i]));
     // zero rows (dual: free) and nonnegative rows of y
+    const int64_t nl = z + l;
     for (int64_t v = tid; v < (nl >> 2); v += stride) {
-      const bool f = prefetch && v == tid;
-      const float4 zz = f ? yz : ld4cg(zy, v), gg = f ? yg : ld4(gy, v);
-      float4 uu = f ? yu : ld4(uy, v), ss = f ? ys : ld4(vs, v);
+      const float4 zz = ld4(zy, v), gg = ld4(gy, v);
+      float4 uu = ld4(uy, v), ss = ld4(vs, v);
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         const float pj = y_pre(a, a1, ut, elc(zz, k), elc(gg, k), el(uu, k), el(ss, k));
@@ -835,13 +796,13 @@ __global__ void k_apply(Ctl* c, int64_t n, int64_t m, int64_t z, int64_t l, int 
       st4(vs, v, ss);
     }
     for (int64_t j = (nl & ~(int64_t)3) + tid; j < nl; j += stride) {
-      float pj = y_pre(a, a1, ut, __ldcg(zy + j), gy[j], uy[j], vs[j]);
+      float pj = y_pre(a, a1, ut, zy[j], gy[j], uy[j], vs[j]);
       float uj = j < z ? pj : fmaxf(pj, 0.f);
       uy[j] = uj;
       vs[j] = __fsub_rn(uj, pj);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-      const double uhat = al * __ldcg(&c->ut_tau) + (1.0 - al) * c->tau;
+      const double uhat = al * c->ut_tau + (1.0 - al) * c->tau;
       const double pt = uhat - c->kappa;
       const double tn = pt > 0.0 ? pt : 0.0;
       c->tau = tn;
@@ -873,38 +834,26 @@ __global__ void k_apply(Ctl* c, int64_t n, int64_t m, int64_t z, int64_t l, int 
   const int64_t ch = blockIdx.x - nlin;
   const int32_t sg = chunk_seg[ch];
   const int64_t head = seg_head[sg];
-  const int64_t r0 = chunk_r0[ch], r1 = chunk_r1[ch];
-  const int64_t q0 = (r0 + 3) & ~(int64_t)3, q1 = r1 & ~(int64_t)3;
-  const int64_t vf = (q0 >> 2) + threadIdx.x;
-  const bool pre = prefetch && q0 < q1 && vf < (q1 >> 2);
-  float4 z4f = zero4(), g4f = zero4(), u4f = zero4(), s4f = zero4();
-  if (pre) {
-    z4f = ld4cg(zy, vf);
-    g4f = ld4(gy, vf);
-    u4f = ld4(uy, vf);
-    s4f = ld4(vs, vf);
-  }
-  if (prefetch) pdl_wait();
-  const double al = c->st.alpha;
-  const float a = (float)al, a1 = (float)(1.0 - al), ut = (float)__ldcg(&c->ut_tau);
-  const double nrm = __ldcg(seg_nrm + sg), p0 = __ldcg(seg_p0 + sg);
+  const double nrm = seg_nrm[sg], p0 = seg_p0[sg];
   // 0: keep, 1: zero, 2: scale onto the boundary
   const int mode = nrm <= p0 ? 0 : (nrm <= -p0 ? 1 : 2);
   const double ah = 0.5 * (p0 + nrm);
   const float head_val = (float)ah;
   const float scl = mode == 2 ? (float)(ah / nrm) : 0.f;
+  const int64_t r0 = chunk_r0[ch], r1 = chunk_r1[ch];
   auto proj = [&](int64_t i, float pi) {
     if (mode == 0) return pi;
     if (mode == 1) return 0.f;
     return (i == head) ? head_val : __fmul_rn(scl, pi);
   };
   auto row = [&](int64_t i) {
-    const float pi = y_pre(a, a1, ut, __ldcg(zy + i), gy[i], uy[i], vs[i]);
+    const float pi = y_pre(a, a1, ut, zy[i], gy[i], uy[i], vs[i]);
     const float ui = proj(i, pi);
     uy[i] = ui;
     vs[i] = __fsub_rn(ui, pi);
   };
   // 16-byte accesses over the chunk's 4-aligned interior, single rows at its edges
+  const int64_t q0 = (r0 + 3) & ~(int64_t)3, q1 = r1 & ~(int64_t)3;
   if (q0 >= q1) {
     for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) row(i);
     return;
@@ -912,10 +861,9 @@ __global__ void k_apply(Ctl* c, int64_t n, int64_t m, int64_t z, int64_t l, int 
   for (int64_t i = r0 + threadIdx.x; i < q0; i += blockDim.x) row(i);
   for (int64_t i = q1 + threadIdx.x; i < r1; i += blockDim.x) row(i);
 #pragma unroll 2
-  for (int64_t v = vf; v < (q1 >> 2); v += blockDim.x) {
-    const bool f = pre && v == vf;
-    const float4 z4 = f ? z4f : ld4cg(zy, v), g4 = f ? g4f : ld4(gy, v);
-    float4 u4 = f ? u4f : ld4(uy, v), s4 = f ? s4f : ld4(vs, v);
+  for (int64_t v = (q0 >> 2) + threadIdx.x; v < (q1 >> 2); v += blockDim.x) {
+    const float4 z4 = ld4(zy, v), g4 = ld4(gy, v);
+    float4 u4 = ld4(uy, v), s4 = ld4(vs, v);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const float pi = y_pre(a, a1, ut, elc(z4, k), elc(g4, k), elc(u4, k), elc(s4, k));
@@ -1270,16 +1218,15 @@ void emit_post_cg(cf_problem* P, const Conds& cd, cudaStream_t s) {
   k_utau<<<red_grid(std::max(n, m)), kThreads, 0, s>>>(P->ctl, n, m, P->zx, P->az, P->zy, P->wy, P->bf, P->cf,
                                                        P->part, P->fold);
   if (P->nchunk > 0)
-    launch_pdl(k_soc_norm, (unsigned)P->nchunk, kThreads, s, (const Ctl*)P->ctl, (const int32_t*)P->chunk_seg,
-               (const int64_t*)P->chunk_r0, (const int64_t*)P->chunk_r1, (const int64_t*)P->seg_head,
-               (const int32_t*)P->seg_c0, (const int32_t*)P->seg_nc, (const float*)P->zy, (const float*)P->gy,
-               (const float*)P->uy, (const float*)P->vs, P->chunk_n2, P->seg_p0, P->seg_nrm, P->seg_cnt);
+    k_soc_norm<<<(unsigned)P->nchunk, kThreads, 0, s>>>(P->ctl, P->chunk_seg, P->chunk_r0, P->chunk_r1,
+                                                        P->seg_head, P->seg_c0, P->seg_nc, P->zy, P->gy,
+                                                        P->uy, P->vs, P->chunk_n2, P->seg_p0, P->seg_nrm,
+                                                        P->seg_cnt);
   const int nlin = grid_for(std::max<int64_t>(n, P->z + P->l));
-  launch_pdl(k_apply, (unsigned)(nlin + P->nchunk), kThreads, s, P->ctl, n, m, (int64_t)P->z, (int64_t)P->l, nlin,
-             P->ux, P->uy, P->vs, (const float*)P->zx, (const float*)P->zy, (const float*)P->gx,
-             (const float*)P->gy, (const int32_t*)P->chunk_seg, (const int64_t*)P->chunk_r0,
-             (const int64_t*)P->chunk_r1, (const int64_t*)P->seg_head, (const double*)P->seg_nrm,
-             (const double*)P->seg_p0, cd.check, cd.refresh, cd.outer, cd.in_graph, P->nchunk > 0 ? 1 : 0);
+  k_apply<<<(unsigned)(nlin + P->nchunk), kThreads, 0, s>>>(
+      P->ctl, n, m, P->z, P->l, nlin, P->ux, P->uy, P->vs, P->zx, P->zy, P->gx, P->gy, P->chunk_seg,
+      P->chunk_r0, P->chunk_r1, P->seg_head, P->seg_nrm, P->seg_p0, cd.check, cd.refresh, cd.outer,
+      cd.in_graph);
 }
 
 // residuals and certificates (every check_interval iterations)
