@@ -851,7 +851,7 @@ def per_iteration_hbm(n, m, iters, cg_total, seconds):
             "achieved_GBs": by / per / 1e9, "peak_GBs": hbm_peak(), "frac": by / per / 1e9 / hbm_peak()}
 
 
-def time_to_accuracy(args, B, ctx, torch, stream, prob, P, opt, eq, pinned):
+def time_to_accuracy(args, B, ctx, torch, stream, prob, P, opt, eq, pinned, cg_rel=DECONV_CG_TOL_REL):
     """Time to an accurate solution of the headline problem: the first eps of
     the ladder whose solve ends with residuals <= 1e-4 and the objective
     within 1e-4 of the FP64 optimum; at the tuned and at the library's
@@ -864,7 +864,7 @@ def time_to_accuracy(args, B, ctx, torch, stream, prob, P, opt, eq, pinned):
                          f"{ACCURACY:g}, t* = FP64 optimum (exact NNLS, certified bracket)"),
            "t_star": t_star, "t_star_bracket": opt["bracket"] if opt else None}
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    for name, pref in (("tuned", DECONV_CG_TOL_REL), ("default", LIB_CG_TOL_REL)):
+    for name, pref in (("tuned", cg_rel), ("default", LIB_CG_TOL_REL)):
         ladder = []
         for eps in EPS_LADDER:
             st = B.settings(max_iters=args.ttc_max_iters, eps=eps, cg_tol_rel=pref, engine=args.engine)
@@ -1141,7 +1141,7 @@ def main():
     ttc = None
     opt = None if small else deconv_optimum()
     if args.ttc_max_iters > 0 and not small:
-        ttc = time_to_accuracy(args, B, ctx, torch, stream, prob, P, opt, eq, pinned)
+        ttc = time_to_accuracy(args, B, ctx, torch, stream, prob, P, opt, eq, pinned, cg_rel)
     elif args.ttc_max_iters > 0:
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         st2 = B.settings(max_iters=args.ttc_max_iters, eps=1e-4, engine=st.engine, cg_tol_rel=cg_rel)
