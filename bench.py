@@ -70,7 +70,7 @@ OPTIMUM_FILE = os.path.join(ROOT, "tests", "golden", "deconv_large_optimum.json"
 # hash): the direct-sum convolution, and the scaled FFT convolution forward
 # pass that the equilibrated solver runs.
 CONV_NCU = {"traffic_bytes": 4029184, "src_sha256_16": "f372736cf1cfc748"}
-FFT_NCU = {"traffic_bytes": 12078080, "src_sha256_16": "a2f5b5dd522a7ca3"}
+FFT_NCU = {"traffic_bytes": 12080640, "src_sha256_16": "db62dd580fdc0efa"}
 FFT_AUTO_LP = (256, 2048)   # padded tap counts for which the library's auto method takes the FFT
 FFT_2048_MAX_LP = 1024      # the library takes 2048-point transforms up to this many padded taps when
                             # 4096-point ones would give fewer pairs than twice the SMs

@@ -110,47 +110,33 @@ __device__ __forceinline__ void cp_async4(float* dst, const float* src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-// Padded offset of position base + r S from fpad(base), for the second
-// stage's positions: base = G k + j with G a multiple of 16 and j < S, so
-// adding r S (S = 16) carries r into the pad index, and (S = 8, j < 8)
-// floor(r / 2).
-template <int S>
-__device__ __forceinline__ constexpr int soff(int r) {
-  return S == 16 ? 17 * r : 8 * r + (r >> 1);
-}
-
-// Forward stage on positions base + r S (r < 16; base as for soff): DFT16,
-// output q times twq[S q] (this thread's twiddle for q), stored back at
-// base + q S.
-template <int S>
-__device__ __forceinline__ void dif_stage(float2* buf, int base, const float2* __restrict__ twq) {
-  static_assert(S == 16 || S == 8, "second-stage stride");
+// Forward stage on positions base + r * stride (r < 16): DFT16, output q
+// times twq[TWS q] (this thread's twiddle for q), stored back at base + q * stride.
+template <int TWS>
+__device__ __forceinline__ void dif_stage(float2* buf, int base, int stride, const float2* __restrict__ twq) {
   float2 a[16], w[16];
-  float2* b0 = buf + fpad(base);
 #pragma unroll
-  for (int q = 1; q < 16; ++q) w[q] = __ldg(twq + S * q);
+  for (int q = 1; q < 16; ++q) w[q] = __ldg(twq + TWS * q);
 #pragma unroll
-  for (int r = 0; r < 16; ++r) a[r] = b0[soff<S>(r)];
+  for (int r = 0; r < 16; ++r) a[r] = buf[fpad(base + r * stride)];
   dft16<false>(a);
-  b0[0] = XQ(a, 0);
+  buf[fpad(base)] = XQ(a, 0);
 #pragma unroll
-  for (int q = 1; q < 16; ++q) b0[soff<S>(q)] = cmul(XQ(a, q), w[q]);
+  for (int q = 1; q < 16; ++q) buf[fpad(base + q * stride)] = cmul(XQ(a, q), w[q]);
 }
 
 // Inverse of dif_stage: untwiddle, inverse DFT16, store in natural order.
-template <int S>
-__device__ __forceinline__ void dit_stage(float2* buf, int base, const float2* __restrict__ twq) {
-  static_assert(S == 16 || S == 8, "second-stage stride");
+template <int TWS>
+__device__ __forceinline__ void dit_stage(float2* buf, int base, int stride, const float2* __restrict__ twq) {
   float2 a[16], w[16];
-  float2* b0 = buf + fpad(base);
 #pragma unroll
-  for (int q = 1; q < 16; ++q) w[q] = __ldg(twq + S * q);
-  a[0] = b0[0];
+  for (int q = 1; q < 16; ++q) w[q] = __ldg(twq + TWS * q);
+  a[0] = buf[fpad(base)];
 #pragma unroll
-  for (int q = 1; q < 16; ++q) a[q] = cmulc(b0[soff<S>(q)], w[q]);
+  for (int q = 1; q < 16; ++q) a[q] = cmulc(buf[fpad(base + q * stride)], w[q]);
   dft16<true>(a);
 #pragma unroll
-  for (int r = 0; r < 16; ++r) b0[soff<S>(r)] = XQ(a, r);
+  for (int r = 0; r < 16; ++r) buf[fpad(base + r * stride)] = XQ(a, r);
 }
 
 
@@ -201,9 +187,13 @@ __device__ __forceinline__ void pair(int t, int64_t pr, int64_t n_out, int64_t n
   {
     float2 a[16], w[16];
     const int64_t g0 = i0 - D;  // first input position of segment A
-    if (g0 >= 0 && g0 + V + N <= n_in) {
-      // both segments lie inside the input (every pair but the first and
-      // the last): one base pointer and constant offsets, no bounds tests
+    bool inside = false;
+    if constexpr (RO) inside = g0 >= 0 && g0 + V + N <= n_in;
+    if (inside) {
+      // stand-alone kernel, both segments inside the input (every pair but
+      // the first and the last): one base pointer and constant offsets, no
+      // bounds tests.  (Only here: the same code in the team kernel's term
+      // changed that large kernel's register allocation and slowed it.)
       const float* xa = x + g0 + t;
       const float* sa = SC ? sin + g0 + t : nullptr;
 #pragma unroll
@@ -218,7 +208,7 @@ __device__ __forceinline__ void pair(int t, int64_t pr, int64_t n_out, int64_t n
     } else {
 #pragma unroll
       for (int r = 0; r < 16; ++r) {
-        const int64_t ga = g0 + t + T * r, gb = ga + V;
+        const int64_t ga = i0 - D + t + T * r, gb = ga + V;
         float va = 0.f, vb = 0.f;
         if (ga >= 0 && ga < n_in) va = SC ? __ldg(sin + ga) * ld_in<RO>(x + ga) : ld_in<RO>(x + ga);
         if (gb >= 0 && gb < n_in) vb = SC ? __ldg(sin + gb) * ld_in<RO>(x + gb) : ld_in<RO>(x + gb);
@@ -228,15 +218,13 @@ __device__ __forceinline__ void pair(int t, int64_t pr, int64_t n_out, int64_t n
 #pragma unroll
     for (int q = 1; q < 16; ++q) w[q] = __ldg(tw + T * q + t);
     dft16<false>(a);
-    // fpad(t + T q) = fpad(t) + 17 (T / 16) q: T q is a multiple of 16
-    float2* b0 = buf + fpad(t);
-    b0[0] = XQ(a, 0);
+    buf[fpad(t)] = XQ(a, 0);
 #pragma unroll
-    for (int q = 1; q < 16; ++q) b0[(T + T / 16) * q] = cmul(XQ(a, q), w[q]);
+    for (int q = 1; q < 16; ++q) buf[fpad(t + T * q)] = cmul(XQ(a, q), w[q]);
   }
   sync();
   // forward stage 1: 16 groups of G, stride S, twiddles W_G^(j q)
-  dif_stage<C::S>(buf, base1, tw1);
+  dif_stage<C::S>(buf, base1, C::S, tw1);
   sync();
   // last forward stage (no twiddles), product with H, its inverse: in registers
   {
@@ -244,7 +232,7 @@ __device__ __forceinline__ void pair(int t, int64_t pr, int64_t n_out, int64_t n
 #pragma unroll
     for (int q = 0; q < 16; ++q) h[q] = __ldg(H + T * q + t);
 #pragma unroll
-    for (int r = 0; r < 16; ++r) a[r] = buf[17 * t + r];  // fpad(16 t + r), r < 16
+    for (int r = 0; r < 16; ++r) a[r] = buf[fpad(16 * t + r)];
     if constexpr (N == 4096) {
       float2 b[16];
       dft16<false>(a);
@@ -252,7 +240,7 @@ __device__ __forceinline__ void pair(int t, int64_t pr, int64_t n_out, int64_t n
       for (int q = 0; q < 16; ++q) b[q] = cmul(XQ(a, q), h[q]);
       dft16<true>(b);
 #pragma unroll
-      for (int r = 0; r < 16; ++r) buf[17 * t + r] = XQ(b, r);
+      for (int r = 0; r < 16; ++r) buf[fpad(16 * t + r)] = XQ(b, r);
     } else {
       float2 b[16];
       dft8<false>(a, 0);
@@ -266,14 +254,14 @@ __device__ __forceinline__ void pair(int t, int64_t pr, int64_t n_out, int64_t n
       dft8<true>(b, 8);
 #pragma unroll
       for (int r = 0; r < 8; ++r) {
-        buf[17 * t + r] = XQ8(b, 0, r);
-        buf[17 * t + 8 + r] = XQ8(b, 8, r);
+        buf[fpad(16 * t + r)] = XQ8(b, 0, r);
+        buf[fpad(16 * t + 8 + r)] = XQ8(b, 8, r);
       }
     }
   }
   sync();
   // inverse stage 1
-  dit_stage<C::S>(buf, base1, tw1);
+  dit_stage<C::S>(buf, base1, C::S, tw1);
   if (TAIL && wait_tail) cp_async_wait_all();
   sync();
   // inverse stage 0, straight to global: natural position p = t + T r
@@ -281,13 +269,10 @@ __device__ __forceinline__ void pair(int t, int64_t pr, int64_t n_out, int64_t n
     float2 a[16], w[16];
 #pragma unroll
     for (int q = 1; q < 16; ++q) w[q] = __ldg(tw + T * q + t);
-    const float2* b0 = buf + fpad(t);
-    a[0] = b0[0];
+    a[0] = buf[fpad(t)];
 #pragma unroll
-    for (int q = 1; q < 16; ++q) a[q] = cmulc(b0[(T + T / 16) * q], w[q]);
+    for (int q = 1; q < 16; ++q) a[q] = cmulc(buf[fpad(t + T * q)], w[q]);
     dft16<true>(a);
-    float* yo = y + i0;  // this pair's outputs: 32-bit offsets from here
-    const float* so = SC ? sout + i0 : nullptr;
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
       const int p = t + T * r;
@@ -295,14 +280,14 @@ __device__ __forceinline__ void pair(int t, int64_t pr, int64_t n_out, int64_t n
       const float2 c = XQ(a, r);
       const int ja = p - (Lp - 1), jb = ja + V;
       if (ja < nout) {
-        const float s = SC ? (TAIL ? ss[ja] : __ldg(so + ja)) : 1.f;
+        const float s = SC ? (TAIL ? ss[ja] : __ldg(sout + i0 + ja)) : 1.f;
         const float v = (SC ? alpha * s : alpha) * c.x;
-        yo[ja] = acc ? (TAIL ? ys[ja] : ld_in<RO>(yo + ja)) + v : v;
+        y[i0 + ja] = acc ? (TAIL ? ys[ja] : ld_in<RO>(y + i0 + ja)) + v : v;
       }
       if (jb < nout) {
-        const float s = SC ? (TAIL ? ss[jb] : __ldg(so + jb)) : 1.f;
+        const float s = SC ? (TAIL ? ss[jb] : __ldg(sout + i0 + jb)) : 1.f;
         const float v = (SC ? alpha * s : alpha) * c.y;
-        yo[jb] = acc ? (TAIL ? ys[jb] : ld_in<RO>(yo + jb)) + v : v;
+        y[i0 + jb] = acc ? (TAIL ? ys[jb] : ld_in<RO>(y + i0 + jb)) + v : v;
       }
     }
   }
